@@ -1,0 +1,281 @@
+"""Pins of the CPU FP64 oracle against what the paper and the mathematics fix
+(closed forms, brute force, invariants), plus planted-mistake checks that show
+the pins catch a transposed gate, a wrong sign and a wrong leg order."""
+import itertools
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from oracle import peps as op
+from oracle import statevector as sv
+from rqc_inputs import GATES, Gate, make_circuit, uniform_bitstrings
+
+RNG = np.random.default_rng(12345)
+
+
+def rand_unitary(rng):
+    z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def g1(q, U):
+    return Gate("1q", (q,), "U", np.asarray(U, dtype=np.complex128))
+
+
+def gcz(a, b):
+    return Gate("cz", (min(a, b), max(a, b)), "CZ")
+
+
+# ---------------------------------------------------------------------------
+# Closed forms for the state vector (P5) -- helpers return the max error so
+# that the planted-mistake tests can reuse them.
+# ---------------------------------------------------------------------------
+
+def err_product_state(n=5, seed=0):
+    """No CZ: a_x = prod_q <x_q| U_q |0> (each U_q a product of random
+    unitaries applied in order)."""
+    rng = np.random.default_rng(seed)
+    gates, tot = [], [np.eye(2, dtype=complex) for _ in range(n)]
+    for _ in range(3):
+        for q in range(n):
+            U = rand_unitary(rng)
+            gates.append(g1(q, U))
+            tot[q] = U @ tot[q]
+    a = sv.amplitudes(n, gates, np.arange(1 << n, dtype=np.uint64))
+    ref = np.array([np.prod([tot[q][(x >> q) & 1, 0] for q in range(n)]) for x in range(1 << n)])
+    return np.abs(a - ref).max()
+
+
+def err_hcz_h(R=3, C=3, layers=(0, 1, 2, 3)):
+    """H on all, some CZ layers, H on all:
+    a_x = 2^-n sum_y (-1)^(x.y + sum_{(i,j) in E} y_i y_j)."""
+    from rqc_inputs import cz_layer_edges
+    n = R * C
+    edges = [e for L in layers for e in cz_layer_edges(R, C, L)]
+    gates = [g1(q, GATES["H"]) for q in range(n)] + [gcz(*e) for e in edges] + \
+            [g1(q, GATES["H"]) for q in range(n)]
+    a = sv.amplitudes(n, gates, np.arange(1 << n, dtype=np.uint64))
+    ys = np.arange(1 << n)
+    ybits = (ys[:, None] >> np.arange(n)[None, :]) & 1
+    phase_e = np.zeros(1 << n, dtype=np.int64)
+    for (i, j) in edges:
+        phase_e += ybits[:, i] * ybits[:, j]
+    ref = np.zeros(1 << n)
+    for x in range(1 << n):
+        xy = ((ys & x).astype(np.int64))
+        par = np.array([bin(v).count("1") for v in xy]) + phase_e
+        ref[x] = np.sum((-1.0) ** par) / 2 ** n
+    return np.abs(a - ref).max()
+
+
+def test_statevector_product_state_closed_form():
+    assert err_product_state() < 1e-14
+
+
+def test_statevector_hh_is_identity():
+    n = 6
+    gates = [g1(q, GATES["H"]) for q in range(n)] * 2
+    a = sv.amplitudes(n, gates, np.arange(1 << n, dtype=np.uint64))
+    ref = np.zeros(1 << n)
+    ref[0] = 1
+    assert np.abs(a - ref).max() < 1e-15
+
+
+def test_statevector_h_cz_h_walsh_formula():
+    assert err_hcz_h() < 1e-14
+    assert err_hcz_h(2, 4, layers=range(8)) < 1e-14
+
+
+def test_statevector_bit_order():
+    # X = SX.SX on qubit q sends |0..0> to the basis state with only bit q set
+    n = 5
+    for q in range(n):
+        gates = [g1(q, GATES["SX"]), g1(q, GATES["SX"])]
+        psi = sv.run(n, gates)
+        assert abs(psi[1 << q] - 1) < 1e-15
+
+
+def test_statevector_norm():
+    for (R, C, d, s) in [(3, 3, 8, 1), (4, 4, 16, 2), (2, 5, 13, 3)]:
+        c = make_circuit(R, C, d, s)
+        psi = sv.run(R * C, c.gates)
+        assert abs(np.vdot(psi, psi) - 1) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# O3 (PEPS) against O2 (state vector): brute force (P1), norm (P2), bond
+# dimensions (P3), scale covariance (P8), orientation (P9), slicing (P6),
+# the SVD split (A1).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R,C,d,seed", [(2, 2, 8, 1), (2, 3, 16, 2), (3, 3, 8, 3),
+                                        (3, 3, 16, 4), (3, 4, 16, 5), (1, 4, 9, 6),
+                                        (4, 1, 9, 7)])
+def test_peps_equals_statevector_all_bitstrings(R, C, d, seed):
+    c = make_circuit(R, C, d, seed)
+    n = R * C
+    allx = np.arange(1 << n, dtype=np.uint64)
+    ref = sv.amplitudes(n, c.gates, allx)
+    p = op.build(R, C, c.gates)
+    a = op.amplitudes(p, allx)
+    assert np.abs(a - ref).max() < 1e-13
+    assert abs(np.sum(np.abs(a) ** 2) - 1) < 1e-12          # P2
+
+
+def test_peps_equals_statevector_4x4_sampled():
+    c = make_circuit(4, 4, 8, 1)
+    x = uniform_bitstrings(16, 512, 1)
+    ref = sv.amplitudes(16, c.gates, x)
+    a = op.amplitudes(op.build(4, 4, c.gates), x)
+    assert np.abs(a - ref).max() < 1e-14
+
+
+def test_peps_equals_statevector_4x5_d16_sampled():
+    c = make_circuit(4, 5, 16, 8)
+    x = uniform_bitstrings(20, 64, 8)
+    ref = sv.amplitudes(20, c.gates, x)
+    a = op.amplitudes(op.build(4, 5, c.gates), x)
+    assert np.abs(a - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("R,C,d", [(4, 4, 8), (5, 5, 16), (6, 6, 24), (6, 6, 32), (3, 4, 20)])
+def test_bond_dims_are_two_to_the_cz_count(R, C, d):
+    c = make_circuit(R, C, d, 1)
+    p = op.build(R, C, c.gates)
+    for r in range(R):
+        for col in range(C):
+            q = r * C + col
+            if col + 1 < C:
+                assert p.bond_dim(q, q + 1) == 2 ** c.cz_count(q, q + 1)
+            if r + 1 < R:
+                assert p.bond_dim(q, q + C) == 2 ** c.cz_count(q, q + C)
+    if d % 8 == 0:  # equality in the "chi" bound when 8 divides d
+        assert max(max(t.shape[1:]) for t in p.A) == 2 ** (d // 8)
+
+
+def test_scale_covariance():
+    c = make_circuit(3, 3, 16, 4)
+    x = uniform_bitstrings(9, 32, 4)
+    p = op.build(3, 3, c.gates)
+    gates2 = list(c.gates)
+    k = [i for i, g in enumerate(gates2) if g.kind == "1q" and g.cycle == 5][0]
+    g = gates2[k]
+    gates2[k] = Gate("1q", g.qubits, g.name, 8.0 * g.U, g.cycle)
+    a1 = op.amplitudes(p, x)
+    a2 = op.amplitudes(op.build(3, 3, gates2), x)
+    assert np.abs(a2 - 8 * a1).max() < 1e-14
+
+
+def test_row_sweep_equals_column_sweep():
+    c = make_circuit(4, 3, 16, 9)
+    x = uniform_bitstrings(12, 64, 9)
+    p = op.build(4, 3, c.gates)
+    assert np.abs(op.amplitudes(p, x, "row") - op.amplitudes(p, x, "column")).max() < 1e-14
+
+
+def transpose_circuit(c):
+    """The same circuit on the transposed lattice: qubit (r, c) -> (c, r)."""
+    R, C = c.R, c.C
+    m = {r * C + col: col * R + r for r in range(R) for col in range(C)}
+    gates = []
+    for g in c.gates:
+        if g.kind == "1q":
+            gates.append(Gate("1q", (m[g.qubits[0]],), g.name, g.U, g.cycle))
+        else:
+            a, b = m[g.qubits[0]], m[g.qubits[1]]
+            gates.append(Gate("cz", (min(a, b), max(a, b)), "CZ", None, g.cycle))
+    return SimpleNamespace(R=C, C=R, gates=gates), m
+
+
+def test_transposed_lattice_same_amplitudes():
+    c = make_circuit(3, 4, 16, 10)
+    ct, m = transpose_circuit(c)
+    x = uniform_bitstrings(12, 64, 10)
+    xt = np.array([sum(((int(v) >> q) & 1) << m[q] for q in range(12)) for v in x],
+                  dtype=np.uint64)
+    a = op.amplitudes(op.build(3, 4, c.gates), x)
+    at = op.amplitudes(op.build(4, 3, ct.gates), xt)
+    assert np.abs(a - at).max() < 1e-14
+
+
+def test_svd_split_gives_same_amplitudes():
+    c = make_circuit(3, 3, 16, 11)
+    x = uniform_bitstrings(9, 64, 11)
+    a = op.amplitudes(op.build(3, 3, c.gates, split="projector"), x)
+    b = op.amplitudes(op.build(3, 3, c.gates, split="svd"), x)
+    assert np.abs(a - b).max() < 1e-13
+    U, V = op.svd_split(op.cz_matrix())
+    assert U.shape[2] == 2  # chi_o = 2 for a controlled gate
+
+
+@pytest.mark.parametrize("sliced", [[0], [3, 7], [1, 5, 9, 20]])
+def test_slice_sum_identity(sliced):
+    c = make_circuit(3, 3, 16, 12)
+    x = uniform_bitstrings(9, 16, 12)
+    full = op.amplitudes(op.build(3, 3, c.gates), x)
+    tot = np.zeros_like(full)
+    for sid in range(1 << len(sliced)):
+        tot += op.amplitudes(op.build(3, 3, c.gates, sliced=sliced, slice_id=sid), x)
+    assert np.abs(tot - full).max() < 1e-14
+
+
+def test_prefix_reuse_equals_plain():
+    from rqc_inputs import prefix_group_bitstrings
+    c = make_circuit(3, 4, 16, 13)
+    x = prefix_group_bitstrings(3, 4, 2, 3, 5, 13)
+    p = op.build(3, 4, c.gates)
+    assert np.abs(op.amplitudes_with_prefix(p, x, 2) - op.amplitudes(p, x)).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each must be caught by one of the pins above.
+# ---------------------------------------------------------------------------
+
+def test_planted_transposed_gate_in_statevector_is_caught(monkeypatch):
+    orig = sv.apply_1q
+    monkeypatch.setattr(sv, "apply_1q", lambda psi, n, q, U: orig(psi, n, q, U.T))
+    assert err_product_state() > 1e-3
+
+
+def test_planted_wrong_cz_sign_is_caught(monkeypatch):
+    def bad_cz(psi, n, q0, q1):
+        lo, hi = min(q0, q1), max(q0, q1)
+        v = psi.reshape(1 << (n - hi - 1), 2, 1 << (hi - lo - 1), 2, 1 << lo)
+        v[:, 0, :, 1, :] *= -1.0          # flips |01> instead of |11>
+    monkeypatch.setattr(sv, "apply_cz", bad_cz)
+    assert err_hcz_h() > 1e-3
+
+
+def test_planted_wrong_bundling_in_peps_is_caught(monkeypatch):
+    # bundling s as the *slow* index on one site only (l' = (s, l) vs r' = (r, s))
+    def bad_split(self, q0, q1, U, V):
+        ax0, ax1 = self._shared_axes(q0, q1)
+        chi_o = U.shape[2]
+        a0 = np.einsum("tos,olrud->tlruds", U, self.A[q0])
+        a0 = np.moveaxis(a0, 5, ax0 + 1)
+        sh = list(self.A[q0].shape)
+        sh[ax0] *= chi_o
+        self.A[q0] = a0.reshape(sh)
+        a1 = np.einsum("sto,olrud->tlruds", V, self.A[q1])
+        a1 = np.moveaxis(a1, 5, ax1)          # s before the old leg
+        sh = list(self.A[q1].shape)
+        sh[ax1] *= chi_o
+        self.A[q1] = a1.reshape(sh)
+    monkeypatch.setattr(op.PEPS, "apply_2q_split", bad_split)
+    c = make_circuit(3, 3, 16, 4)
+    x = uniform_bitstrings(9, 64, 4)
+    ref = sv.amplitudes(9, c.gates, x)
+    a = op.amplitudes(op.build(3, 3, c.gates), x)
+    assert np.abs(a - ref).max() > 1e-3
+
+
+def test_planted_transposed_peps_gate_is_caught(monkeypatch):
+    orig = op.PEPS.apply_1q
+    monkeypatch.setattr(op.PEPS, "apply_1q", lambda self, q, U: orig(self, q, np.asarray(U).T))
+    c = make_circuit(3, 3, 8, 2)
+    x = uniform_bitstrings(9, 64, 2)
+    ref = sv.amplitudes(9, c.gates, x)
+    a = op.amplitudes(op.build(3, 3, c.gates), x)
+    assert np.abs(a - ref).max() > 1e-3
