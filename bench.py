@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the PEPS amplitude path on GB300.
+
+Workload: the 6x6 lattice at depth (1+32+1) (bond dimension 16 on every
+edge), 512 seeded bitstrings in 8 groups of 64 that share the bits of columns
+0-2, whose running tensor after column 2 is computed once per group.  One
+step = the whole path over the batch: circuit evolution (PEPS init, gate
+absorption), projection / operand build, the 36 site absorptions of every
+chain, FP64 reduction.
+
+value   amplitudes/s of the mixed-precision path (FP16 hi/lo split, three
+        tensor-core products, FP32 accumulate), bitstrings resident in HBM,
+        CUDA events around the timed steps on the launch stream.
+e2e     the same through the host C-ABI call (pinned host bitstrings copied
+        in, amplitudes copied out, inside the timed region).
+fp32_path  the plain FP32 CUDA-core form on the same GPU (timed on one group
+        of 64 bitstrings; the work per amplitude is identical across groups).
+roofline  the tensor-core contraction kernel: algorithmic flops per launch
+        (8 real flops per complex multiply-add) / mean launch time from CUDA
+        events recorded by the library around each launch.
+cpu_baseline  the CPU FP64 oracle on a bounded sample (see "sample").
+
+--impl reference times the oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitudes/s at 6x6 (1+32+1), mixed vs FP32 path, rel.err <= 1e-5"
+UNIT = "amplitudes/s"
+WORKLOAD = "6x6_d32"
+FLOPS_PER_CMAC = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--lanes", type=int, default=16)
+    ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default="bench", choices=["bench", "profile"],
+                    help="profile: one amplitude of the workload on one lane, no timing "
+                         "(the small case for ncu captures, about 4 GiB on the device)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample
+# ---------------------------------------------------------------------------
+
+def oracle_sample(seconds: float):
+    """Time the FP64 oracle's column sweep of the batch's first bitstring for
+    about `seconds` and scale by flops to the batched job's flops per
+    amplitude.  Returns (amplitudes/s, description, cores)."""
+    import numpy as np
+
+    from oracle import peps as op
+    from paper_1905_08394_gb300 import complexity as cx
+    from rqc_inputs import workload
+
+    circ, bits = workload(WORKLOAD)
+    p = op.build(circ.R, circ.C, circ.gates)
+    E = p.project(int(bits[0]))
+    steps = cx.column_sweep_step_cmacs(circ.R, circ.C, 16)
+    order = op.sweep_order(circ.R, circ.C, "column")
+    G, labels = np.ones((), dtype=np.complex128), []
+    t0 = time.perf_counter()
+    done = 0
+    cmacs = 0
+    for i, q in enumerate(order):
+        G, labels = op.absorb(G, labels, E[q], q, circ.R, circ.C)
+        cmacs += steps[i]
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    per_amp = (8 * sum(steps[:18]) + 512 * sum(steps[18:])) / 512  # prefix reuse, as the GPU job
+    rate = (cmacs / dt) / per_amp
+    desc = (f"oracle O3 (numpy complex128 tensordot) column sweep of bitstring 0, first {done} of "
+            f"36 site absorptions ({cmacs * FLOPS_PER_CMAC:.3e} flops in {dt:.1f} s), scaled by "
+            f"{per_amp * FLOPS_PER_CMAC:.3e} flops per amplitude of the batched job")
+    return rate, desc, os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+# Clocks
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index),
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1].split()[0]))
+                    smax.append(float(parts[2].split()[0]))
+                    power.append(float(parts[3].split()[0]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "mine" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        if pg:
+            pg.barrier()
+        return
+    vals = []
+    desc = cores = None
+    for _ in range(args.warmup):
+        oracle_sample(max(2.0, args.cpu_seconds / 4))
+    for _ in range(args.steps):
+        v, desc, cores = oracle_sample(args.cpu_seconds)
+        vals.append(v)
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 512 / value * 1000, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
+                                   "columns 0-2", "seed": 4},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+
+
+def run_mine(args):
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    circ, bits = workload(WORKLOAD)
+    n = len(bits)
+    sim = Simulator(circ.R, circ.C, device=local)
+    sim.apply_circuit(circ)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
+    d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
+    d_out = torch.empty(n, dtype=torch.complex128, device=dev)
+    flags = B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING
+
+    def step(s):
+        sim.amplitudes_device(d_bits, d_out, stream=s, flags=flags, **kw)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+    stream.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    tc_ms = tc_launches = 0.0
+    tc_flops = 0.0
+    launches = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(stream)
+        st = sim.stats()
+        tc_ms += st["contract_tc_ms"]
+        tc_launches += st["launches_contract_tc"]
+        tc_flops += st["contract_tc_flops"]
+        launches += st["launches_total"]
+    ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms / 1e3)
+
+    # correctness of the timed output on two sampled bitstrings is the job of
+    # tests/; here the result is only read back to be sure it is finite.
+    out = d_out.cpu().numpy()
+    finite = bool(np.isfinite(out).all())
+
+    # e2e through the host C-ABI call with pinned buffers
+    pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    opts, keep = B.make_opts(flags=B.PEPS_FLAG_REBUILD, **kw)
+    ws, nbytes = sim.workspace(n, opts)
+    out_host = torch.empty(n, dtype=torch.complex128).pin_memory()
+    lib = B.load()
+    sptr = stream.cuda_stream
+
+    def e2e_step():
+        rc = lib.peps_amplitudes(sim.h, pin_bits.data_ptr(), n, out_host.data_ptr(),
+                                 B.ct.byref(opts), ws, nbytes, sptr)
+        if rc != 0:
+            raise B.PepsError(rc, B.peps_last_error())
+
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * n * e2e_steps / e2e_s
+
+    # FP32 CUDA-core form on one group of 64
+    f32 = None
+    if args.fp32_steps > 0:
+        kw32 = dict(precision="fp32", prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
+        d_b64 = d_bits[:64].contiguous()
+        d_o64 = torch.empty(64, dtype=torch.complex128, device=dev)
+        sim.amplitudes_device(d_b64, d_o64, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kw32)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp32_steps):
+            sim.amplitudes_device(d_b64, d_o64, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kw32)
+        e1.record(stream)
+        stream.synchronize()
+        ms32 = e0.elapsed_time(e1) / args.fp32_steps
+        f32 = {"value": 64 / (ms32 / 1e3), "unit": UNIT, "bitstrings": 64,
+               "ms_per_step": ms32, "note": "plain FP32 CUDA-core form, one group of 64"}
+
+    peaks, src = load_peaks()
+    tc_avg_ms = tc_ms / tc_launches if tc_launches else None
+    achieved = (tc_flops / tc_launches) / (tc_avg_ms / 1e3) / 1e12 if tc_avg_ms else None
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    roof = None
+    if achieved is not None:
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_contract_tc (tcgen05, fp16 hi/lo, 3 MMAs per k-step)",
+                "peak_source": f"{src} bf16 dense sustained (fp16 dense rate = bf16 rate)",
+                "issued_frac": 3 * achieved / peak if args.precision in ("fp16x3", "bf16x3") else None,
+                "mean_launch_ms": tc_avg_ms, "launches": int(tc_launches)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, desc, cores = oracle_sample(args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "fp16x3" if args.precision == "fp16x3" else args.precision,
+                "data": "synthetic",
+                "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
+                                       "columns 0-2, prefix reuse", "seed": 4,
+                           "precision": args.precision, "lanes": args.lanes,
+                           "l2": "inputs larger than L2 (running tensor 2 GiB per lane)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                        "d2h_bytes_per_step": 16 * n},
+                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "fp32_path": f32, "clocks": clk, "finite": finite}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def run_profile_case(args):
+    """One amplitude (bitstring 0) of the workload through one lane."""
+    import numpy as np
+
+    from paper_1905_08394_gb300 import Simulator
+    from rqc_inputs import workload
+
+    circ, bits = workload(WORKLOAD)
+    sim = Simulator(circ.R, circ.C)
+    sim.apply_circuit(circ)
+    out = sim.amplitudes(bits[:1], precision=args.precision, max_lanes=1)
+    st = sim.stats()
+    print(json.dumps({"case": "profile", "amplitude": [out[0].real, out[0].imag],
+                      "launches": st["launches_total"], "tc_launches": st["launches_contract_tc"],
+                      "finite": bool(np.isfinite(out).all())}))
+    sim.close()
+
+
+def main():
+    args = parse()
+    if args.case == "profile":
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * peps_gb300.h -- C ABI of the GB300 (sm_103a) PEPS amplitude engine.
+ *
+ * Computes exact output amplitudes <x| C |0...0> of circuits on an R x C
+ * qubit lattice whose gates are single-qubit gates and nearest-neighbour CZ
+ * gates.  The state is held as an untruncated PEPS (paper, main text: the PEPS
+ * equation, single-qubit absorption "onebody", two-qubit split "factorize" and
+ * bundling "twoqubita/b"); each amplitude is obtained by projecting every site
+ * on its output bit (main text, "overlap") and contracting the network
+ * exactly, column by column (supplementary "exact computation of the
+ * overlap", generic scheme, transposed to sweep columns left to right).
+ *
+ * Conventions shared by every call:
+ *  - qubit index q = r*C + c, 0 <= r < R, 0 <= c < C, R*C <= 64;
+ *  - bit q of a uint64 bitstring is the output bit of qubit q;
+ *  - a 2x2 gate matrix U is row-major, U[tau*2 + sigma] = <tau|U|sigma>;
+ *  - CZ on an edge is split exactly as P_0 (x) I + P_1 (x) Z; the projector
+ *    factor goes on the site with the lower q; the new Schmidt bit s is the
+ *    least significant bit of the grown bond index (new = old*2 + s) on both
+ *    sites, so the k-th CZ applied to an edge owns bit (n_cz - 1 - k).
+ *
+ * Memory: the library never allocates device memory.  Every call that touches
+ * the GPU takes a caller-owned device workspace (size from
+ * peps_workspace_bytes) and a cudaStream_t passed as void*.  Host pointers
+ * stay owned by the caller and are not retained after a call returns.
+ *
+ * Errors: every function returns a peps_status.  On failure the outputs are
+ * left untouched and peps_last_error() returns a text for the calling thread.
+ * A device-side watchdog expiry returns PEPS_ETIMEOUT and marks the context
+ * PEPS_ESTATE until it is destroyed.
+ *
+ * Thread safety: a context may be used by one thread at a time.
+ */
+#ifndef PEPS_GB300_H
+#define PEPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PEPS_API __attribute__((visibility("default")))
+#else
+#define PEPS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct peps_ctx peps_ctx;
+
+typedef struct {
+    double re, im;
+} peps_c128;
+
+typedef enum {
+    PEPS_OK = 0,
+    PEPS_EINVAL = -1,       /* bad argument (range, null, size)              */
+    PEPS_ENOTADJ = -2,      /* CZ on qubits that are not lattice neighbours  */
+    PEPS_ENOMEM = -3,       /* workspace smaller than peps_workspace_bytes   */
+    PEPS_ECUDA = -4,        /* a CUDA runtime/driver call failed             */
+    PEPS_ETIMEOUT = -5,     /* a device wait exceeded the watchdog budget    */
+    PEPS_ESTATE = -6,       /* context unusable after an earlier failure     */
+    PEPS_EUNSUPPORTED = -7  /* valid request this build cannot run           */
+} peps_status;
+
+/* Arithmetic of the column-absorption contraction (the other kernels are
+ * FP32 complex; the final reduction is FP64).  Storage of the running tensor
+ * G between absorptions follows the form:
+ *   FP32_SIMT  fp32 complex, CUDA-core FMA                     (8 B / entry)
+ *   TF32       tcgen05 kind::tf32, G stored fp32 rounded to TF32 (8 B)
+ *   BF16       tcgen05 kind::f16 (bf16 inputs), G stored bf16   (4 B)
+ *   BF16X3     bf16 hi/lo split of G and of the site operand, three
+ *              products hi*hi + hi*lo + lo*hi                    (8 B)
+ *   FP16       tcgen05 kind::f16 (fp16 inputs), G stored fp16   (4 B)
+ *   FP16X3     fp16 hi/lo split, three products, G held in range by the
+ *              per-step power-of-two scaling                    (8 B)
+ * All tensor-core forms accumulate in FP32. */
+typedef enum {
+    PEPS_FP32_SIMT = 0,
+    PEPS_TF32 = 1,
+    PEPS_BF16 = 2,
+    PEPS_BF16X3 = 3,
+    PEPS_FP16 = 4,
+    PEPS_FP16X3 = 5,
+    PEPS_N_PRECISIONS = 6
+} peps_precision;
+
+enum {
+    PEPS_FLAG_REBUILD = 1,  /* re-run the circuit evolution even if unchanged */
+    PEPS_FLAG_TIMING = 2,   /* time every contraction launch with CUDA events */
+    PEPS_FLAG_NO_TC = 4     /* run every absorption on the CUDA-core kernel   */
+};
+
+/* Options of an amplitude call.  All-zero means: FP32_SIMT, no prefix reuse,
+ * lanes chosen from the workspace, no slicing, default watchdog. */
+typedef struct {
+    int32_t precision;        /* peps_precision                               */
+    int32_t flags;            /* PEPS_FLAG_*                                  */
+    int32_t prefix_cols;      /* >0: bitstrings are in groups of prefix_group
+                                 consecutive entries that share the bits of
+                                 every qubit in columns < prefix_cols; the
+                                 running tensor after those columns is
+                                 computed once per group (checked on device;
+                                 a violating group gives PEPS_EINVAL)          */
+    int32_t prefix_group;     /* group size for prefix_cols (>= 1)            */
+    int32_t max_lanes;        /* bitstrings contracted concurrently; 0 = as
+                                 many as the workspace holds (<= 64)          */
+    int32_t n_sliced;         /* number of sliced CZ gates                    */
+    const uint32_t *sliced_cz;/* ordinals (0 = first CZ applied) of the CZ
+                                 gates whose Schmidt bit is fixed per slice   */
+    const uint64_t *slice_ids;/* slices to sum: bit j = fixed s of
+                                 sliced_cz[j]; NULL = all 2^n_sliced          */
+    int64_t n_slice_ids;
+    int64_t watchdog_ns;      /* device wait budget; 0 = 2 s                  */
+} peps_opts;
+
+/* Counters of the last amplitude call (kernel launches are the library's own
+ * kernels; times are CUDA-event times on the call's stream). */
+typedef struct {
+    int64_t launches_total;
+    int64_t launches_evolve;     /* K1/K2: gate absorption                   */
+    int64_t launches_operand;    /* K3: projection + operand build           */
+    int64_t launches_contract;   /* K4: column absorption (all forms)        */
+    int64_t launches_contract_tc;/* of which tcgen05 kernels                 */
+    int64_t launches_finalize;   /* K6 (+checks)                             */
+    double contract_flops;       /* algorithmic real flops of K4 (8/cMAC)    */
+    double contract_bytes;       /* algorithmic bytes of K4 (read G + write G') */
+    double contract_ms;          /* summed event time of K4 launches (TIMING) */
+    double contract_tc_ms;       /* of which tcgen05 launches                */
+    double contract_tc_flops;
+    double contract_tc_bytes;
+    int64_t n_steps;             /* site absorptions per lane chain           */
+    int64_t n_lanes;             /* lanes used                                */
+} peps_stats;
+
+/* Create an empty circuit on an R x C lattice (state |0...0>, every bond of
+ * dimension 1).  Host-only; no GPU work.  R, C >= 1, R*C <= 64. */
+PEPS_API int peps_create(int R, int C, peps_ctx **out);
+
+/* Destroy a context.  Does not touch caller memory. */
+PEPS_API int peps_destroy(peps_ctx *ctx);
+
+/* Queue a single-qubit gate on qubit (r, c): A'^tau = sum_sigma U[tau][sigma]
+ * A^sigma (paper, main-text "onebody" equation).  U: 4 complex, row-major. */
+PEPS_API int peps_apply_1q(peps_ctx *ctx, int r, int c, const peps_c128 U[4]);
+
+/* Queue a CZ on nearest neighbours (r0,c0), (r1,c1) (|dr| + |dc| == 1;
+ * otherwise PEPS_ENOTADJ).  The bond on that edge doubles (paper, main-text
+ * "factorize" and "twoqubita/b" equations with chi_o = 2). */
+PEPS_API int peps_apply_cz(peps_ctx *ctx, int r0, int c0, int r1, int c1);
+
+/* Bond dimension of the edge between neighbours (r0,c0), (r1,c1):
+ * 2^(number of CZ gates applied to it) (paper, "chi" bound equation). */
+PEPS_API int peps_bond_dim(const peps_ctx *ctx, int r0, int c0, int r1, int c1, int64_t *dim);
+
+/* Static description of the contraction an amplitude call would run. */
+typedef struct {
+    int64_t n_steps;          /* site absorptions per chain (= R*C)          */
+    int64_t max_entries;      /* largest running tensor, complex entries     */
+    double flops_per_chain;   /* algorithmic real flops of one full sweep:
+                                 8 * sum over steps of M*K*N                 */
+    double bytes_per_chain;   /* algorithmic bytes of one full sweep: the
+                                 storage size of G read + G' written         */
+    double flops_call;        /* the same summed over every chain of the call
+                                 (prefix chains once per group, slices each) */
+    double bytes_call;
+    int64_t n_launches;       /* contraction launches of the call            */
+    int64_t n_tc_launches;    /* of which tcgen05                            */
+    int64_t n_slices;         /* slices summed                               */
+    int64_t lanes;            /* bitstrings contracted concurrently          */
+} peps_plan_info;
+
+/* Plan of an amplitude call on n_bitstrings with opts (host only). */
+PEPS_API int peps_plan_info_get(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
+                                peps_plan_info *info);
+
+/* Device workspace needed for an amplitude call on n_bitstrings with opts. */
+PEPS_API int peps_workspace_bytes(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
+                         size_t *bytes);
+
+/* Amplitudes <x_i| C |0...0> for host bitstrings[0..n) into host out[0..n).
+ * Copies the bitstrings to the device on `stream`, runs the device path,
+ * copies the results back and synchronises the stream before returning.
+ * With slicing, out[i] is the FP64 sum over the selected slices. */
+PEPS_API int peps_amplitudes(peps_ctx *ctx, const uint64_t *bitstrings, int64_t n, peps_c128 *out,
+                    const peps_opts *opts, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Same with device-resident bitstrings (d_bitstrings) and results (d_out,
+ * n peps_c128).  Enqueued on `stream`; returns after the host-side launch
+ * sequence, without synchronising unless PEPS_FLAG_TIMING is set or a check
+ * needs the device (prefix-group validation reads one int back). */
+PEPS_API int peps_amplitudes_device(peps_ctx *ctx, const uint64_t *d_bitstrings, int64_t n,
+                           peps_c128 *d_out, const peps_opts *opts, void *d_workspace,
+                           size_t ws_bytes, void *stream);
+
+/* Counters of the last amplitude call on this context. */
+PEPS_API int peps_get_stats(const peps_ctx *ctx, peps_stats *out);
+
+/* Number of CZ gates queued so far (their ordinals are 0..n-1). */
+PEPS_API int peps_cz_count(const peps_ctx *ctx, int64_t *n);
+
+/* Text of the last error on the calling thread ("" if none). */
+PEPS_API const char *peps_last_error(void);
+
+/* Library version string. */
+PEPS_API const char *peps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEPS_GB300_H */

@@ -1,0 +1,1081 @@
+// C ABI of the PEPS amplitude engine: circuit bookkeeping, the host planner
+// (evolution schedule, step list of the column sweep, lanes, prefix reuse,
+// slices, workspace layout) and the launch sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+using namespace peps;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(PEPS_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+namespace {
+
+struct GateRec {
+  int kind;        // 0 = 1q, 1 = cz
+  int q0, q1;      // q0 < q1 for cz
+  int horiz;       // cz on a horizontal edge (same row)
+  double U[8];     // re, im of U00, U01, U10, U11
+};
+
+struct Launch {
+  int kind;        // 0 = contraction step, 1 = finalize
+  StepShape shape;
+  bool tc;
+  void *tc_handle = nullptr;  // tensor maps of a tcgen05 launch
+  size_t a_base_rel = 0;      // input buffer of item lane 0 (relative to the buffer area)
+  int a_lanes = 1;            // lanes addressed through the A tensor map
+  int64_t items_off;  // index into the item array
+  int n_items;
+  int64_t fin_off;
+  int n_fin;
+  double flops, bytes;
+};
+
+struct Plan {
+  // key
+  uint64_t generation = 0;
+  int64_t n = 0;
+  peps_opts opts{};
+  std::vector<uint32_t> sliced;
+  std::vector<uint64_t> slice_ids;
+  const void *ws = nullptr;
+  size_t ws_bytes = 0;
+  const uint64_t *bits = nullptr;
+  bool host_bits = false;
+
+  // layout
+  size_t need = 0;
+  int fmt = FMT_F32;
+  int64_t cap = 0;          // entries per G buffer
+  int64_t plane = 0;        // lo-plane offset in 16-bit units
+  int n_steps = 0;
+  int lanes = 0;
+  int n_groups = 0;
+  size_t off_status = 0, off_site_ptrs = 0, off_g1 = 0, off_cz = 0, off_opdesc = 0,
+         off_opbuild = 0, off_recs = 0, off_items = 0, off_fin = 0, off_acc = 0,
+         off_bits = 0, off_out = 0, off_tables_end = 0;
+  std::vector<size_t> site_buf_off[2];
+  std::vector<int64_t> site_elems;
+  std::vector<size_t> ec_off, bt_off[2];
+  size_t lane_off = 0, prefix_off = 0;
+  size_t gbuf_bytes = 0;
+
+  // evolution batches
+  struct EvoBatch {
+    int kind;             // 0 = gate1, 1 = cz
+    int64_t off;          // first entry
+    int n;
+    int64_t max_work;
+  };
+  std::vector<EvoBatch> evo;
+  std::vector<int> final_buf;  // which ping-pong buffer holds the final site tensor
+
+  // step shapes
+  std::vector<StepShape> steps;
+  std::vector<int> step_site;
+
+  // launches (per slice iteration)
+  std::vector<Launch> launches;
+  int n_recs = 0;
+  int64_t n_opbuild_per_slice = 0;
+  int max_kn = 0;
+  std::vector<int64_t> slice_list;
+  double flops_per_slice = 0, bytes_per_slice = 0;
+
+  // host copy of the tables blob (uploaded once)
+  std::vector<unsigned char> blob;
+
+  ~Plan() {
+    for (auto &l : launches)
+      if (l.tc_handle) tc_release(l.tc_handle);
+  }
+};
+
+}  // namespace
+
+struct peps_ctx {
+  int R = 0, C = 0, n = 0;
+  std::vector<GateRec> gates;
+  std::vector<int> ncz_h, ncz_v;  // CZ count per horizontal / vertical edge
+  uint64_t generation = 1;
+  uint64_t built_generation = 0;
+  const void *built_ws = nullptr;
+  std::unique_ptr<Plan> plan;
+  peps_stats stats{};
+  bool broken = false;
+  std::vector<cudaEvent_t> ev;
+  int sm_count = 0;
+};
+
+static int edge_h(const peps_ctx *c, int r, int col) { return r * (c->C - 1) + col; }
+static int edge_v(const peps_ctx *c, int r, int col) { return r * c->C + col; }
+
+// ---------------------------------------------------------------------------
+// Circuit bookkeeping
+// ---------------------------------------------------------------------------
+extern "C" int peps_create(int R, int C, peps_ctx **out) {
+  if (!out) return fail(PEPS_EINVAL, "peps_create: out is NULL");
+  if (R < 1 || C < 1 || (int64_t)R * C > 64)
+    return fail(PEPS_EINVAL, "peps_create: need R, C >= 1 and R*C <= 64 (got %d x %d)", R, C);
+  peps_ctx *c = new peps_ctx();
+  c->R = R;
+  c->C = C;
+  c->n = R * C;
+  c->ncz_h.assign(R * std::max(C - 1, 0), 0);
+  c->ncz_v.assign(std::max(R - 1, 0) * C, 0);
+  *out = c;
+  return PEPS_OK;
+}
+
+extern "C" int peps_destroy(peps_ctx *c) {
+  if (!c) return fail(PEPS_EINVAL, "peps_destroy: NULL context");
+  for (auto e : c->ev) cudaEventDestroy(e);
+  delete c;
+  return PEPS_OK;
+}
+
+extern "C" int peps_apply_1q(peps_ctx *c, int r, int col, const peps_c128 U[4]) {
+  if (!c || !U) return fail(PEPS_EINVAL, "peps_apply_1q: NULL argument");
+  if (c->broken) return fail(PEPS_ESTATE, "context unusable after an earlier device failure");
+  if (r < 0 || r >= c->R || col < 0 || col >= c->C)
+    return fail(PEPS_EINVAL, "peps_apply_1q: qubit (%d,%d) outside %dx%d", r, col, c->R, c->C);
+  GateRec g{};
+  g.kind = 0;
+  g.q0 = g.q1 = r * c->C + col;
+  for (int i = 0; i < 4; ++i) {
+    if (!std::isfinite(U[i].re) || !std::isfinite(U[i].im))
+      return fail(PEPS_EINVAL, "peps_apply_1q: non-finite matrix entry");
+    g.U[2 * i] = U[i].re;
+    g.U[2 * i + 1] = U[i].im;
+  }
+  c->gates.push_back(g);
+  c->generation++;
+  return PEPS_OK;
+}
+
+extern "C" int peps_apply_cz(peps_ctx *c, int r0, int c0, int r1, int c1) {
+  if (!c) return fail(PEPS_EINVAL, "peps_apply_cz: NULL context");
+  if (c->broken) return fail(PEPS_ESTATE, "context unusable after an earlier device failure");
+  if (r0 < 0 || r0 >= c->R || c0 < 0 || c0 >= c->C || r1 < 0 || r1 >= c->R || c1 < 0 ||
+      c1 >= c->C)
+    return fail(PEPS_EINVAL, "peps_apply_cz: qubit outside the %dx%d lattice", c->R, c->C);
+  if (std::abs(r0 - r1) + std::abs(c0 - c1) != 1)
+    return fail(PEPS_ENOTADJ, "peps_apply_cz: (%d,%d) and (%d,%d) are not nearest neighbours",
+                r0, c0, r1, c1);
+  int qa = r0 * c->C + c0, qb = r1 * c->C + c1;
+  if (qa > qb) std::swap(qa, qb);
+  const int ra = qa / c->C, ca = qa % c->C;
+  const bool horiz = r0 == r1;  // by coordinates: on a one-column lattice qb == qa + 1 is vertical
+  int &cnt = horiz ? c->ncz_h[edge_h(c, ra, ca)] : c->ncz_v[edge_v(c, ra, ca)];
+  if (cnt >= 20) return fail(PEPS_EUNSUPPORTED, "peps_apply_cz: more than 20 CZ on one edge");
+  cnt++;
+  GateRec g{};
+  g.kind = 1;
+  g.q0 = qa;
+  g.q1 = qb;
+  g.horiz = horiz ? 1 : 0;
+  c->gates.push_back(g);
+  c->generation++;
+  return PEPS_OK;
+}
+
+extern "C" int peps_bond_dim(const peps_ctx *c, int r0, int c0, int r1, int c1, int64_t *dim) {
+  if (!c || !dim) return fail(PEPS_EINVAL, "peps_bond_dim: NULL argument");
+  if (r0 < 0 || r0 >= c->R || c0 < 0 || c0 >= c->C || r1 < 0 || r1 >= c->R || c1 < 0 ||
+      c1 >= c->C)
+    return fail(PEPS_EINVAL, "peps_bond_dim: qubit outside the lattice");
+  if (std::abs(r0 - r1) + std::abs(c0 - c1) != 1)
+    return fail(PEPS_ENOTADJ, "peps_bond_dim: not nearest neighbours");
+  int qa = r0 * c->C + c0, qb = r1 * c->C + c1;
+  if (qa > qb) std::swap(qa, qb);
+  const int ra = qa / c->C, ca = qa % c->C;
+  const int cnt = (r0 == r1) ? c->ncz_h[edge_h(c, ra, ca)] : c->ncz_v[edge_v(c, ra, ca)];
+  *dim = (int64_t)1 << cnt;
+  return PEPS_OK;
+}
+
+extern "C" int peps_cz_count(const peps_ctx *c, int64_t *n) {
+  if (!c || !n) return fail(PEPS_EINVAL, "peps_cz_count: NULL argument");
+  int64_t k = 0;
+  for (auto &g : c->gates) k += g.kind == 1;
+  *n = k;
+  return PEPS_OK;
+}
+
+extern "C" const char *peps_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *peps_version(void) { return "peps_gb300 0.1 (sm_103a)"; }
+
+extern "C" int peps_get_stats(const peps_ctx *c, peps_stats *out) {
+  if (!c || !out) return fail(PEPS_EINVAL, "peps_get_stats: NULL argument");
+  *out = c->stats;
+  return PEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Planner
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+struct LegInfo {
+  // per edge: full dim, sliced-bit mask (bits of the bond index that are fixed)
+  std::vector<int> dim_h, dim_v;
+  std::vector<uint32_t> fix_h, fix_v;
+};
+
+int popcount32(uint32_t x) { return __builtin_popcount(x); }
+
+// Which edge and bond bit a CZ ordinal owns.
+struct CzPos {
+  bool horiz;
+  int edge;
+  int bit;
+};
+
+int locate_cz(const peps_ctx *c, std::vector<CzPos> &pos) {
+  std::vector<int> seen_h(c->ncz_h.size(), 0), seen_v(c->ncz_v.size(), 0);
+  for (auto &g : c->gates) {
+    if (g.kind != 1) continue;
+    const int ra = g.q0 / c->C, ca = g.q0 % c->C;
+    CzPos p{};
+    if (g.horiz) {
+      p.horiz = true;
+      p.edge = edge_h(c, ra, ca);
+      p.bit = c->ncz_h[p.edge] - 1 - seen_h[p.edge]++;
+    } else {
+      p.horiz = false;
+      p.edge = edge_v(c, ra, ca);
+      p.bit = c->ncz_v[p.edge] - 1 - seen_v[p.edge]++;
+    }
+    pos.push_back(p);
+  }
+  return 0;
+}
+
+}  // namespace
+
+static bool opts_equal(const peps_opts &a, const peps_opts &b) {
+  return a.precision == b.precision && (a.flags & ~PEPS_FLAG_TIMING) == (b.flags & ~PEPS_FLAG_TIMING) &&
+         a.prefix_cols == b.prefix_cols && a.prefix_group == b.prefix_group &&
+         a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
+         a.n_slice_ids == b.n_slice_ids;
+}
+
+// Build (or size) the plan.  With ws == nullptr only sizes are computed.
+static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws,
+                      size_t ws_bytes, const uint64_t *bits_dev, bool host_bits, Plan &P) {
+  const int R = c->R, C = c->C, NQ = c->n;
+  if (n < 0) return fail(PEPS_EINVAL, "negative bitstring count");
+  if (o.precision < 0 || o.precision >= PEPS_N_PRECISIONS)
+    return fail(PEPS_EINVAL, "unknown precision %d", o.precision);
+  if (o.prefix_cols < 0 || o.prefix_cols >= C)
+    return fail(PEPS_EINVAL, "prefix_cols must be in [0, C) (got %d)", o.prefix_cols);
+  if (o.prefix_cols > 0 && o.prefix_group < 1)
+    return fail(PEPS_EINVAL, "prefix_group must be >= 1 with prefix_cols > 0");
+  if (o.prefix_cols > 0 && n % o.prefix_group != 0)
+    return fail(PEPS_EINVAL, "n (%lld) must be a multiple of prefix_group (%d)", (long long)n,
+                o.prefix_group);
+  if (o.max_lanes < 0 || o.max_lanes > 4096) return fail(PEPS_EINVAL, "max_lanes out of range");
+  if (o.n_sliced < 0 || o.n_sliced > 62) return fail(PEPS_EINVAL, "n_sliced out of range");
+  if (o.n_sliced > 0 && !o.sliced_cz) return fail(PEPS_EINVAL, "sliced_cz is NULL");
+  if (o.n_slice_ids < 0) return fail(PEPS_EINVAL, "n_slice_ids < 0");
+
+  P.generation = c->generation;
+  P.n = n;
+  P.opts = o;
+  P.ws = ws;
+  P.ws_bytes = ws_bytes;
+  P.bits = bits_dev;
+  P.host_bits = host_bits;
+  P.fmt = format_of(o.precision);
+  const int fmt = P.fmt;
+  const int bpe = format_bytes_per_entry(fmt);
+
+  // ---- slicing: which bond bits are fixed ----
+  std::vector<CzPos> czpos;
+  locate_cz(c, czpos);
+  LegInfo L;
+  L.dim_h.resize(c->ncz_h.size());
+  L.dim_v.resize(c->ncz_v.size());
+  for (size_t e = 0; e < c->ncz_h.size(); ++e) L.dim_h[e] = 1 << c->ncz_h[e];
+  for (size_t e = 0; e < c->ncz_v.size(); ++e) L.dim_v[e] = 1 << c->ncz_v[e];
+  L.fix_h.assign(c->ncz_h.size(), 0u);
+  L.fix_v.assign(c->ncz_v.size(), 0u);
+  P.sliced.assign(o.sliced_cz ? o.sliced_cz : nullptr, o.sliced_cz ? o.sliced_cz + o.n_sliced : nullptr);
+  for (int j = 0; j < o.n_sliced; ++j) {
+    const uint32_t k = o.sliced_cz[j];
+    if (k >= czpos.size()) return fail(PEPS_EINVAL, "sliced CZ ordinal %u out of range", k);
+    const CzPos &p = czpos[k];
+    uint32_t &m = p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge];
+    if (m & (1u << p.bit)) return fail(PEPS_EINVAL, "CZ ordinal %u sliced twice", k);
+    m |= 1u << p.bit;
+  }
+  P.slice_list.clear();
+  if (o.n_sliced > 0) {
+    if (o.slice_ids) {
+      for (int64_t i = 0; i < o.n_slice_ids; ++i) {
+        if (o.n_sliced < 64 && (o.slice_ids[i] >> o.n_sliced) != 0)
+          return fail(PEPS_EINVAL, "slice id %llu has bits beyond n_sliced",
+                      (unsigned long long)o.slice_ids[i]);
+        P.slice_list.push_back((int64_t)o.slice_ids[i]);
+      }
+      P.slice_ids.assign(o.slice_ids, o.slice_ids + o.n_slice_ids);
+    } else {
+      if (o.n_sliced > 24) return fail(PEPS_EINVAL, "pass slice_ids when n_sliced > 24");
+      for (int64_t s = 0; s < ((int64_t)1 << o.n_sliced); ++s) P.slice_list.push_back(s);
+    }
+  } else {
+    P.slice_list.push_back(0);
+  }
+
+  auto rdim_h = [&](int r, int col) -> int64_t {
+    if (col < 0 || col >= C - 1) return 1;
+    const int e = edge_h(c, r, col);
+    return (int64_t)L.dim_h[e] >> popcount32(L.fix_h[e]);
+  };
+  auto rdim_v = [&](int r, int col) -> int64_t {
+    if (r < 0 || r >= R - 1) return 1;
+    const int e = edge_v(c, r, col);
+    return (int64_t)L.dim_v[e] >> popcount32(L.fix_v[e]);
+  };
+  auto fdim_h = [&](int r, int col) -> int {
+    return (col < 0 || col >= C - 1) ? 1 : L.dim_h[edge_h(c, r, col)];
+  };
+  auto fdim_v = [&](int r, int col) -> int {
+    return (r < 0 || r >= R - 1) ? 1 : L.dim_v[edge_v(c, r, col)];
+  };
+
+  // ---- step list of the column sweep (legs tracked by identity) ----
+  // leg ids: h-edge (r, col) -> 1000 + r*64 + col ; v-leg -> 2 (dim 1 at the
+  // column ends, so the bottom leg of column c and the top leg of column c+1
+  // share the id).
+  struct Leg { int id; int64_t dim; };
+  std::vector<Leg> legs;
+  auto hid = [&](int r, int col) { return 1000 + r * 64 + (col + 1); };
+  for (int j = 1; j < R; ++j) legs.push_back({hid(j, -1), 1});
+  legs.push_back({hid(0, -1), 1});
+  legs.push_back({2, 1});
+  P.steps.clear();
+  P.step_site.clear();
+  int64_t cap = 1;
+  double flops = 0, bytes = 0;
+  for (int col = 0; col < C; ++col) {
+    for (int r = 0; r < R; ++r) {
+      const size_t nl = legs.size();
+      if (legs[nl - 2].id != hid(r, col - 1))
+        return fail(PEPS_EINVAL, "internal: leg order broken at (%d,%d)", r, col);
+      const int64_t K = legs[nl - 2].dim * legs[nl - 1].dim;
+      int64_t M = 1;
+      for (size_t i = 0; i + 2 < nl; ++i) M *= legs[i].dim;
+      const int64_t dh = rdim_h(r, col), dv = rdim_v(r, col);
+      const int64_t N = dh * dv;
+      const int64_t Pdim = (nl > 2) ? legs[0].dim : 1;
+      if (K > (1 << 20) || N > (1 << 20))
+        return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r, col);
+      StepShape sh{};
+      sh.M = M;
+      sh.K = (int)K;
+      sh.N = (int)N;
+      sh.P = Pdim;
+      sh.dv_out = (int)dv;
+      sh.dh_out = (int)dh;
+      sh.q = r * C + col;
+      sh.fmt = fmt;
+      sh.target = scale_target(fmt);
+      P.steps.push_back(sh);
+      P.step_site.push_back(r * C + col);
+      cap = std::max(cap, std::max(M * K, M * N));
+      flops += 8.0 * (double)M * K * N;
+      bytes += (double)bpe * (double)(M * K + M * N);
+      std::vector<Leg> nlgs;
+      if (nl > 2) {
+        for (size_t i = 1; i + 2 < nl; ++i) nlgs.push_back(legs[i]);
+        nlgs.push_back({hid(r, col), dh});
+        nlgs.push_back(legs[0]);
+        nlgs.push_back({r == R - 1 ? 2 : 3000 + r, dv});
+      } else {
+        nlgs.push_back({hid(r, col), dh});
+        nlgs.push_back({r == R - 1 ? 2 : 3000 + r, dv});
+      }
+      legs.swap(nlgs);
+    }
+  }
+  if (cap > ((int64_t)1 << 36)) return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
+  P.cap = cap;
+  P.n_steps = (int)P.steps.size();
+  P.flops_per_slice = flops;
+  P.bytes_per_slice = bytes;
+  // two-plane formats: the lo plane starts 1 KiB-aligned after the hi plane
+  if (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) {
+    const size_t plane_bytes = align_up((size_t)cap * 4, 1024);
+    P.plane = (int64_t)plane_bytes / 2;
+    P.gbuf_bytes = 2 * plane_bytes;
+  } else {
+    P.plane = 0;
+    P.gbuf_bytes = align_up((size_t)cap * bpe, 1024);
+  }
+  for (auto &s : P.steps) s.plane = P.plane;
+
+  // ---- lanes ----
+  const int pc = o.prefix_cols;
+  const int pre_steps = pc * R;
+  int64_t gs = pc > 0 ? o.prefix_group : std::max<int64_t>(n, 1);
+  P.n_groups = (pc > 0 && n > 0) ? (int)(n / gs) : 0;
+  int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
+  lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, gs), 1));
+  P.lanes = lanes;
+
+  // ---- site tensors ----
+  std::vector<int> sd(4 * NQ);
+  P.site_elems.assign(NQ, 0);
+  for (int q = 0; q < NQ; ++q) {
+    const int r = q / C, col = q % C;
+    sd[4 * q + 0] = fdim_h(r, col - 1);
+    sd[4 * q + 1] = fdim_h(r, col);
+    sd[4 * q + 2] = fdim_v(r - 1, col);
+    sd[4 * q + 3] = fdim_v(r, col);
+    P.site_elems[q] = 2LL * sd[4 * q] * sd[4 * q + 1] * sd[4 * q + 2] * sd[4 * q + 3];
+  }
+
+  // ---- workspace layout ----
+  size_t off = 0;
+  P.off_status = off; off = align_up(off + sizeof(DeviceStatus));
+  for (int b = 0; b < 2; ++b) P.site_buf_off[b].assign(NQ, 0);
+  for (int q = 0; q < NQ; ++q)
+    for (int b = 0; b < 2; ++b) {
+      P.site_buf_off[b][q] = off;
+      off = align_up(off + (size_t)P.site_elems[q] * sizeof(float2));
+    }
+  P.off_site_ptrs = off; off = align_up(off + NQ * sizeof(float2 *));
+
+  // evolution schedule (needs only offsets)
+  std::vector<Gate1Entry> g1;
+  std::vector<CzEntry> cz;
+  P.evo.clear();
+  {
+    std::vector<int> cur(NQ, 0);
+    std::vector<int> dims(4 * NQ, 1);
+    std::vector<int> in_batch(NQ, -1);
+    int batch_id = -1, batch_kind = -1;
+    auto site_ptr = [&](int q, int b) -> float2 * {
+      return (float2 *)((char *)ws + P.site_buf_off[b][q]);
+    };
+    auto start_batch = [&](int kind) {
+      Plan::EvoBatch eb{};
+      eb.kind = kind;
+      eb.off = kind == 0 ? (int64_t)g1.size() : (int64_t)cz.size();
+      eb.n = 0;
+      eb.max_work = 0;
+      P.evo.push_back(eb);
+      batch_id = (int)P.evo.size() - 1;
+      batch_kind = kind;
+    };
+    for (auto &g : c->gates) {
+      const int kind = g.kind;
+      bool clash = batch_kind != kind;
+      if (!clash) {
+        if (in_batch[g.q0] == batch_id) clash = true;
+        if (kind == 1 && in_batch[g.q1] == batch_id) clash = true;
+      }
+      if (clash || batch_id < 0) start_batch(kind);
+      Plan::EvoBatch &eb = P.evo[batch_id];
+      if (kind == 0) {
+        const int q = g.q0;
+        Gate1Entry e{};
+        e.A = site_ptr(q, cur[q]);
+        e.half = (int64_t)dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
+        for (int i = 0; i < 4; ++i) e.U[i] = make_float2((float)g.U[2 * i], (float)g.U[2 * i + 1]);
+        g1.push_back(e);
+        eb.n++;
+        eb.max_work = std::max(eb.max_work, e.half);
+        in_batch[q] = batch_id;
+      } else {
+        const bool horiz = g.horiz != 0;
+        const int qs[2] = {g.q0, g.q1};
+        const int axes[2] = {horiz ? 1 : 3, horiz ? 0 : 2};
+        for (int side = 0; side < 2; ++side) {
+          const int q = qs[side];
+          CzEntry e{};
+          e.in = site_ptr(q, cur[q]);
+          e.out = site_ptr(q, cur[q] ^ 1);
+          for (int a = 0; a < 4; ++a) e.dims[a] = dims[4 * q + a];
+          e.axis = axes[side];
+          e.kind = side;  // projector on the lower q, phase on the other
+          e.fixed_s = -1;
+          e.pad_ = 0;
+          dims[4 * q + e.axis] *= 2;
+          const int64_t out_n =
+              2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
+          cur[q] ^= 1;
+          cz.push_back(e);
+          eb.n++;
+          eb.max_work = std::max(eb.max_work, out_n);
+          in_batch[q] = batch_id;
+        }
+      }
+    }
+    P.final_buf = cur;
+    for (int q = 0; q < NQ; ++q)
+      for (int a = 0; a < 4; ++a)
+        if (dims[4 * q + a] != sd[4 * q + a])
+          return fail(PEPS_EINVAL, "internal: evolution dims mismatch at site %d", q);
+  }
+  P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
+  P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
+
+  // operands (restricted dims), two per site
+  const int n_ops = 2 * NQ;
+  P.ec_off.assign(n_ops, 0);
+  P.bt_off[0].assign(n_ops, 0);
+  P.bt_off[1].assign(n_ops, 0);
+  P.max_kn = 1;
+  const bool want_tc = o.precision != PEPS_FP32_SIMT && !(o.flags & PEPS_FLAG_NO_TC);
+  for (int s = 0; s < P.n_steps; ++s) {
+    const StepShape &sh = P.steps[s];
+    P.max_kn = std::max<int>(P.max_kn, sh.K * sh.N);
+    for (int t = 0; t < 2; ++t) {
+      const int op = 2 * sh.q + t;
+      P.ec_off[op] = off;
+      off = align_up(off + (size_t)sh.K * sh.N * sizeof(float2), 1024);
+      if (want_tc && tc_supports(sh, fmt)) {
+        const size_t planes = (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) ? 2 : 1;
+        const size_t esz = (fmt == FMT_TF32) ? 4 : 2;
+        const size_t pb = (size_t)tc_Kr_pad(sh.K) * tc_Nr_pad(sh.N) * esz;
+        for (size_t p = 0; p < planes; ++p) {
+          P.bt_off[p][op] = off;
+          off = align_up(off + pb, 1024);
+        }
+      }
+    }
+  }
+  P.off_opdesc = off; off = align_up(off + n_ops * sizeof(OpDesc));
+  P.n_opbuild_per_slice = n_ops;
+  P.off_opbuild = off;
+  off = align_up(off + (size_t)n_ops * P.slice_list.size() * sizeof(OpBuildEntry));
+
+  // records: chains = groups + bitstrings
+  P.n_recs = (int)((P.n_groups + n) * P.n_steps);
+  P.off_recs = off; off = align_up(off + std::max<size_t>(P.n_recs, 1) * sizeof(Rec));
+
+  // launches + items
+  std::vector<StepItem> items;
+  std::vector<FinalEntry> fins;
+  P.launches.clear();
+  const size_t lane_off_rel = 0;  // filled below
+  (void)lane_off_rel;
+  // buffers are placed after all tables; compute their offsets after sizing
+  // the item arrays, using relative positions first.
+  struct Pending { int64_t first_item; };
+  const int64_t NS = P.n_steps;
+  // Relative buffer addresses, resolved once the table sizes are known.
+  auto lane_buf = [&](int lane, int b) -> size_t {
+    return (size_t)(2 * lane + b) * P.gbuf_bytes;
+  };
+  auto pre_buf = [&](int b) -> size_t { return (size_t)(2 * P.lanes + b) * P.gbuf_bytes; };
+  const size_t REL = (size_t)1 << 62;  // marker: relative to the buffer area
+  struct RelItem { size_t a, d; bool a_unit; int64_t bit; };
+  std::vector<RelItem> rel;
+  auto add_step_launch = [&](int s, std::vector<StepItem> its, const std::vector<RelItem> &rs,
+                             int a_lanes) {
+    Launch ln{};
+    ln.kind = 0;
+    ln.shape = P.steps[s];
+    ln.tc = want_tc && tc_supports(P.steps[s], fmt);
+    ln.a_base_rel = rs[0].a;
+    ln.a_lanes = a_lanes;
+    for (size_t i = 0; i < its.size(); ++i) its[i].a_lane = a_lanes > 1 ? (int)i : 0;
+    ln.items_off = (int64_t)items.size();
+    ln.n_items = (int)its.size();
+    ln.flops = 8.0 * (double)ln.shape.M * ln.shape.K * ln.shape.N * ln.n_items;
+    ln.bytes = (double)bpe * (double)(ln.shape.M * ln.shape.K + ln.shape.M * ln.shape.N) * ln.n_items;
+    items.insert(items.end(), its.begin(), its.end());
+    rel.insert(rel.end(), rs.begin(), rs.end());
+    P.launches.push_back(ln);
+  };
+  if (pc > 0) {
+    for (int g = 0; g < P.n_groups; ++g) {
+      const int chain = g;
+      for (int s = 0; s < pre_steps; ++s) {
+        StepItem it{};
+        it.op_base = 2 * P.steps[s].q;
+        it.in_rec = s == 0 ? -1 : (int)(chain * NS + s - 1);
+        it.out_rec = (int)(chain * NS + s);
+        RelItem ri{s == 0 ? 0 : pre_buf((s - 1) % 2), pre_buf(s % 2), s == 0, (int64_t)g * gs};
+        add_step_launch(s, {it}, {ri}, 1);
+      }
+      const size_t pre_out = pre_buf((pre_steps - 1) % 2);
+      for (int64_t base = 0; base < gs; base += P.lanes) {
+        const int nl = (int)std::min<int64_t>(P.lanes, gs - base);
+        for (int s = pre_steps; s < NS; ++s) {
+          std::vector<StepItem> its;
+          std::vector<RelItem> rs;
+          for (int l = 0; l < nl; ++l) {
+            const int64_t i = (int64_t)g * gs + base + l;
+            const int64_t ch = P.n_groups + i;
+            StepItem it{};
+            it.op_base = 2 * P.steps[s].q;
+            it.in_rec = s == pre_steps ? (int)(chain * NS + pre_steps - 1) : (int)(ch * NS + s - 1);
+            it.out_rec = (int)(ch * NS + s);
+            RelItem ri{s == pre_steps ? pre_out : lane_buf(l, (s - 1 - pre_steps) % 2),
+                       lane_buf(l, (s - pre_steps) % 2), false, i};
+            its.push_back(it);
+            rs.push_back(ri);
+          }
+          add_step_launch(s, its, rs, s == pre_steps ? 1 : nl);
+        }
+        Launch fl{};
+        fl.kind = 1;
+        fl.fin_off = (int64_t)fins.size();
+        fl.n_fin = nl;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t i = (int64_t)g * gs + base + l;
+          FinalEntry f{};
+          f.G = (const void *)(REL + lane_buf(l, (NS - 1 - pre_steps) % 2));
+          f.rec = (int)((P.n_groups + i) * NS + NS - 1);
+          f.out_index = (int)i;
+          fins.push_back(f);
+        }
+        P.launches.push_back(fl);
+      }
+    }
+  } else {
+    for (int64_t base = 0; base < n; base += P.lanes) {
+      const int nl = (int)std::min<int64_t>(P.lanes, n - base);
+      for (int s = 0; s < NS; ++s) {
+        std::vector<StepItem> its;
+        std::vector<RelItem> rs;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t i = base + l;
+          StepItem it{};
+          it.op_base = 2 * P.steps[s].q;
+          it.in_rec = s == 0 ? -1 : (int)(i * NS + s - 1);
+          it.out_rec = (int)(i * NS + s);
+          RelItem ri{s == 0 ? 0 : lane_buf(l, (s - 1) % 2), lane_buf(l, s % 2), s == 0, i};
+          its.push_back(it);
+          rs.push_back(ri);
+        }
+        add_step_launch(s, its, rs, nl);
+      }
+      Launch fl{};
+      fl.kind = 1;
+      fl.fin_off = (int64_t)fins.size();
+      fl.n_fin = nl;
+      for (int l = 0; l < nl; ++l) {
+        const int64_t i = base + l;
+        FinalEntry f{};
+        f.G = (const void *)(REL + lane_buf(l, (NS - 1) % 2));
+        f.rec = (int)(i * NS + NS - 1);
+        f.out_index = (int)i;
+        fins.push_back(f);
+      }
+      P.launches.push_back(fl);
+    }
+  }
+  P.off_items = off; off = align_up(off + std::max<size_t>(items.size(), 1) * sizeof(StepItem));
+  P.off_fin = off; off = align_up(off + std::max<size_t>(fins.size(), 1) * sizeof(FinalEntry));
+  P.off_acc = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(double2));
+  P.off_bits = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(uint64_t));
+  P.off_out = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(peps_c128));
+  P.off_tables_end = off;
+  off = align_up(off, 4096);
+  P.lane_off = off;
+  const int n_gbufs = 2 * P.lanes + (pc > 0 ? 2 : 0);
+  off += (size_t)n_gbufs * P.gbuf_bytes;
+  P.need = off;
+  if (!ws) return PEPS_OK;
+  if (ws_bytes < P.need)
+    return fail(PEPS_ENOMEM, "workspace too small: %zu bytes given, %zu needed", ws_bytes, P.need);
+
+  // ---- resolve addresses and assemble the table blob ----
+  char *base = (char *)ws;
+  const DeviceStatus *st = (const DeviceStatus *)(base + P.off_status);
+  (void)st;
+  const uint64_t *bsrc = host_bits ? (const uint64_t *)(base + P.off_bits) : bits_dev;
+  for (size_t i = 0; i < items.size(); ++i) {
+    items[i].bits = bsrc + rel[i].bit;
+    items[i].A = rel[i].a_unit ? nullptr : (const void *)(base + P.lane_off + rel[i].a);
+    items[i].D = (void *)(base + P.lane_off + rel[i].d);
+  }
+  for (auto &f : fins) f.G = (const void *)(base + P.lane_off + ((size_t)f.G - REL));
+  for (auto &l : P.launches) {
+    if (l.kind != 0 || !l.tc) continue;
+    const int q = l.shape.q;
+    const void *bp[2][2];
+    for (int t = 0; t < 2; ++t)
+      for (int pl = 0; pl < 2; ++pl)
+        bp[t][pl] = P.bt_off[pl][2 * q + t] ? (const void *)(base + P.bt_off[pl][2 * q + t])
+                                             : (const void *)(base + P.bt_off[0][2 * q + t]);
+    int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
+                        (int64_t)(2 * P.gbuf_bytes), P.plane * 2, bp, &l.tc_handle);
+    if (rc != 0)
+      return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
+  }
+
+  std::vector<OpDesc> ops(n_ops);
+  for (int s = 0; s < P.n_steps; ++s) {
+    const StepShape &sh = P.steps[s];
+    for (int t = 0; t < 2; ++t) {
+      const int op = 2 * sh.q + t;
+      OpDesc d{};
+      d.Ec = (const float2 *)(base + P.ec_off[op]);
+      d.Bt[0] = P.bt_off[0][op] ? (const void *)(base + P.bt_off[0][op]) : nullptr;
+      d.Bt[1] = P.bt_off[1][op] ? (const void *)(base + P.bt_off[1][op]) : nullptr;
+      d.b_t = operand_scale_exp(fmt);
+      d.K = sh.K;
+      d.N = sh.N;
+      ops[op] = d;
+    }
+  }
+  // operand build entries per slice
+  std::vector<OpBuildEntry> obe;
+  for (int64_t sid : P.slice_list) {
+    // fixed values of every edge for this slice
+    std::vector<uint32_t> val_h(c->ncz_h.size(), 0u), val_v(c->ncz_v.size(), 0u);
+    for (int j = 0; j < o.n_sliced; ++j) {
+      const CzPos &p = czpos[o.sliced_cz[j]];
+      if ((sid >> j) & 1) (p.horiz ? val_h[p.edge] : val_v[p.edge]) |= 1u << p.bit;
+    }
+    for (int q = 0; q < NQ; ++q) {
+      const int r = q / C, col = q % C;
+      for (int t = 0; t < 2; ++t) {
+        OpBuildEntry e{};
+        const int fb = P.final_buf[q];
+        e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
+        for (int a = 0; a < 4; ++a) e.dims[a] = sd[4 * q + a];
+        // legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
+        auto leg = [&](int a, bool horiz, int rr, int cc) {
+          bool inside = horiz ? (cc >= 0 && cc < C - 1) : (rr >= 0 && rr < R - 1);
+          uint32_t fm = 0, fv = 0;
+          if (inside) {
+            const int eidx = horiz ? edge_h(c, rr, cc) : edge_v(c, rr, cc);
+            fm = horiz ? L.fix_h[eidx] : L.fix_v[eidx];
+            fv = horiz ? val_h[eidx] : val_v[eidx];
+          }
+          e.free_mask[a] = (uint32_t)(e.dims[a] - 1) & ~fm;
+          e.fixed_val[a] = fv;
+          e.rdims[a] = e.dims[a] >> popcount32(fm);
+        };
+        leg(0, true, r, col - 1);
+        leg(1, true, r, col);
+        leg(2, false, r - 1, col);
+        leg(3, false, r, col);
+        e.tau = t;
+        e.op = 2 * q + t;
+        obe.push_back(e);
+      }
+    }
+  }
+
+  std::vector<float2 *> site_ptrs(NQ);
+  for (int q = 0; q < NQ; ++q) site_ptrs[q] = (float2 *)(base + P.site_buf_off[0][q]);
+
+  P.blob.assign(P.off_tables_end - P.off_site_ptrs, 0);
+  auto put = [&](size_t off_abs, const void *src, size_t nbytes) {
+    if (nbytes) std::memcpy(P.blob.data() + (off_abs - P.off_site_ptrs), src, nbytes);
+  };
+  put(P.off_site_ptrs, site_ptrs.data(), NQ * sizeof(float2 *));
+  put(P.off_g1, g1.data(), g1.size() * sizeof(Gate1Entry));
+  put(P.off_cz, cz.data(), cz.size() * sizeof(CzEntry));
+  put(P.off_opdesc, ops.data(), ops.size() * sizeof(OpDesc));
+  put(P.off_opbuild, obe.data(), obe.size() * sizeof(OpBuildEntry));
+  put(P.off_items, items.data(), items.size() * sizeof(StepItem));
+  put(P.off_fin, fins.data(), fins.size() * sizeof(FinalEntry));
+  return PEPS_OK;
+}
+
+extern "C" int peps_workspace_bytes(const peps_ctx *c, int64_t n, const peps_opts *opts,
+                                    size_t *bytes) {
+  if (!c || !bytes) return fail(PEPS_EINVAL, "peps_workspace_bytes: NULL argument");
+  peps_opts o{};
+  if (opts) o = *opts;
+  Plan P;
+  int rc = build_plan(const_cast<peps_ctx *>(c), n, o, nullptr, 0, nullptr, false, P);
+  if (rc) return rc;
+  *bytes = P.need;
+  return PEPS_OK;
+}
+
+extern "C" int peps_plan_info_get(const peps_ctx *c, int64_t n, const peps_opts *opts,
+                                  peps_plan_info *info) {
+  if (!c || !info) return fail(PEPS_EINVAL, "peps_plan_info_get: NULL argument");
+  peps_opts o{};
+  if (opts) o = *opts;
+  Plan P;
+  int rc = build_plan(const_cast<peps_ctx *>(c), n, o, nullptr, 0, nullptr, false, P);
+  if (rc) return rc;
+  peps_plan_info I{};
+  I.n_steps = P.n_steps;
+  I.max_entries = P.cap;
+  I.flops_per_chain = P.flops_per_slice;
+  I.bytes_per_chain = P.bytes_per_slice;
+  for (auto &l : P.launches) {
+    if (l.kind != 0) continue;
+    I.flops_call += l.flops;
+    I.bytes_call += l.bytes;
+    I.n_launches++;
+    I.n_tc_launches += l.tc;
+  }
+  I.n_slices = (int64_t)P.slice_list.size();
+  I.flops_call *= (double)I.n_slices;
+  I.bytes_call *= (double)I.n_slices;
+  I.n_launches *= I.n_slices;
+  I.n_tc_launches *= I.n_slices;
+  I.lanes = P.lanes;
+  *info = I;
+  return PEPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Execution
+// ---------------------------------------------------------------------------
+static int ensure_events(peps_ctx *c, size_t n) {
+  while (c->ev.size() < n) {
+    cudaEvent_t e;
+    CUDA_TRY(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  return PEPS_OK;
+}
+
+static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s) {
+  char *base = (char *)P.ws;
+  DeviceStatus *st = (DeviceStatus *)(base + P.off_status);
+  const bool timing = (P.opts.flags & PEPS_FLAG_TIMING) != 0;
+  peps_stats S{};
+  S.n_steps = P.n_steps;
+  S.n_lanes = P.lanes;
+
+  if (c->sm_count == 0) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t wd_ns = P.opts.watchdog_ns > 0 ? P.opts.watchdog_ns : 2000000000LL;
+
+  // status + evolution
+  CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
+  const bool rebuild = (P.opts.flags & PEPS_FLAG_REBUILD) || c->built_generation != c->generation ||
+                       c->built_ws != P.ws;
+  if (rebuild) {
+    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs), c->n, st, s));
+    S.launches_evolve++;
+    for (auto &eb : P.evo) {
+      if (eb.kind == 0)
+        CUDA_TRY(launch_gate1((const Gate1Entry *)(base + P.off_g1) + eb.off, eb.n, eb.max_work / 1, s));
+      else
+        CUDA_TRY(launch_cz((const CzEntry *)(base + P.off_cz) + eb.off, eb.n, eb.max_work, s));
+      S.launches_evolve++;
+    }
+    c->built_generation = c->generation;
+    c->built_ws = P.ws;
+  } else {
+    // status block still needs its unit scalars
+    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs), 0, st, s));
+    S.launches_evolve++;
+  }
+
+  if (P.opts.prefix_cols > 0 && P.n > 0) {
+    uint64_t mask = 0;
+    for (int q = 0; q < c->n; ++q)
+      if (q % c->C < P.opts.prefix_cols) mask |= 1ull << q;
+    CUDA_TRY(launch_check_groups(d_bits_in, P.n, P.opts.prefix_group, mask, st, s));
+    S.launches_finalize++;
+  }
+
+  double2 *acc = (double2 *)(base + P.off_acc);
+  CUDA_TRY(cudaMemsetAsync(acc, 0, std::max<int64_t>(P.n, 1) * sizeof(double2), s));
+  Rec *recs = (Rec *)(base + P.off_recs);
+  OpDesc *ops = (OpDesc *)(base + P.off_opdesc);
+  const StepItem *items = (const StepItem *)(base + P.off_items);
+  const FinalEntry *fins = (const FinalEntry *)(base + P.off_fin);
+  const OpBuildEntry *obe = (const OpBuildEntry *)(base + P.off_opbuild);
+
+  size_t n_timed = 0;
+  if (timing) {
+    size_t nl = 0;
+    for (auto &l : P.launches) nl += l.kind == 0;
+    int rc = ensure_events(c, 2 * nl * P.slice_list.size());
+    if (rc) return rc;
+  }
+  std::vector<char> timed_tc;
+
+  for (size_t si = 0; si < P.slice_list.size(); ++si) {
+    if (P.n_recs > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, P.n_recs * sizeof(Rec), s));
+    const OpBuildEntry *e = obe + si * P.n_opbuild_per_slice;
+    CUDA_TRY(launch_build_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, s));
+    S.launches_operand += 2;
+    bool any_tc = false;
+    for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
+    if (any_tc) {
+      CUDA_TRY(launch_build_tc_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, P.fmt, s));
+      S.launches_operand++;
+    }
+    for (auto &l : P.launches) {
+      if (l.kind == 0) {
+        if (timing) CUDA_TRY(cudaEventRecord(c->ev[2 * n_timed], s));
+        if (l.tc) {
+          CUDA_TRY(launch_contract_tc(l.tc_handle, items + l.items_off, l.n_items, ops, recs,
+                                      st, wd_ns, c->sm_count, s));
+          S.launches_contract_tc++;
+          S.contract_tc_flops += l.flops;
+          S.contract_tc_bytes += l.bytes;
+        } else {
+          CUDA_TRY(launch_contract_simt(l.shape, items + l.items_off, l.n_items, ops, recs, st, s));
+        }
+        if (timing) {
+          CUDA_TRY(cudaEventRecord(c->ev[2 * n_timed + 1], s));
+          timed_tc.push_back(l.tc);
+          n_timed++;
+        }
+        S.launches_contract++;
+        S.contract_flops += l.flops;
+        S.contract_bytes += l.bytes;
+      } else {
+        CUDA_TRY(launch_finalize(fins + l.fin_off, l.n_fin, P.fmt, P.plane, recs, acc, s));
+        S.launches_finalize++;
+      }
+    }
+  }
+  S.launches_total = S.launches_evolve + S.launches_operand + S.launches_contract + S.launches_finalize;
+  if (timing) {
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < n_timed; ++i) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+      S.contract_ms += ms;
+      if (timed_tc[i]) S.contract_tc_ms += ms;
+    }
+  }
+  c->stats = S;
+  return PEPS_OK;
+}
+
+static int check_status(peps_ctx *c, Plan &P, cudaStream_t s) {
+  DeviceStatus h{};
+  CUDA_TRY(cudaMemcpyAsync(&h, (char *)P.ws + P.off_status, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.timeout) {
+    c->broken = true;
+    return fail(PEPS_ETIMEOUT, "a device wait exceeded the watchdog budget (site step %d)", h.error_info);
+  }
+  if (h.error)
+    return fail(PEPS_EINVAL, "prefix group check failed at bitstring %d: bits of the first %d "
+                "columns differ inside a group", h.error_info, P.opts.prefix_cols);
+  return PEPS_OK;
+}
+
+static int prepare(peps_ctx *c, int64_t n, const peps_opts *opts, void *ws, size_t ws_bytes,
+                   const uint64_t *bits_dev, bool host_bits) {
+  peps_opts o{};
+  if (opts) o = *opts;
+  Plan *P = c->plan.get();
+  bool reuse = P && P->generation == c->generation && P->n == n && opts_equal(P->opts, o) &&
+               P->ws == ws && P->ws_bytes == ws_bytes && P->bits == bits_dev &&
+               P->host_bits == host_bits;
+  if (reuse && o.n_sliced > 0) {
+    reuse = P->sliced == std::vector<uint32_t>(o.sliced_cz, o.sliced_cz + o.n_sliced);
+    if (reuse && o.slice_ids)
+      reuse = P->slice_ids == std::vector<uint64_t>(o.slice_ids, o.slice_ids + o.n_slice_ids);
+  }
+  if (reuse) {
+    P->opts.flags = o.flags;
+    P->opts.watchdog_ns = o.watchdog_ns;
+    return PEPS_OK;
+  }
+  auto NP = std::make_unique<Plan>();
+  int rc = build_plan(c, n, o, ws, ws_bytes, bits_dev, host_bits, *NP);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpy((char *)ws + NP->off_site_ptrs, NP->blob.data(), NP->blob.size(),
+                      cudaMemcpyHostToDevice));
+  c->plan = std::move(NP);
+  c->built_generation = 0;  // site buffers may have moved: re-evolve
+  return PEPS_OK;
+}
+
+extern "C" int peps_amplitudes_device(peps_ctx *c, const uint64_t *d_bits, int64_t n,
+                                      peps_c128 *d_out, const peps_opts *opts, void *ws,
+                                      size_t ws_bytes, void *stream) {
+  if (!c) return fail(PEPS_EINVAL, "peps_amplitudes_device: NULL context");
+  if (c->broken) return fail(PEPS_ESTATE, "context unusable after an earlier device failure");
+  if (n < 0 || (n > 0 && (!d_bits || !d_out)) || !ws)
+    return fail(PEPS_EINVAL, "peps_amplitudes_device: bad arguments");
+  if (n == 0) return PEPS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = prepare(c, n, opts, ws, ws_bytes, d_bits, false);
+  if (rc) return rc;
+  Plan &P = *c->plan;
+  rc = run_plan(c, P, d_bits, s);
+  if (rc) return rc;
+  CUDA_TRY(launch_store_out((const double2 *)((char *)ws + P.off_acc), d_out, n, s));
+  c->stats.launches_finalize++;
+  c->stats.launches_total++;
+  const bool needs_check = (P.opts.flags & PEPS_FLAG_TIMING) || P.opts.prefix_cols > 0;
+  if (needs_check) return check_status(c, P, s);
+  return PEPS_OK;
+}
+
+extern "C" int peps_amplitudes(peps_ctx *c, const uint64_t *bits, int64_t n, peps_c128 *out,
+                               const peps_opts *opts, void *ws, size_t ws_bytes, void *stream) {
+  if (!c) return fail(PEPS_EINVAL, "peps_amplitudes: NULL context");
+  if (c->broken) return fail(PEPS_ESTATE, "context unusable after an earlier device failure");
+  if (n < 0 || (n > 0 && (!bits || !out)) || !ws)
+    return fail(PEPS_EINVAL, "peps_amplitudes: bad arguments");
+  if (n == 0) return PEPS_OK;
+  for (int64_t i = 0; i < n; ++i)
+    if (c->n < 64 && (bits[i] >> c->n) != 0)
+      return fail(PEPS_EINVAL, "bitstring %lld has bits beyond qubit %d", (long long)i, c->n - 1);
+  cudaStream_t s = (cudaStream_t)stream;
+  // The staging area sits at a fixed place in the workspace; the plan's items
+  // point there.
+  int rc = prepare(c, n, opts, ws, ws_bytes, nullptr, true);
+  if (rc) return rc;
+  Plan &P = *c->plan;
+  uint64_t *d_bits = (uint64_t *)((char *)ws + P.off_bits);
+  peps_c128 *d_out = (peps_c128 *)((char *)ws + P.off_out);
+  CUDA_TRY(cudaMemcpyAsync(d_bits, bits, n * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  rc = run_plan(c, P, d_bits, s);
+  if (rc) return rc;
+  CUDA_TRY(launch_store_out((const double2 *)((char *)ws + P.off_acc), d_out, n, s));
+  c->stats.launches_finalize++;
+  c->stats.launches_total++;
+  rc = check_status(c, P, s);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(out, d_out, n * sizeof(peps_c128), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PEPS_OK;
+}

@@ -1,0 +1,188 @@
+// Internal declarations shared by the translation units of libpeps_gb300.
+// Not part of the public ABI (see include/peps_gb300.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/peps_gb300.h"
+
+namespace peps {
+
+// ---------------------------------------------------------------------------
+// Storage formats of the running tensor G (one complex entry = re, im).
+// ---------------------------------------------------------------------------
+enum Format : int {
+  FMT_F32 = 0,     // float2                                  (8 B / entry)
+  FMT_BF16 = 1,    // bf16 re, bf16 im, interleaved            (4 B)
+  FMT_FP16 = 2,    // fp16 re, fp16 im, interleaved            (4 B)
+  FMT_BF16X2 = 3,  // two planes (hi, lo) of interleaved bf16  (8 B)
+  FMT_FP16X2 = 4,  // two planes (hi, lo) of interleaved fp16  (8 B)
+  FMT_TF32 = 5,    // float2 holding values rounded to TF32    (8 B)
+};
+
+inline int format_of(int precision) {
+  switch (precision) {
+    case PEPS_FP32_SIMT: return FMT_F32;
+    case PEPS_TF32: return FMT_TF32;
+    case PEPS_BF16: return FMT_BF16;
+    case PEPS_BF16X3: return FMT_BF16X2;
+    case PEPS_FP16: return FMT_FP16;
+    case PEPS_FP16X3: return FMT_FP16X2;
+  }
+  return -1;
+}
+
+inline int format_bytes_per_entry(int fmt) {
+  return (fmt == FMT_BF16 || fmt == FMT_FP16) ? 4 : 8;
+}
+
+// Largest stored magnitude the per-step scaling aims for: 2^target.  FP16
+// formats keep G near the top of their range so that the lo plane of a
+// hi/lo split stays normal; the other formats keep G at most 1.
+inline int scale_target(int fmt) {
+  return (fmt == FMT_FP16 || fmt == FMT_FP16X2) ? 14 : 0;
+}
+
+// Scale exponent of the tensor-core site operand (B) per format: the site
+// tensor entries satisfy |E| <= 1, so 2^12 keeps fp16 pieces in range.
+inline int operand_scale_exp(int fmt) {
+  return (fmt == FMT_FP16 || fmt == FMT_FP16X2) ? 12 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Device-side tables
+// ---------------------------------------------------------------------------
+
+// One site operand E = A_q^{tau} (optionally restricted to a slice), in the
+// layouts the contraction kernels read.
+struct OpDesc {
+  const float2 *Ec;     // [K][N] complex64, k = l*du + u, n = r*dd + d
+  const void *Bt[2];    // tensor-core planes [Nr_pad][Kr_pad] (hi, lo), or null
+  uint32_t beta_c_bits; // max_n sum_k (|Re E_kn| + |Im E_kn|), float bits
+  uint32_t beta_t_bits; // same bound for the scaled tensor-core planes
+  int32_t b_t;          // scale exponent of the tensor-core planes
+  int32_t K, N;         // complex dims
+  int32_t pad_;
+};
+
+// Per (lane, step) record: the max |stored entry| of the step's output
+// (float bits, atomicMax target) and the cumulative scale exponent S:
+// stored G = true G * 2^S.
+struct Rec {
+  uint32_t maxbits;
+  int32_t exp;
+};
+
+// One work item of a contraction launch: one lane (bitstring or prefix
+// chain) absorbing one site.
+struct StepItem {
+  const void *A;          // input G (format of the launch)
+  void *D;                // output G
+  const uint64_t *bits;   // the lane's bitstring (device)
+  int32_t op_base;        // OpDesc index of tau = 0 (tau = 1 is op_base + 1)
+  int32_t in_rec;         // Rec index of the input (-1: the unit scalar)
+  int32_t out_rec;        // Rec index of the output
+  int32_t a_lane;         // lane coordinate of A in the launch's tensor map
+};
+
+// Shape shared by all items of a launch.
+struct StepShape {
+  int64_t M;      // product of the untouched h legs
+  int32_t K;      // dim(h_r) * dim(v)
+  int32_t N;      // dim(h'_r) * dim(v')
+  int64_t P;      // dim of the slowest M leg (moved next to v' on store)
+  int32_t dv_out; // dim(v')
+  int32_t dh_out; // dim(h'_r)
+  int32_t q;      // site
+  int32_t fmt;    // storage format of A and D
+  int64_t plane;  // element offset of the lo plane (FMT_*X2), in 16-bit units
+  int32_t target; // scale target exponent
+  int32_t pad_;
+};
+
+// Evolution tables.
+struct Gate1Entry {  // single-qubit gate on one site tensor (in place)
+  float2 *A;
+  int64_t half;      // elements per sigma slice
+  float2 U[4];
+};
+
+struct CzEntry {     // one half of a CZ on one site tensor (out of place)
+  const float2 *in;
+  float2 *out;
+  int32_t dims[4];   // input l, r, u, d
+  int32_t axis;      // 0..3 = l, r, u, d
+  int32_t kind;      // 0 = projector P_s, 1 = phase Z^s
+  int32_t fixed_s;   // -1: bundle s into the leg; 0/1: sliced term
+  int32_t pad_;
+};
+
+// Operand build entry (one site, one tau, one slice variant).
+struct OpBuildEntry {
+  const float2 *A;      // site tensor [2][l][r][u][d] (full dims)
+  int32_t dims[4];      // full dims l, r, u, d
+  int32_t rdims[4];     // restricted dims
+  uint32_t free_mask[4];// bits of the full index that vary (per leg)
+  uint32_t fixed_val[4];// value of the fixed bits (per leg)
+  int32_t tau;
+  int32_t op;           // OpDesc index to fill
+};
+
+struct FinalEntry {     // one output amplitude contribution
+  const void *G;        // final 1x1 G of a lane
+  int32_t rec;          // its Rec
+  int32_t out_index;    // bitstring index
+};
+
+// Status words at the head of the workspace.
+struct DeviceStatus {
+  int32_t error;        // nonzero: a device check failed
+  int32_t error_info;
+  int32_t timeout;      // nonzero: a bounded wait expired
+  int32_t pad_;
+  float2 unit_f32;      // the scalar 1 in each format
+  uint32_t unit_h16[2]; // bf16 (re=1, im=0) hi plane / lo plane
+  uint32_t unit_f16[2]; // fp16 (re=1, im=0) hi plane / lo plane
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+cudaError_t launch_init_sites(float2 *const *bufs, int n_sites, DeviceStatus *st,
+                              cudaStream_t s);
+cudaError_t launch_gate1(const Gate1Entry *d_entries, int n, int64_t max_half,
+                         cudaStream_t s);
+cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStream_t s);
+cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
+                                  OpDesc *d_ops, cudaStream_t s);
+cudaError_t launch_build_tc_operands(const OpBuildEntry *d_entries, int n, int max_kn,
+                                     OpDesc *d_ops, int fmt, cudaStream_t s);
+cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, int n_items,
+                                 const OpDesc *d_ops, Rec *d_recs, const DeviceStatus *st,
+                                 cudaStream_t s);
+cudaError_t launch_finalize(const FinalEntry *d_entries, int n, int fmt, int64_t plane,
+                            const Rec *d_recs, double2 *d_acc, cudaStream_t s);
+cudaError_t launch_store_out(const double2 *d_acc, peps_c128 *d_out, int64_t n,
+                             cudaStream_t s);
+cudaError_t launch_check_groups(const uint64_t *d_bits, int64_t n, int group,
+                                uint64_t mask, DeviceStatus *st, cudaStream_t s);
+
+// tcgen05 contraction (contract_tc.cu).
+bool tc_supports(const StepShape &sh, int fmt);
+// Encode the launch's tensor maps (A over the lanes' input buffers, Bt for
+// tau = 0/1 and each plane); returns 0 and an opaque handle, or < 0.
+int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
+               void **out_handle);
+void tc_release(void *handle);
+cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
+                               const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,
+                               int64_t watchdog_ns, int sm_count, cudaStream_t s);
+int tc_Kr_pad(int K);   // real K of a tensor-core operand
+int tc_Nr_pad(int N);   // real N
+
+}  // namespace peps

@@ -1,0 +1,621 @@
+// K4 (tensor-core forms): one site absorption of the column sweep as a
+// complex-as-real GEMM on the 5th-generation tensor cores (tcgen05), for a
+// batch of lanes,
+//   D[M x Nr] = A[M x Kr] * Bt[Nr x Kr]^T,   Kr = 2K, Nr = 2N,
+// A = the running tensor G (interleaved re/im, the contracted legs (h_r, v)
+// fastest), Bt = the real embedding of the site operand E:
+//   Bt[2n  ][2k] =  Re E_kn   Bt[2n  ][2k+1] = -Im E_kn
+//   Bt[2n+1][2k] =  Im E_kn   Bt[2n+1][2k+1] =  Re E_kn
+// so that D's row is the interleaved complex output row (supplementary
+// exact-overlap absorption step, transposed to columns).
+//
+// Forms: BF16 / FP16 (kind::f16, one MMA per k-step), BF16X2 / FP16X2 (hi/lo
+// planes of A and Bt, three MMAs hi*hi + hi*lo + lo*hi accumulated in FP32),
+// TF32 (kind::tf32, one MMA).
+//
+// Structure: persistent CTAs (one per SM) walk tiles (lane, 128-row M block,
+// N block of up to 256 real columns).  Warp 0 issues TMA loads of A and Bt
+// tiles (128-byte or 64-byte swizzle) into a ring of shared-memory stages,
+// warp 1 issues tcgen05.mma into one of two TMEM accumulators, warps 2..5
+// drain the other accumulator with tcgen05.ld, apply the step's power-of-two
+// scale, split into the storage format and store permuted (the slowest
+// untouched leg moves next to v'), and record the max |entry|.  Every wait is
+// bounded by a %globaltimer budget; on expiry the CTA raises an abort flag,
+// sets the device timeout word, drains and releases TMEM before returning.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "common.h"
+#include "format.cuh"
+
+namespace peps {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer, mma, 4 epilogue warps
+
+template <int FMT> struct FormTraits;
+template <> struct FormTraits<FMT_BF16>   { static constexpr int NP = 1, ESZ = 2, KIND = 0, AB = 1; };
+template <> struct FormTraits<FMT_FP16>   { static constexpr int NP = 1, ESZ = 2, KIND = 0, AB = 0; };
+template <> struct FormTraits<FMT_BF16X2> { static constexpr int NP = 2, ESZ = 2, KIND = 0, AB = 1; };
+template <> struct FormTraits<FMT_FP16X2> { static constexpr int NP = 2, ESZ = 2, KIND = 0, AB = 0; };
+template <> struct FormTraits<FMT_TF32>   { static constexpr int NP = 1, ESZ = 4, KIND = 1, AB = 2; };
+
+struct __align__(64) TcParams {
+  CUtensorMap mapA;        // {k, m, plane, lane}
+  CUtensorMap mapB[2][2];  // [tau][plane] {k, n}
+  StepShape sh;
+  const StepItem *items;
+  const OpDesc *ops;
+  Rec *recs;
+  DeviceStatus *st;
+  int n_items;
+  int tiles_m, tiles_n;
+  int BN;
+  int stages;
+  int tmem_cols;
+  int64_t watchdog_ns;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+struct Watch {
+  volatile int *abort;
+  DeviceStatus *st;
+  uint64_t deadline;
+  int where;
+};
+
+// Bounded wait on an mbarrier phase.  Returns false on abort or timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Watch &w) {
+  uint32_t spins = 0;
+  while (!mbar_test(bar, parity)) {
+    if ((++spins & 63) == 0) {
+      if (*w.abort) return false;
+      if (globaltimer() > w.deadline) {
+        *w.abort = 1;
+        atomicExch(&w.st->timeout, 1);
+        atomicExch(&w.st->error_info, w.where);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major swizzled tile (rows of
+// `rowb` bytes, 8-row core groups `8 * rowb` bytes apart).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t rowb) {
+  const uint64_t layout = rowb == 128 ? 2ull : 4ull;  // SWIZZLE_128B : SWIZZLE_64B
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                               // leading offset (unused, K-major swizzled)
+  d |= (uint64_t)(((8u * rowb) >> 4) & 0x3FFFu) << 32;  // stride offset between 8-row groups
+  d |= (uint64_t)1 << 46;                               // descriptor version
+  d |= layout << 61;
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel
+// ---------------------------------------------------------------------------
+template <int FMT, int ROWB>
+__global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constant__ TcParams p) {
+  using T = FormTraits<FMT>;
+  constexpr int NP = T::NP;
+  constexpr int KSTEPS = ROWB / 32;  // 32-byte MMA k-steps per stage
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem =
+      (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+
+  const int BN = p.BN;
+  const int S = p.stages;
+  const uint32_t a_bytes = BM * ROWB;
+  const uint32_t b_bytes = (uint32_t)BN * ROWB;
+  const uint32_t stage_bytes = NP * (a_bytes + b_bytes);
+  uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes);
+  uint64_t *full = bars;
+  uint64_t *empty = bars + S;
+  uint64_t *tfull = bars + 2 * S;
+  uint64_t *tempty = bars + 2 * S + 2;
+  uint64_t *done = bars + 2 * S + 4;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 5);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 32 * EPI_WARPS);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int tiles_per_item = p.tiles_m * p.tiles_n;
+  const int total = p.n_items * tiles_per_item;
+  // a row of A holds 2K real entries of ESZ bytes; one stage covers ROWB bytes
+  const int kb_count = (2 * p.sh.K * T::ESZ) / ROWB;
+  Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q};
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int item = t / tiles_per_item;
+        const int rem = t - item * tiles_per_item;
+        const int mt = rem / p.tiles_n, nt = rem - mt * p.tiles_n;
+        const StepItem &si = p.items[item];
+        const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
+        bool ok = true;
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, w)) { ok = false; break; }
+          unsigned char *st = smem + (size_t)s * stage_bytes;
+          mbar_expect_tx(&full[s], stage_bytes);
+          const int k0 = kb * (ROWB / T::ESZ);
+          for (int pl = 0; pl < NP; ++pl) {
+            tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
+            tma_load_2d(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl], &full[s], k0,
+                        nt * BN);
+          }
+        }
+        if (!ok) break;
+      }
+      // Every issued stage must have landed before the CTA may exit: wait
+      // (bounded) on the full barrier of the last S issued stages.
+      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q};
+      volatile int zero = 0;
+      w2.abort = &zero;
+      for (uint32_t j = it > (uint32_t)S ? it - S : 0u; j < it; ++j)
+        if (!mbar_wait(&full[j % S], (j / S) & 1u, w2)) break;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      uint32_t idesc = (1u << 4) | ((uint32_t)T::AB << 7) | ((uint32_t)T::AB << 10) |
+                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+      uint32_t it = 0, local = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+        const int acc = local & 1;
+        const uint32_t aph = (local >> 1) & 1u;
+        if (!mbar_wait(&tempty[acc], aph ^ 1u, w)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem_base + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < kb_count; ++kb, ++it) {
+          const int s = it % S;
+          const uint32_t ph = (it / S) & 1u;
+          if (!mbar_wait(&full[s], ph, w)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+          const uint32_t sb = sa + NP * a_bytes;
+#pragma unroll
+          for (int j = 0; j < KSTEPS; ++j) {
+            const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+            const uint64_t a0 = sdesc(sa + 32 * j, ROWB);
+            const uint64_t b0 = sdesc(sb + 32 * j, ROWB);
+            mma<T::KIND>(dt, a0, b0, idesc, first);
+            if (NP == 2) {
+              const uint64_t a1 = sdesc(sa + a_bytes + 32 * j, ROWB);
+              const uint64_t b1 = sdesc(sb + b_bytes + 32 * j, ROWB);
+              mma<T::KIND>(dt, a0, b1, idesc, 1u);
+              mma<T::KIND>(dt, a1, b0, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+      }
+      // all issued MMAs retire before TMEM is released
+      mma_commit(done);
+      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q};
+      volatile int zero = 0;
+      w2.abort = &zero;
+      mbar_wait(done, 0u, w2);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3;
+    const int row = 32 * quad + lane;
+    const int dv = p.sh.dv_out, dh = p.sh.dh_out;
+    const int64_t M = p.sh.M, P = p.sh.P, Mlo = M / P;
+    uint32_t local = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+      const int item = t / tiles_per_item;
+      const int rem = t - item * tiles_per_item;
+      const int mt = rem / p.tiles_n, nt = rem - mt * p.tiles_n;
+      const StepItem &si = p.items[item];
+      const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
+      const OpDesc &op = p.ops[si.op_base + tau];
+      const bool unit_in = si.in_rec < 0;
+      const float mu = unit_in ? 1.f : __uint_as_float(p.recs[si.in_rec].maxbits);
+      const int s_in = unit_in ? 0 : p.recs[si.in_rec].exp;
+      const int x = step_scale_exp(mu, __uint_as_float(op.beta_t_bits), p.sh.target);
+      const int acc = local & 1;
+      const uint32_t aph = (local >> 1) & 1u;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&tfull[acc], aph, w) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int64_t m = (int64_t)mt * BM + row;
+      const bool live = m < M;
+      const int64_t m_hi = live ? m / Mlo : 0, m_lo = live ? m % Mlo : 0;
+      float vmax = 0.f;
+      const uint32_t tbase = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN);
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)c, v);
+        if (live) {
+          const int nc0 = (nt * BN + c) >> 1;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int nc = nc0 + j;
+            const int hh = nc / dv, vv = nc - hh * dv;
+            const int64_t dest = ((m_lo * dh + hh) * P + m_hi) * dv + vv;
+            float2 o = make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x));
+            float2 stv = store_g<FMT>(si.D, dest, p.sh.plane, o);
+            vmax = fmaxf(vmax, max_abs2(stv));
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0) atomicMax(&p.recs[si.out_rec].maxbits, __float_as_uint(vmax));
+      if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si.out_rec].exp = s_in + op.b_t + x;
+    }
+  }
+
+  // teardown: everyone done issuing; wait for the last MMAs to retire before
+  // releasing TMEM (the epilogue consumed every committed accumulator, or the
+  // CTA aborted, in which case outstanding MMAs are drained by the commit wait).
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(p.tmem_cols));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &f, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)f;
+  });
+  return fn;
+}
+
+int esz_of(int fmt) { return fmt == FMT_TF32 ? 4 : 2; }
+int np_of(int fmt) { return (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) ? 2 : 1; }
+
+int rowb_for(int Kr, int esz) {
+  const int bytes = Kr * esz;
+  if (bytes % 128 == 0) return 128;
+  if (bytes == 64) return 64;
+  return 0;
+}
+
+}  // namespace
+
+int tc_Kr_pad(int K) { return 2 * K; }
+int tc_Nr_pad(int N) { return 2 * N; }
+
+bool tc_supports(const StepShape &sh, int fmt) {
+  if (!(fmt == FMT_BF16 || fmt == FMT_FP16 || fmt == FMT_BF16X2 || fmt == FMT_FP16X2 ||
+        fmt == FMT_TF32))
+    return false;
+  const int Kr = 2 * sh.K, Nr = 2 * sh.N;
+  if (rowb_for(Kr, esz_of(fmt)) == 0) return false;
+  if (sh.M < BM) return false;
+  if (!(Nr % 256 == 0 || (Nr % 16 == 0 && Nr <= 256))) return false;
+  if (sh.M > 0x7fffffffLL) return false;
+  return true;
+}
+
+struct TcLaunchData {
+  TcParams prm;
+  int rowb;
+};
+
+int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
+               void **out_handle) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return -1;
+  const int esz = esz_of(fmt), np = np_of(fmt);
+  const int Kr = 2 * sh.K, Nr = 2 * sh.N;
+  const int rowb = rowb_for(Kr, esz);
+  if (!rowb) return -2;
+  auto *d = new TcLaunchData();
+  std::memset(&d->prm, 0, sizeof(TcParams));
+  d->rowb = rowb;
+  const CUtensorMapDataType dt =
+      esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  const CUtensorMapSwizzle sw =
+      rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)Kr, (cuuint64_t)sh.M, (cuuint64_t)np,
+                          (cuuint64_t)a_lanes};
+    // unused dimensions (one plane, one lane) get the packed stride
+    const int64_t packed = (int64_t)Kr * esz * sh.M;
+    const int64_t plane_st = np > 1 ? plane_stride_bytes : packed;
+    const int64_t lane_st = a_lanes > 1 ? a_lane_stride : plane_st * np;
+    cuuint64_t strides[3] = {(cuuint64_t)Kr * esz, (cuuint64_t)((plane_st + 15) / 16 * 16),
+                             (cuuint64_t)((lane_st + 15) / 16 * 16)};
+    cuuint32_t box[4] = {(cuuint32_t)(rowb / esz), (cuuint32_t)BM, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(&d->prm.mapA, dt, 4, const_cast<void *>(a_base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      delete d;
+      return -3;
+    }
+  }
+  const int BN = Nr >= 256 ? 256 : Nr;
+  for (int t = 0; t < 2; ++t)
+    for (int pl = 0; pl < np; ++pl) {
+      cuuint64_t dims[2] = {(cuuint64_t)Kr, (cuuint64_t)Nr};
+      cuuint64_t strides[1] = {(cuuint64_t)Kr * esz};
+      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)BN};
+      cuuint32_t es[2] = {1, 1};
+      CUresult r = enc(&d->prm.mapB[t][pl], dt, 2, const_cast<void *>(b_ptr[t][pl]), dims,
+                       strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        delete d;
+        return -4;
+      }
+    }
+  d->prm.sh = sh;
+  d->prm.BN = BN;
+  d->prm.tiles_m = (int)((sh.M + BM - 1) / BM);
+  d->prm.tiles_n = Nr / BN;
+  int cols = 32;
+  while (cols < 2 * BN) cols *= 2;
+  d->prm.tmem_cols = cols;
+  const int stage_bytes = np * (BM + BN) * rowb;
+  const int budget = 220 * 1024 - 1024 - 256;
+  int stages = budget / stage_bytes;
+  if (stages > 8) stages = 8;
+  d->prm.stages = stages;
+  *out_handle = d;
+  return stages >= 2 ? 0 : -5;
+}
+
+void tc_release(void *h) { delete (TcLaunchData *)h; }
+
+template <int FMT, int ROWB>
+static cudaError_t launch_one(const TcParams &prm, int grid, size_t smem, cudaStream_t s) {
+  auto kern = k_contract_tc<FMT, ROWB>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  kern<<<grid, THREADS, smem, s>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
+                               const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,
+                               int64_t watchdog_ns, int sm_count, cudaStream_t s) {
+  TcLaunchData *d = (TcLaunchData *)handle;
+  TcParams prm = d->prm;
+  prm.items = d_items;
+  prm.n_items = n_items;
+  prm.ops = d_ops;
+  prm.recs = d_recs;
+  prm.st = st;
+  prm.watchdog_ns = watchdog_ns;
+  const int total = n_items * prm.tiles_m * prm.tiles_n;
+  int grid = total < sm_count ? total : sm_count;
+  if (grid < 1) return cudaSuccess;
+  const int np = np_of(prm.sh.fmt);
+  const size_t smem = (size_t)prm.stages * np * (BM + prm.BN) * d->rowb + 1024 +
+                      (2 * prm.stages + 4) * 8 + 16;
+  const bool r128 = d->rowb == 128;
+  switch (prm.sh.fmt) {
+    case FMT_BF16: return r128 ? launch_one<FMT_BF16, 128>(prm, grid, smem, s) : launch_one<FMT_BF16, 64>(prm, grid, smem, s);
+    case FMT_FP16: return r128 ? launch_one<FMT_FP16, 128>(prm, grid, smem, s) : launch_one<FMT_FP16, 64>(prm, grid, smem, s);
+    case FMT_BF16X2: return r128 ? launch_one<FMT_BF16X2, 128>(prm, grid, smem, s) : launch_one<FMT_BF16X2, 64>(prm, grid, smem, s);
+    case FMT_FP16X2: return r128 ? launch_one<FMT_FP16X2, 128>(prm, grid, smem, s) : launch_one<FMT_FP16X2, 64>(prm, grid, smem, s);
+    case FMT_TF32: return r128 ? launch_one<FMT_TF32, 128>(prm, grid, smem, s) : launch_one<FMT_TF32, 64>(prm, grid, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core operand build: the real embedding of E (scaled by 2^b_t), split
+// into the form's planes, K-major [Nr][Kr].  Also the bound beta_t.
+// ---------------------------------------------------------------------------
+template <int FMT>
+__global__ void k_build_bt(const OpBuildEntry *__restrict__ entries, OpDesc *ops) {
+  const OpBuildEntry &g = entries[blockIdx.y];
+  OpDesc &op = ops[g.op];
+  if (op.Bt[0] == nullptr) return;
+  const int K = op.K, N = op.N;
+  const int Kr = 2 * K, Nr = 2 * N;
+  const float sc = ldexpf(1.f, op.b_t);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Kr * Nr; i += gridDim.x * blockDim.x) {
+    const int nr = i / Kr, kr = i - nr * Kr;
+    const int k = kr >> 1, a = kr & 1, n = nr >> 1, b = nr & 1;
+    const float2 e = op.Ec[(int64_t)k * N + n];
+    float v;
+    if (b == 0) v = a == 0 ? e.x : -e.y;
+    else v = a == 0 ? e.y : e.x;
+    v *= sc;
+    if (FMT == FMT_TF32) {
+      ((float *)op.Bt[0])[i] = round_tf32(v);
+    } else if (FMT == FMT_BF16) {
+      ((__nv_bfloat16 *)op.Bt[0])[i] = __float2bfloat16_rn(v);
+    } else if (FMT == FMT_FP16) {
+      ((__half *)op.Bt[0])[i] = __float2half_rn(v);
+    } else if (FMT == FMT_BF16X2) {
+      __nv_bfloat16 h = __float2bfloat16_rn(v);
+      ((__nv_bfloat16 *)op.Bt[0])[i] = h;
+      ((__nv_bfloat16 *)op.Bt[1])[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    } else {
+      __half h = __float2half_rn(v);
+      ((__half *)op.Bt[0])[i] = h;
+      ((__half *)op.Bt[1])[i] = __float2half_rn(v - __half2float(h));
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // beta_t = beta_c * 2^b_t (beta_c already carries a rounding margin; the
+    // rounded planes differ from the scaled values by at most 2^-8 relative)
+    const float bc = __uint_as_float(op.beta_c_bits);
+    op.beta_t_bits = __float_as_uint(bc * sc * (1.0f + 1.0f / 128.0f));
+  }
+}
+
+cudaError_t launch_build_tc_operands(const OpBuildEntry *d_entries, int n, int max_kn,
+                                     OpDesc *d_ops, int fmt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (4 * max_kn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  dim3 grid(blocks, n);
+  switch (fmt) {
+    case FMT_TF32: k_build_bt<FMT_TF32><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    case FMT_BF16: k_build_bt<FMT_BF16><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    case FMT_FP16: k_build_bt<FMT_FP16><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    case FMT_BF16X2: k_build_bt<FMT_BF16X2><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    case FMT_FP16X2: k_build_bt<FMT_FP16X2><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace peps

@@ -1,0 +1,129 @@
+"""The C-ABI library: it loads, exports every function include/peps_gb300.h
+declares, and its host-side logic (argument checks, bond dimensions, plan
+sizes) is right.  No GPU needed: nothing here launches a kernel."""
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1905_08394_gb300 import binding as B
+from paper_1905_08394_gb300 import complexity as cx
+from rqc_inputs import make_circuit, workload
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    txt = (ROOT / "include" / "peps_gb300.h").read_text()
+    return sorted(set(re.findall(r"PEPS_API\s+[\w\s\*]*?\b(peps_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_function():
+    lib = B.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B.EXPORTED)
+    assert "sm_103a" in B.peps_version()
+
+
+def make(R, C, d, seed):
+    c = make_circuit(R, C, d, seed)
+    h = B.peps_create(R, C)
+    for g in c.gates:
+        if g.kind == "1q":
+            q = g.qubits[0]
+            B.peps_apply_1q(h, q // C, q % C, g.U)
+        else:
+            a, b = g.qubits
+            B.peps_apply_cz(h, a // C, a % C, b // C, b % C)
+    return c, h
+
+
+def test_argument_checks():
+    with pytest.raises(B.PepsError) as e:
+        B.peps_create(0, 3)
+    assert e.value.code == B.PEPS_EINVAL
+    with pytest.raises(B.PepsError):
+        B.peps_create(9, 8)  # 72 qubits > 64
+    h = B.peps_create(3, 3)
+    with pytest.raises(B.PepsError) as e:
+        B.peps_apply_cz(h, 0, 0, 1, 1)
+    assert e.value.code == B.PEPS_ENOTADJ
+    with pytest.raises(B.PepsError) as e:
+        B.peps_apply_1q(h, 3, 0, np.eye(2))
+    assert e.value.code == B.PEPS_EINVAL
+    with pytest.raises(B.PepsError):
+        B.peps_apply_1q(h, 0, 0, np.array([[np.nan, 0], [0, 1]]))
+    o, k = B.make_opts(prefix_cols=3)
+    with pytest.raises(B.PepsError):
+        B.peps_workspace_bytes(h, 8, o)   # prefix_cols must be < C
+    o, k = B.make_opts(prefix_cols=1, prefix_group=3)
+    with pytest.raises(B.PepsError):
+        B.peps_workspace_bytes(h, 8, o)   # n not a multiple of the group
+    o, k = B.make_opts(sliced_cz=[0])
+    with pytest.raises(B.PepsError):
+        B.peps_workspace_bytes(h, 8, o)   # no CZ yet
+    B.peps_destroy(h)
+
+
+@pytest.mark.parametrize("R,C,d", [(4, 4, 8), (5, 5, 16), (6, 6, 32), (7, 7, 40), (3, 5, 13),
+                                   (6, 1, 10), (1, 6, 10)])
+def test_bond_dims_follow_cz_counts(R, C, d):
+    c, h = make(R, C, d, 1)
+    for r in range(R):
+        for col in range(C):
+            q = r * C + col
+            if col + 1 < C:
+                assert B.peps_bond_dim(h, r, col, r, col + 1) == 2 ** c.cz_count(q, q + 1)
+                assert B.peps_bond_dim(h, r, col + 1, r, col) == 2 ** c.cz_count(q, q + 1)
+            if r + 1 < R:
+                assert B.peps_bond_dim(h, r, col, r + 1, col) == 2 ** c.cz_count(q, q + C)
+    assert B.peps_cz_count(h) == sum(1 for g in c.gates if g.kind == "cz")
+    B.peps_destroy(h)
+
+
+def test_plan_counts_match_cost_model():
+    c, h = make(6, 6, 32, 4)
+    o, k = B.make_opts(precision="fp32")
+    info = B.peps_plan_info_get(h, 1, o)
+    assert info["n_steps"] == 36
+    assert info["max_entries"] == 16 ** 7
+    assert info["flops_per_chain"] == 8 * cx.column_sweep_cmacs(6, 6, 16)
+    # prefix reuse: 8 groups x 64, first 3 columns shared
+    o, k = B.make_opts(precision="fp32", prefix_cols=3, prefix_group=64)
+    info = B.peps_plan_info_get(h, 512, o)
+    steps = cx.column_sweep_step_cmacs(6, 6, 16)
+    # the first 3 columns are contracted once per group, the rest per bitstring
+    assert info["flops_call"] == 8 * (8 * sum(steps[:18]) + 512 * sum(steps[18:]))
+    assert info["n_launches"] == 8 * 18 + 8 * 4 * 18   # 16 lanes per launch
+    B.peps_destroy(h)
+
+
+def test_slicing_plan():
+    c, h = make(5, 5, 16, 2)
+    ncz = B.peps_cz_count(h)
+    o, k = B.make_opts(precision="fp32", sliced_cz=[0, 1, 2])
+    info = B.peps_plan_info_get(h, 4, o)
+    assert info["n_slices"] == 8
+    o2, k2 = B.make_opts(precision="fp32")
+    full = B.peps_plan_info_get(h, 4, o2)
+    assert info["max_entries"] <= full["max_entries"]
+    o, k = B.make_opts(precision="fp32", sliced_cz=[0, 0])
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 4, o)
+    o, k = B.make_opts(precision="fp32", sliced_cz=[ncz])
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 4, o)
+    B.peps_destroy(h)
+
+
+def test_seven_by_seven_needs_slicing():
+    c, h = make(7, 7, 40, 5)
+    o, k = B.make_opts(precision="fp32")
+    with pytest.raises(B.PepsError) as e:
+        B.peps_workspace_bytes(h, 1, o)
+    assert e.value.code == B.PEPS_EUNSUPPORTED
+    B.peps_destroy(h)

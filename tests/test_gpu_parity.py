@@ -1,0 +1,267 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Metric (the paper defines none): normwise relative error over the checked
+set, ||a_gpu - a_ref||_2 / ||a_ref||_2.  Tolerances:
+  * FP32 and FP16X3 (the FP32-equivalent forms): 1e-5;
+  * the other forms: a bound from the arithmetic, 8 * u * sqrt(#site
+    absorptions), u the unit roundoff of the operand representation
+    (2^-11 for TF32 and FP16 inputs, 2^-8 for BF16, 2^-16 for the BF16 hi/lo
+    pair).  Independent per-step rounding errors add in quadrature over the
+    sweep; the factor 8 covers the input rounding of both operands and the
+    spread between amplitude sets.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import peps as op
+from oracle import statevector as sv
+from paper_1905_08394_gb300 import binding as B
+from rqc_inputs import make_circuit, uniform_bitstrings, workload
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 1e-5
+
+
+UNIT_ROUNDOFF = {"bf16": 2.0 ** -8, "tf32": 2.0 ** -11, "fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16}
+
+
+def tol_for(prec, n_steps):
+    if prec in ("fp32", "fp16x3"):
+        return SPLIT_TOL
+    return 8 * UNIT_ROUNDOFF[prec] * math.sqrt(n_steps)
+
+
+def relerr(a, ref):
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def sim_factory(cuda_device):
+    from paper_1905_08394_gb300 import Simulator
+
+    made = []
+
+    def make(circ):
+        s = Simulator(circ.R, circ.C, device=cuda_device.index or 0)
+        s.apply_circuit(circ)
+        made.append(s)
+        return s
+
+    yield make
+    for s in made:
+        s.close()
+
+
+# ---------------------------------------------------------------------------
+# 4x4 (1+8+1): all 65536 amplitudes against the state vector, norm 1
+# ---------------------------------------------------------------------------
+
+def test_4x4_d8_all_amplitudes(sim_factory):
+    circ, bits64 = workload("4x4_d8")
+    sim = sim_factory(circ)
+    allx = np.arange(1 << 16, dtype=np.uint64)
+    ref = sv.amplitudes(16, circ.gates, allx)
+    out = sim.amplitudes(allx, precision="fp32", max_lanes=64)
+    assert relerr(out, ref) < SPLIT_TOL
+    assert np.abs(out - ref).max() * 2 ** 8 < 1e-5
+    assert abs(np.sum(np.abs(out) ** 2) - 1) < 1e-5
+    out64 = sim.amplitudes(bits64, precision="fp32")
+    assert relerr(out64, ref[bits64.astype(np.int64)]) < SPLIT_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"])
+def test_4x4_d8_every_form(sim_factory, prec):
+    circ, bits = workload("4x4_d8")
+    sim = sim_factory(circ)
+    ref = sv.amplitudes(16, circ.gates, bits)
+    out = sim.amplitudes(bits, precision=prec)
+    assert relerr(out, ref) < tol_for(prec, 16)
+
+
+# ---------------------------------------------------------------------------
+# 5x5 (1+16+1): 1024 bitstrings against the PEPS oracle and the state vector
+# ---------------------------------------------------------------------------
+
+def test_5x5_d16_against_both_oracles(sim_factory):
+    circ, bits = workload("5x5_d16")
+    sim = sim_factory(circ)
+    out = sim.amplitudes(bits, precision="fp32")
+    ref3 = op.amplitudes(op.build(5, 5, circ.gates), bits)
+    assert relerr(out, ref3) < SPLIT_TOL
+    ref2 = sv.amplitudes(25, circ.gates, bits)
+    assert relerr(out, ref2) < SPLIT_TOL
+    assert relerr(ref3, ref2) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# 6x6 (1+24+1): precision study, 64 of the 4096 bitstrings vs the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def d24_ref():
+    circ, bits = workload("6x6_d24")
+    p = op.build(6, 6, circ.gates)
+    return circ, bits, op.amplitudes(p, bits[:64])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"])
+def test_6x6_d24_precision_forms(sim_factory, d24_ref, prec):
+    circ, bits, ref = d24_ref
+    sim = sim_factory(circ)
+    out = sim.amplitudes(bits, precision=prec)
+    err = relerr(out[:64], ref)
+    print(f"6x6 d24 {prec}: normwise rel.err {err:.3e}")
+    assert err < tol_for(prec, 36)
+    # Porter-Thomas: N |a|^2 over 4096 bitstrings has mean 1
+    pt = (2 ** 36) * np.abs(out) ** 2
+    assert abs(pt.mean() - 1) < 3 / math.sqrt(len(out))
+
+
+# ---------------------------------------------------------------------------
+# Ragged shapes, lanes, boundary cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R,C,d,seed", [(1, 1, 0, 1), (1, 6, 10, 2), (6, 1, 10, 3),
+                                        (2, 7, 20, 4), (4, 5, 20, 5), (3, 3, 30, 6)])
+def test_ragged_lattices(sim_factory, R, C, d, seed):
+    circ = make_circuit(R, C, d, seed)
+    n = R * C
+    bits = uniform_bitstrings(n, 37, seed)   # 37: lanes of 16 leave a ragged tail
+    ref = sv.amplitudes(n, circ.gates, bits)
+    sim = sim_factory(circ)
+    for prec in ("fp32", "fp16x3"):
+        out = sim.amplitudes(bits, precision=prec, max_lanes=16)
+        assert relerr(out, ref) < SPLIT_TOL, prec
+
+
+def test_lanes_do_not_change_results(sim_factory):
+    circ, bits = workload("5x5_d16")
+    sim = sim_factory(circ)
+    a1 = sim.amplitudes(bits[:50], precision="fp32", max_lanes=1)
+    a2 = sim.amplitudes(bits[:50], precision="fp32", max_lanes=7)
+    a3 = sim.amplitudes(bits[:50], precision="fp32", max_lanes=64)
+    assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
+
+
+def test_device_api_matches_host_api(sim_factory):
+    import torch
+
+    circ, bits = workload("5x5_d16")
+    sim = sim_factory(circ)
+    a = sim.amplitudes(bits, precision="fp32")
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = sim.amplitudes_device(d_bits, precision="fp32")
+    torch.cuda.synchronize()
+    assert np.array_equal(d_out.cpu().numpy(), a)
+
+
+def test_scale_covariance_is_exact(sim_factory):
+    from rqc_inputs import Gate
+
+    circ, bits = workload("5x5_d16")
+    k = [i for i, g in enumerate(circ.gates) if g.kind == "1q" and g.cycle == 7][0]
+    g = circ.gates[k]
+    circ2 = make_circuit(5, 5, 16, 2)
+    circ2.gates[k] = Gate("1q", g.qubits, g.name, 8.0 * g.U, g.cycle)
+    a1 = sim_factory(circ).amplitudes(bits[:64], precision="fp32")
+    a2 = sim_factory(circ2).amplitudes(bits[:64], precision="fp32")
+    assert np.array_equal(a2, 8.0 * a1)
+
+
+def test_gates_after_amplitudes_evolve_further(sim_factory):
+    from rqc_inputs import GATES
+
+    circ = make_circuit(3, 3, 8, 9)
+    bits = uniform_bitstrings(9, 20, 9)
+    sim = sim_factory(circ)
+    sim.amplitudes(bits)
+    sim.apply_1q(1, 1, GATES["SY"])
+    sim.apply_cz(1, 1, 1, 2)
+    from rqc_inputs import Gate
+    gates = list(circ.gates) + [Gate("1q", (4,), "SY", GATES["SY"]), Gate("cz", (4, 5), "CZ")]
+    ref = sv.amplitudes(9, gates, bits)
+    assert relerr(sim.amplitudes(bits), ref) < SPLIT_TOL
+
+
+def test_errors_on_bad_input(sim_factory):
+    circ, bits = workload("4x4_d8")
+    sim = sim_factory(circ)
+    with pytest.raises(B.PepsError) as e:
+        sim.amplitudes(np.array([1 << 20], dtype=np.uint64))
+    assert e.value.code == B.PEPS_EINVAL
+    # prefix groups that do not share their prefix bits are rejected on device
+    bad = uniform_bitstrings(16, 8, 3)
+    with pytest.raises(B.PepsError) as e:
+        sim.amplitudes(bad, prefix_cols=2, prefix_group=4)
+    assert e.value.code == B.PEPS_EINVAL
+    assert len(sim.amplitudes(np.zeros(0, dtype=np.uint64))) == 0
+    # the context still works after a rejected call
+    ref = sv.amplitudes(16, circ.gates, bits)
+    assert relerr(sim.amplitudes(bits), ref) < SPLIT_TOL
+
+
+def test_workspace_too_small():
+    import torch
+
+    circ, bits = workload("4x4_d8")
+    h = B.peps_create(4, 4)
+    for g in circ.gates:
+        if g.kind == "1q":
+            B.peps_apply_1q(h, g.qubits[0] // 4, g.qubits[0] % 4, g.U)
+        else:
+            a, b = g.qubits
+            B.peps_apply_cz(h, a // 4, a % 4, b // 4, b % 4)
+    o, keep = B.make_opts()
+    need = B.peps_workspace_bytes(h, len(bits), o)
+    ws = torch.empty(need - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.PepsError) as e:
+        B.peps_amplitudes(h, bits, o, ws.data_ptr(), need - 1,
+                          torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == B.PEPS_ENOMEM
+    B.peps_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# Prefix reuse and slicing
+# ---------------------------------------------------------------------------
+
+def test_prefix_reuse_equals_plain(sim_factory):
+    from rqc_inputs import prefix_group_bitstrings
+
+    circ = make_circuit(5, 5, 16, 2)
+    bits = prefix_group_bitstrings(5, 5, 2, 3, 20, 2)
+    sim = sim_factory(circ)
+    for prec in ("fp32", "fp16x3"):
+        a = sim.amplitudes(bits, precision=prec)
+        b = sim.amplitudes(bits, precision=prec, prefix_cols=2, prefix_group=20, max_lanes=8)
+        ref = op.amplitudes(op.build(5, 5, circ.gates), bits)
+        assert relerr(a, ref) < SPLIT_TOL and relerr(b, ref) < SPLIT_TOL
+
+
+def test_slices_sum_to_unsliced(sim_factory):
+    circ, bits = workload("5x5_d16")
+    bits = bits[:24]
+    sim = sim_factory(circ)
+    full = sim.amplitudes(bits, precision="fp32")
+    sliced = [3, 17, 40]
+    tot = sim.amplitudes(bits, precision="fp32", sliced_cz=sliced)
+    assert relerr(tot, full) < 1e-6
+    # each slice against the oracle's sliced PEPS
+    for sid in (0, 5):
+        one = sim.amplitudes(bits, precision="fp32", sliced_cz=sliced, slice_ids=[sid])
+        ref = op.amplitudes(op.build(5, 5, circ.gates, sliced=sliced, slice_id=sid), bits)
+        assert relerr(one, ref) < SPLIT_TOL
+
+
+def test_timing_and_launch_counters(sim_factory):
+    circ, bits = workload("5x5_d16")
+    sim = sim_factory(circ)
+    sim.amplitudes(bits[:32], precision="fp32", flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
+    st = sim.stats()
+    assert st["contract_ms"] > 0
+    assert st["launches_contract"] == 25 * 2   # 2 lane chunks of 16, 25 steps
+    assert st["launches_evolve"] > 10
+    assert st["launches_total"] >= st["launches_contract"] + st["launches_evolve"]
