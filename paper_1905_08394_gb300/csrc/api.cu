@@ -85,7 +85,7 @@ struct Plan {
   int n_steps = 0;
   int lanes = 0;
   int n_groups = 0;
-  size_t off_status = 0, off_site_ptrs = 0, off_g1 = 0, off_cz = 0, off_opdesc = 0,
+  size_t off_status = 0, off_site_ptrs = 0, off_site_lo = 0, off_g1 = 0, off_cz = 0, off_opdesc = 0,
          off_opbuild = 0, off_recs = 0, off_items = 0, off_fin = 0, off_acc = 0,
          off_bits = 0, off_out = 0, off_tables_end = 0;
   std::vector<size_t> site_buf_off[2];
@@ -478,10 +478,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   for (int b = 0; b < 2; ++b) P.site_buf_off[b].assign(NQ, 0);
   for (int q = 0; q < NQ; ++q)
     for (int b = 0; b < 2; ++b) {
-      P.site_buf_off[b][q] = off;
-      off = align_up(off + (size_t)P.site_elems[q] * sizeof(float2));
+      P.site_buf_off[b][q] = off;  // hi plane, then lo plane (float-float)
+      off = align_up(off + 2 * (size_t)P.site_elems[q] * sizeof(float2));
     }
   P.off_site_ptrs = off; off = align_up(off + NQ * sizeof(float2 *));
+  P.off_site_lo = off; off = align_up(off + NQ * sizeof(int64_t));
 
   // evolution schedule (needs only offsets)
   std::vector<Gate1Entry> g1;
@@ -519,7 +520,13 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         Gate1Entry e{};
         e.A = site_ptr(q, cur[q]);
         e.half = (int64_t)dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
-        for (int i = 0; i < 4; ++i) e.U[i] = make_float2((float)g.U[2 * i], (float)g.U[2 * i + 1]);
+        e.lo_off = P.site_elems[q];
+        for (int i = 0; i < 4; ++i) {
+          const float hr = (float)g.U[2 * i], hi_ = (float)g.U[2 * i + 1];
+          e.U_hi[i] = make_float2(hr, hi_);
+          e.U_lo[i] = make_float2((float)(g.U[2 * i] - (double)hr),
+                                  (float)(g.U[2 * i + 1] - (double)hi_));
+        }
         g1.push_back(e);
         eb.n++;
         eb.max_work = std::max(eb.max_work, e.half);
@@ -533,6 +540,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           CzEntry e{};
           e.in = site_ptr(q, cur[q]);
           e.out = site_ptr(q, cur[q] ^ 1);
+          e.lo_off = P.site_elems[q];
           for (int a = 0; a < 4; ++a) e.dims[a] = dims[4 * q + a];
           e.axis = axes[side];
           e.kind = side;  // projector on the lower q, phase on the other
@@ -776,6 +784,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         OpBuildEntry e{};
         const int fb = P.final_buf[q];
         e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
+        e.lo_off = P.site_elems[q];
         for (int a = 0; a < 4; ++a) e.dims[a] = sd[4 * q + a];
         // legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
         auto leg = [&](int a, bool horiz, int rr, int cc) {
@@ -809,6 +818,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     if (nbytes) std::memcpy(P.blob.data() + (off_abs - P.off_site_ptrs), src, nbytes);
   };
   put(P.off_site_ptrs, site_ptrs.data(), NQ * sizeof(float2 *));
+  put(P.off_site_lo, P.site_elems.data(), NQ * sizeof(int64_t));
   put(P.off_g1, g1.data(), g1.size() * sizeof(Gate1Entry));
   put(P.off_cz, cz.data(), cz.size() * sizeof(CzEntry));
   put(P.off_opdesc, ops.data(), ops.size() * sizeof(OpDesc));
@@ -892,7 +902,8 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
   const bool rebuild = (P.opts.flags & PEPS_FLAG_REBUILD) || c->built_generation != c->generation ||
                        c->built_ws != P.ws;
   if (rebuild) {
-    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs), c->n, st, s));
+    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
+                               (const int64_t *)(base + P.off_site_lo), c->n, st, s));
     S.launches_evolve++;
     for (auto &eb : P.evo) {
       if (eb.kind == 0)
@@ -905,7 +916,8 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
     c->built_ws = P.ws;
   } else {
     // status block still needs its unit scalars
-    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs), 0, st, s));
+    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
+                               (const int64_t *)(base + P.off_site_lo), 0, st, s));
     S.launches_evolve++;
   }
 

@@ -104,16 +104,21 @@ struct StepShape {
   int32_t pad_;
 };
 
-// Evolution tables.
+// Evolution tables.  Site tensors are kept as float-float pairs: a hi plane
+// and a lo plane (value = hi + lo), the lo plane `lo_off` entries after the
+// hi plane of the same buffer.
 struct Gate1Entry {  // single-qubit gate on one site tensor (in place)
   float2 *A;
   int64_t half;      // elements per sigma slice
-  float2 U[4];
+  int64_t lo_off;    // entries from the hi plane to the lo plane
+  float2 U_hi[4];    // the gate as float-float: U = U_hi + U_lo
+  float2 U_lo[4];
 };
 
 struct CzEntry {     // one half of a CZ on one site tensor (out of place)
   const float2 *in;
   float2 *out;
+  int64_t lo_off;
   int32_t dims[4];   // input l, r, u, d
   int32_t axis;      // 0..3 = l, r, u, d
   int32_t kind;      // 0 = projector P_s, 1 = phase Z^s
@@ -123,7 +128,8 @@ struct CzEntry {     // one half of a CZ on one site tensor (out of place)
 
 // Operand build entry (one site, one tau, one slice variant).
 struct OpBuildEntry {
-  const float2 *A;      // site tensor [2][l][r][u][d] (full dims)
+  const float2 *A;      // site tensor [2][l][r][u][d] (full dims), hi plane
+  int64_t lo_off;       // entries from the hi plane to the lo plane
   int32_t dims[4];      // full dims l, r, u, d
   int32_t rdims[4];     // restricted dims
   uint32_t free_mask[4];// bits of the full index that vary (per leg)
@@ -152,8 +158,8 @@ struct DeviceStatus {
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
-cudaError_t launch_init_sites(float2 *const *bufs, int n_sites, DeviceStatus *st,
-                              cudaStream_t s);
+cudaError_t launch_init_sites(float2 *const *bufs, const int64_t *lo_off, int n_sites,
+                              DeviceStatus *st, cudaStream_t s);
 cudaError_t launch_gate1(const Gate1Entry *d_entries, int n, int64_t max_half,
                          cudaStream_t s);
 cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStream_t s);

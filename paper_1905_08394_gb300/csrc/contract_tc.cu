@@ -356,19 +356,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       const int64_t m_hi = live ? m / Mlo : 0, m_lo = live ? m % Mlo : 0;
       float vmax = 0.f;
       const uint32_t tbase = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN);
+      // 8 consecutive complex columns per 16-column chunk; contiguous in the
+      // permuted destination when dim(v') is a multiple of 8 (then one row
+      // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
+      const bool vec = (dv & 7) == 0;
+      const int64_t row_base = m_lo * dh;
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(tbase + (uint32_t)c, v);
         if (live) {
           const int nc0 = (nt * BN + c) >> 1;
+          if (vec) {
+            const int hh = nc0 / dv, vv = nc0 - hh * dv;
+            const int64_t dest0 = ((row_base + hh) * P + m_hi) * dv + vv;
+            vmax = fmaxf(vmax, store8_g<FMT>(si.D, dest0, p.sh.plane, v, x));
+          } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int nc = nc0 + j;
-            const int hh = nc / dv, vv = nc - hh * dv;
-            const int64_t dest = ((m_lo * dh + hh) * P + m_hi) * dv + vv;
-            float2 o = make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x));
-            float2 stv = store_g<FMT>(si.D, dest, p.sh.plane, o);
-            vmax = fmaxf(vmax, max_abs2(stv));
+            for (int j = 0; j < 8; ++j) {
+              const int nc = nc0 + j;
+              const int hh = nc / dv, vv = nc - hh * dv;
+              const int64_t dest = ((row_base + hh) * P + m_hi) * dv + vv;
+              float2 o = make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x));
+              float2 stv = store_g<FMT>(si.D, dest, p.sh.plane, o);
+              vmax = fmaxf(vmax, max_abs2(stv));
+            }
           }
         }
       }

@@ -33,6 +33,10 @@ __device__ __forceinline__ float2 unpack_f16(uint32_t w) {
   return __half22float2(h);
 }
 
+__device__ __forceinline__ float max_abs2(float2 v) {
+  return fmaxf(fabsf(v.x), fabsf(v.y));
+}
+
 // Split v into hi + lo (both 16-bit); returns the packed words and the
 // stored value hi + lo (exact in fp32).
 template <bool BF>
@@ -101,6 +105,58 @@ __device__ __forceinline__ float2 store_g(void *base, int64_t e, int64_t plane, 
   }
 }
 
+// Store 8 consecutive complex entries dest0 .. dest0+7 (dest0 % 8 == 0) from
+// 16 floats (re, im interleaved) scaled by 2^x, with 16-byte vector stores.
+// Returns the max |stored component|.
+template <int FMT>
+__device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t plane,
+                                          const float (&v)[16], int x) {
+  float m = 0.f;
+  if (FMT == FMT_F32 || FMT == FMT_TF32) {
+    float o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float t = ldexpf(v[i], x);
+      if (FMT == FMT_TF32) t = round_tf32(t);
+      o[i] = t;
+      m = fmaxf(m, fabsf(t));
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<float2 *>(base) + dest0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      d[i] = make_uint4(__float_as_uint(o[4 * i]), __float_as_uint(o[4 * i + 1]),
+                        __float_as_uint(o[4 * i + 2]), __float_as_uint(o[4 * i + 3]));
+  } else if (FMT == FMT_BF16 || FMT == FMT_FP16) {
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float a = ldexpf(v[2 * j], x), b = ldexpf(v[2 * j + 1], x);
+      w[j] = FMT == FMT_BF16 ? pack_bf16(a, b) : pack_f16(a, b);
+      const float2 r = FMT == FMT_BF16 ? unpack_bf16(w[j]) : unpack_f16(w[j]);
+      m = fmaxf(m, max_abs2(r));
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(base) + dest0);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  } else {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float2 r = split16<FMT == FMT_BF16X2>(
+          make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x)), hi[j], lo[j]);
+      m = fmaxf(m, max_abs2(r));
+    }
+    uint32_t *p = reinterpret_cast<uint32_t *>(base);
+    uint4 *dh = reinterpret_cast<uint4 *>(p + dest0);
+    uint4 *dl = reinterpret_cast<uint4 *>(p + plane / 2 + dest0);
+    dh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    dh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    dl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    dl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+  }
+  return m;
+}
+
 // Power-of-two scale of one absorption step.  The input's stored entries are
 // bounded by mu (max of |Re|, |Im|) and the operand's column sums by beta, so
 // every output entry is bounded by mu*beta; the step multiplies its output by
@@ -117,10 +173,6 @@ __device__ __forceinline__ int step_scale_exp(float mu, float beta, int target) 
   if (x > 120) x = 120;
   if (x < -120) x = -120;
   return x;
-}
-
-__device__ __forceinline__ float max_abs2(float2 v) {
-  return fmaxf(fabsf(v.x), fabsf(v.y));
 }
 
 }  // namespace peps

@@ -37,7 +37,8 @@ __device__ __forceinline__ float2 fetch_E(const OpBuildEntry &g, int k, int n) {
   const int d = (int)g.fixed_val[3] | deposit_bits(d_, g.free_mask[3]);
   const int64_t e =
       ((((int64_t)g.tau * g.dims[0] + l) * g.dims[1] + r) * g.dims[2] + u) * g.dims[3] + d;
-  return g.A[e];
+  const float2 h = g.A[e], lo = g.A[g.lo_off + e];
+  return make_float2(h.x + lo.x, h.y + lo.y);  // float-float -> one FP32 rounding
 }
 
 // One block row per entry; threads cover Ec's K*N entries.
