@@ -194,6 +194,30 @@ PEPS_API int peps_amplitudes_device(peps_ctx *ctx, const uint64_t *d_bitstrings,
                            peps_c128 *d_out, const peps_opts *opts, void *d_workspace,
                            size_t ws_bytes, void *stream);
 
+/* Allocation-free variant of peps_amplitudes_device, for callers that cannot
+ * call cudaMalloc (code running inside another framework's memory pool, a
+ * plug-in whose host owns every device allocation, a tool that must not grow
+ * device memory after start-up).  The paper has no counterpart; this is a
+ * deployment convenience.
+ *
+ * The workspace is a static device array of 64 MiB inside this library: every
+ * GPU that loads the library holds it until the process exits.  The caller
+ * still passes the device bitstrings (n uint64) and the device output (n
+ * peps_c128), and the stream.  Calls whose workspace (peps_workspace_bytes)
+ * exceeds 64 MiB return PEPS_ENOMEM with a message; PEPS_FLAG_TIMING is
+ * rejected (PEPS_EINVAL).  The function calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call, from any context, shares the one array, which keeps the
+ * previous call's contents: each call clears what must start at zero and
+ * rebuilds the site tensors and tables it needs, so results never depend on an
+ * earlier call -- but calls that overlap on the GPU (other streams, other
+ * threads) race on the array and must be serialised by the caller. */
+PEPS_API int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrings, int64_t n,
+                                     peps_c128 *d_out, const peps_opts *opts, void *stream);
+
 /* Counters of the last amplitude call on this context. */
 PEPS_API int peps_get_stats(const peps_ctx *ctx, peps_stats *out);
 

@@ -42,7 +42,7 @@ PEPS_FLAG_NO_TC = 4
 EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_bond_dim",
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",
             "peps_get_stats", "peps_cz_count", "peps_last_error", "peps_version",
-            "peps_plan_info_get")
+            "peps_plan_info_get", "peps_amplitudes_noalloc")
 
 
 class peps_c128(ct.Structure):
@@ -111,6 +111,7 @@ def load() -> ct.CDLL:
     lib.peps_amplitudes.argtypes = [P, P, ct.c_int64, P, ct.POINTER(peps_opts), P, ct.c_size_t, P]
     lib.peps_amplitudes_device.argtypes = [P, P, ct.c_int64, P, ct.POINTER(peps_opts), P,
                                            ct.c_size_t, P]
+    lib.peps_amplitudes_noalloc.argtypes = [P, P, ct.c_int64, P, ct.POINTER(peps_opts), P]
     lib.peps_get_stats.argtypes = [P, ct.POINTER(peps_stats)]
     lib.peps_cz_count.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.peps_plan_info_get.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
@@ -208,6 +209,12 @@ def peps_amplitudes_device(h, d_bits_ptr: int, n: int, d_out_ptr: int, opts: pep
                            ws_ptr: int, ws_bytes: int, stream: int) -> None:
     _check(load().peps_amplitudes_device(h, d_bits_ptr, n, d_out_ptr, ct.byref(opts), ws_ptr,
                                          ws_bytes, stream))
+
+
+def peps_amplitudes_noalloc(h, d_bits_ptr: int, n: int, d_out_ptr: int, opts: peps_opts,
+                            stream: int) -> None:
+    """Allocation-free variant (static device scratch inside the library)."""
+    _check(load().peps_amplitudes_noalloc(h, d_bits_ptr, n, d_out_ptr, ct.byref(opts), stream))
 
 
 def peps_get_stats(h) -> dict:

@@ -16,7 +16,7 @@ BUILD = PKG / "_build"
 LIB = PKG / "libpeps_gb300.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "evolve.cu", "operands.cu", "contract_simt.cu", "contract_tc.cu",
-           "finalize.cu"]
+           "finalize.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

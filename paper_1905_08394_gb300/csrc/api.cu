@@ -1091,3 +1091,22 @@ extern "C" int peps_amplitudes(peps_ctx *c, const uint64_t *bits, int64_t n, pep
   CUDA_TRY(cudaStreamSynchronize(s));
   return PEPS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Helpers for the allocation-free entry point (noalloc.cu)
+// ---------------------------------------------------------------------------
+int peps::internal_fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+void peps::internal_forget_workspace(peps_ctx *c) {
+  c->plan.reset();
+  c->built_generation = 0;
+  c->built_ws = nullptr;
+}

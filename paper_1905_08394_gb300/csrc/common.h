@@ -191,4 +191,9 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
 int tc_Kr_pad(int K);   // real K of a tensor-core operand
 int tc_Nr_pad(int N);   // real N
 
+// For the allocation-free entry point (noalloc.cu): set the thread's error
+// text and return `code`; drop a context's cached plan and built site tensors.
+int internal_fail(int code, const char *fmt, ...);
+void internal_forget_workspace(peps_ctx *ctx);
+
 }  // namespace peps
