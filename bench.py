@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "profile"],
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "slices"],
                     help="profile: one amplitude of the workload on one lane, no timing "
-                         "(the small case for ncu captures, about 4 GiB on the device)")
+                         "(the small case for ncu captures, about 4 GiB on the device); "
+                         "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
+                         "projected full time from a seeded subset of slices")
+    ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
 
@@ -367,10 +370,66 @@ def run_profile_case(args):
     sim.close()
 
 
+def run_slices_case(args):
+    """7x7 (1+40+1), one bitstring: the slice set that keeps every running
+    tensor at <= 2^33 entries (two 64 GiB buffers), a seeded subset of slices
+    timed one by one, projected full time = seconds per slice x 2^|S|."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator, slicing
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload("7x7_d40")
+    ss = slicing.choose(circ, 2 ** 33, seed=5)
+    ids = slicing.seeded_slice_ids(len(ss.sliced_cz), args.slices + 1, seed=5)
+    sim = Simulator(circ.R, circ.C)
+    sim.apply_circuit(circ)
+    stream = torch.cuda.current_stream()
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    kw = dict(precision=args.precision, sliced_cz=ss.sliced_cz, max_lanes=1)
+    # warm-up slice (plan, tensor maps, evolution)
+    sim.amplitudes_device(d_bits, slice_ids=[ids[0]], flags=B.PEPS_FLAG_TIMING, **kw)
+    torch.cuda.synchronize()
+    times, tc = [], []
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for sid in ids[1:]:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = sim.amplitudes_device(d_bits, slice_ids=[sid],
+                                    flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        st = sim.stats()
+        tc.append((st["contract_tc_flops"], st["contract_tc_ms"], st["launches_contract_tc"]))
+    clk = clocks.stop()
+    ws_opts, ws_keep = B.make_opts(slice_ids=[0], **kw)
+    ws_gib = B.peps_workspace_bytes(sim.h, 1, ws_opts) / 2 ** 30
+    s_per = sum(times) / len(times)
+    n_sl = 2 ** len(ss.sliced_cz)
+    flops = 8 * sum(ss.step_cmacs)
+    tcf = sum(t[0] for t in tc) / max(1e-9, sum(t[1] for t in tc)) / 1e9
+    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring", "precision": args.precision,
+            "sliced_cz": len(ss.sliced_cz), "n_slices": n_sl, "max_entries": ss.max_entries,
+            "flops_per_slice": flops, "timed_slice_ids": ids[1:], "seconds_per_slice": s_per,
+            "slice_seconds": times, "projected_seconds": s_per * n_sl,
+            "projected_years": s_per * n_sl / 3.156e7, "tc_tflops": tcf,
+            "workspace_gib": ws_gib,
+            "clocks": clk, "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
+            "(odd-square partition, 92.51 TB)"}
+    print(json.dumps(line), flush=True)
+    sim.close()
+
+
 def main():
     args = parse()
     if args.case == "profile":
         run_profile_case(args)
+    elif args.case == "slices":
+        run_slices_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -113,6 +113,18 @@ typedef struct {
                                  sliced_cz[j]; NULL = all 2^n_sliced          */
     int64_t n_slice_ids;
     int64_t watchdog_ns;      /* device wait budget; 0 = 2 s                  */
+    int32_t n_fixed;          /* CZ gates whose Schmidt bit is held at one
+                                 value in every slice of the call (evaluates a
+                                 sub-slice: a slice with more bits fixed)     */
+    int32_t pad_;
+    const uint32_t *fixed_cz; /* their ordinals (disjoint from sliced_cz)     */
+    const uint8_t *fixed_s;   /* their values, 0 or 1                         */
+    int32_t tc_kchunk;        /* tensor-core tuning: bytes of K per pipeline
+                                 stage, 64 or 128 (0 = 128 where the row
+                                 length allows); smaller means more stages  */
+    int32_t tc_cluster;       /* tensor-core tuning: CTAs sharing the operand
+                                 tile by multicast, 1 or 2 (0 = 2 where the
+                                 tiles pair up)                              */
 } peps_opts;
 
 /* Counters of the last amplitude call (kernel launches are the library's own

@@ -54,7 +54,10 @@ class peps_opts(ct.Structure):
                 ("prefix_cols", ct.c_int32), ("prefix_group", ct.c_int32),
                 ("max_lanes", ct.c_int32), ("n_sliced", ct.c_int32),
                 ("sliced_cz", ct.POINTER(ct.c_uint32)), ("slice_ids", ct.POINTER(ct.c_uint64)),
-                ("n_slice_ids", ct.c_int64), ("watchdog_ns", ct.c_int64)]
+                ("n_slice_ids", ct.c_int64), ("watchdog_ns", ct.c_int64),
+                ("n_fixed", ct.c_int32), ("pad_", ct.c_int32),
+                ("fixed_cz", ct.POINTER(ct.c_uint32)), ("fixed_s", ct.POINTER(ct.c_uint8)),
+                ("tc_kchunk", ct.c_int32), ("tc_cluster", ct.c_int32)]
 
 
 class peps_stats(ct.Structure):
@@ -167,7 +170,8 @@ def peps_cz_count(h) -> int:
 
 
 def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_group: int = 0,
-              max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0):
+              max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0,
+              fixed_cz=None, fixed_s=None, tc_kchunk: int = 0, tc_cluster: int = 0):
     """peps_opts plus the arrays it points to (keep both alive)."""
     o = peps_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -187,6 +191,16 @@ def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_gro
         o.n_slice_ids = len(b)
         o.slice_ids = b.ctypes.data_as(ct.POINTER(ct.c_uint64))
     o.watchdog_ns = watchdog_ns
+    o.tc_kchunk = tc_kchunk
+    o.tc_cluster = tc_cluster
+    if fixed_cz is not None and len(fixed_cz):
+        f = np.ascontiguousarray(fixed_cz, dtype=np.uint32)
+        v = np.ascontiguousarray(fixed_s, dtype=np.uint8)
+        assert len(f) == len(v)
+        keep += [f, v]
+        o.n_fixed = len(f)
+        o.fixed_cz = f.ctypes.data_as(ct.POINTER(ct.c_uint32))
+        o.fixed_s = v.ctypes.data_as(ct.POINTER(ct.c_uint8))
     return o, keep
 
 

@@ -72,6 +72,8 @@ struct Plan {
   peps_opts opts{};
   std::vector<uint32_t> sliced;
   std::vector<uint64_t> slice_ids;
+  std::vector<uint32_t> fixed;
+  std::vector<uint8_t> fixed_s;
   const void *ws = nullptr;
   size_t ws_bytes = 0;
   const uint64_t *bits = nullptr;
@@ -293,7 +295,8 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
   return a.precision == b.precision && (a.flags & ~PEPS_FLAG_TIMING) == (b.flags & ~PEPS_FLAG_TIMING) &&
          a.prefix_cols == b.prefix_cols && a.prefix_group == b.prefix_group &&
          a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
-         a.n_slice_ids == b.n_slice_ids;
+         a.n_slice_ids == b.n_slice_ids && a.n_fixed == b.n_fixed &&
+         a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster;
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
@@ -314,6 +317,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   if (o.n_sliced < 0 || o.n_sliced > 62) return fail(PEPS_EINVAL, "n_sliced out of range");
   if (o.n_sliced > 0 && !o.sliced_cz) return fail(PEPS_EINVAL, "sliced_cz is NULL");
   if (o.n_slice_ids < 0) return fail(PEPS_EINVAL, "n_slice_ids < 0");
+  if (o.n_fixed < 0) return fail(PEPS_EINVAL, "n_fixed < 0");
+  if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster))
+    return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128 and tc_cluster 0, 1 or 2");
+  if (o.n_fixed > 0 && (!o.fixed_cz || !o.fixed_s)) return fail(PEPS_EINVAL, "fixed_cz / fixed_s is NULL");
 
   P.generation = c->generation;
   P.n = n;
@@ -344,6 +351,20 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     uint32_t &m = p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge];
     if (m & (1u << p.bit)) return fail(PEPS_EINVAL, "CZ ordinal %u sliced twice", k);
     m |= 1u << p.bit;
+  }
+  // CZ bits held at one value in every slice (sub-slices)
+  std::vector<uint32_t> fixval_h(c->ncz_h.size(), 0u), fixval_v(c->ncz_v.size(), 0u);
+  P.fixed.assign(o.fixed_cz ? o.fixed_cz : nullptr, o.fixed_cz ? o.fixed_cz + o.n_fixed : nullptr);
+  P.fixed_s.assign(o.fixed_s ? o.fixed_s : nullptr, o.fixed_s ? o.fixed_s + o.n_fixed : nullptr);
+  for (int j = 0; j < o.n_fixed; ++j) {
+    const uint32_t k = o.fixed_cz[j];
+    if (k >= czpos.size()) return fail(PEPS_EINVAL, "fixed CZ ordinal %u out of range", k);
+    if (o.fixed_s[j] > 1) return fail(PEPS_EINVAL, "fixed_s[%d] must be 0 or 1", j);
+    const CzPos &p = czpos[k];
+    uint32_t &m = p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge];
+    if (m & (1u << p.bit)) return fail(PEPS_EINVAL, "CZ ordinal %u fixed or sliced twice", k);
+    m |= 1u << p.bit;
+    if (o.fixed_s[j]) (p.horiz ? fixval_h[p.edge] : fixval_v[p.edge]) |= 1u << p.bit;
   }
   P.slice_list.clear();
   if (o.n_sliced > 0) {
@@ -749,7 +770,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         bp[t][pl] = P.bt_off[pl][2 * q + t] ? (const void *)(base + P.bt_off[pl][2 * q + t])
                                              : (const void *)(base + P.bt_off[0][2 * q + t]);
     int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
-                        (int64_t)(2 * P.gbuf_bytes), P.plane * 2, bp, &l.tc_handle);
+                        (int64_t)(2 * P.gbuf_bytes), P.plane * 2, bp, o.tc_kchunk, o.tc_cluster,
+                        &l.tc_handle);
     if (rc != 0)
       return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
   }
@@ -773,7 +795,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<OpBuildEntry> obe;
   for (int64_t sid : P.slice_list) {
     // fixed values of every edge for this slice
-    std::vector<uint32_t> val_h(c->ncz_h.size(), 0u), val_v(c->ncz_v.size(), 0u);
+    std::vector<uint32_t> val_h = fixval_h, val_v = fixval_v;
     for (int j = 0; j < o.n_sliced; ++j) {
       const CzPos &p = czpos[o.sliced_cz[j]];
       if ((sid >> j) & 1) (p.horiz ? val_h[p.edge] : val_v[p.edge]) |= 1u << p.bit;
@@ -1019,6 +1041,9 @@ static int prepare(peps_ctx *c, int64_t n, const peps_opts *opts, void *ws, size
   bool reuse = P && P->generation == c->generation && P->n == n && opts_equal(P->opts, o) &&
                P->ws == ws && P->ws_bytes == ws_bytes && P->bits == bits_dev &&
                P->host_bits == host_bits;
+  if (reuse && o.n_fixed > 0)
+    reuse = P->fixed == std::vector<uint32_t>(o.fixed_cz, o.fixed_cz + o.n_fixed) &&
+            P->fixed_s == std::vector<uint8_t>(o.fixed_s, o.fixed_s + o.n_fixed);
   if (reuse && o.n_sliced > 0) {
     reuse = P->sliced == std::vector<uint32_t>(o.sliced_cz, o.sliced_cz + o.n_sliced);
     if (reuse && o.slice_ids)

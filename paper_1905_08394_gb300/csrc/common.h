@@ -179,11 +179,12 @@ cudaError_t launch_check_groups(const uint64_t *d_bits, int64_t n, int group,
 
 // tcgen05 contraction (contract_tc.cu).
 bool tc_supports(const StepShape &sh, int fmt);
+bool tc_tuning_valid(int kchunk, int cluster);
 // Encode the launch's tensor maps (A over the lanes' input buffers, Bt for
 // tau = 0/1 and each plane); returns 0 and an opaque handle, or < 0.
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
                int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
-               void **out_handle);
+               int kchunk, int cluster, void **out_handle);
 void tc_release(void *handle);
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
                                const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,

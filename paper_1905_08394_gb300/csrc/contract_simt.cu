@@ -108,6 +108,7 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   const int s_in = unit_in ? 0 : recs[it.in_rec].exp;
   const float beta = __uint_as_float(op.beta_c_bits);
   const int x = step_scale_exp(mu, beta, sh.target);
+  const float sc = pow2f(x);
   const int64_t Mlo = M / sh.P;
   const int dv = sh.dv_out, dh = sh.dh_out;
   float vmax = 0.f;
@@ -122,9 +123,9 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
       if (n >= N) continue;
       const int hh = n / dv, vv = n % dv;
       const int64_t dest = ((m_lo * dh + hh) * sh.P + m_hi) * dv + vv;
-      float2 v = make_float2(ldexpf(acc[i][j].x, x), ldexpf(acc[i][j].y, x));
-      float2 st = store_g<FMT>(it.D, dest, sh.plane, v);
-      vmax = fmaxf(vmax, max_abs2(st));
+      const float2 v = make_float2(acc[i][j].x * sc, acc[i][j].y * sc);
+      store_g<FMT>(it.D, dest, sh.plane, v);
+      vmax = fmaxf(vmax, max_abs2(v));
     }
   }
   for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));

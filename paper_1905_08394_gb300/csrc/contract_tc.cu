@@ -36,8 +36,8 @@ namespace peps {
 namespace {
 
 constexpr int BM = 128;
-constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer, mma, 4 epilogue warps
+constexpr int EPI_WARPS = 4;                  // one per TMEM lane quadrant
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer, mma, epilogue warps
 
 template <int FMT> struct FormTraits;
 template <> struct FormTraits<FMT_BF16>   { static constexpr int NP = 1, ESZ = 2, KIND = 0, AB = 1; };
@@ -95,11 +95,29 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Set the int at the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ void st_cluster_flag(volatile int *local, uint32_t rank, int v) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote)
+               : "r"(smem_u32((const void *)local)), "r"(rank));
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(remote), "r"(v) : "memory");
+}
+
 struct Watch {
   volatile int *abort;
   DeviceStatus *st;
   uint64_t deadline;
   int where;
+  int cs;  // cluster size: an expired wait raises the abort flag in every CTA
 };
 
 // Bounded wait on an mbarrier phase.  Returns false on abort or timeout.
@@ -110,6 +128,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Watch 
       if (*w.abort) return false;
       if (globaltimer() > w.deadline) {
         *w.abort = 1;
+        if (w.cs > 1)
+          for (int r = 0; r < w.cs; ++r) st_cluster_flag(w.abort, (uint32_t)r, 1);
         atomicExch(&w.st->timeout, 1);
         atomicExch(&w.st->error_info, w.where);
         return false;
@@ -125,6 +145,16 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+// 2-D tile multicast to the CTAs of `mask`, landing at the same shared-memory
+// offset in each and signalling the mbarrier at the same offset in each.
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                               int c0, int c1, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -170,14 +200,22 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
           smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// Issue a 32-lane x 16-column TMEM load (asynchronous: the registers are
+// valid after tmem_wait()).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
       "%14,%15}, [%16];"
@@ -185,15 +223,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
         "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+// Wait for the outstanding TMEM loads; the registers of the last load are
+// in/out operands so that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // ---------------------------------------------------------------------------
 // Kernel
 // ---------------------------------------------------------------------------
-template <int FMT, int ROWB>
+// CS: CTAs per cluster.  With CS > 1 the CTAs of a cluster take CS
+// neighbouring 128-row tiles of the same lane and N block; each loads 1/CS of
+// the Bt tile and multicasts it to all of them, and each MMA warp's commit
+// frees the stage in all of them (the empty barriers count CS arrivals).
+template <int FMT, int ROWB, int CS>
 __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constant__ TcParams p) {
   using T = FormTraits<FMT>;
   constexpr int NP = T::NP;
@@ -220,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CS);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -238,23 +287,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   }
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int tiles_per_item = p.tiles_m * p.tiles_n;
+  const uint32_t rank = CS > 1 ? cluster_ctarank() : 0u;
+  const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
+  const int mgroups = (p.tiles_m + CS - 1) / CS;
+  const int tiles_per_item = mgroups * p.tiles_n;  // cluster tiles
   const int total = p.n_items * tiles_per_item;
+  const uint16_t mc_mask = (uint16_t)((1u << CS) - 1u);
+  const int bslice = BN / CS;  // Bt rows each CTA loads
   // a row of A holds 2K real entries of ESZ bytes; one stage covers ROWB bytes
   const int kb_count = (2 * p.sh.K * T::ESZ) / ROWB;
-  Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q};
+  Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q, CS};
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       uint32_t it = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      for (int t = cid; t < total; t += ncl) {
         const int item = t / tiles_per_item;
         const int rem = t - item * tiles_per_item;
-        const int mt = rem / p.tiles_n, nt = rem - mt * p.tiles_n;
+        const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
+        const int mt = mg * CS + (int)rank;  // >= tiles_m: rows past M, loaded as zeros
         const StepItem &si = p.items[item];
         const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
         bool ok = true;
@@ -267,15 +323,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           const int k0 = kb * (ROWB / T::ESZ);
           for (int pl = 0; pl < NP; ++pl) {
             tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
-            tma_load_2d(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl], &full[s], k0,
-                        nt * BN);
+            unsigned char *bdst = st + NP * a_bytes + pl * b_bytes;
+            if (CS == 1)
+              tma_load_2d(bdst, &p.mapB[tau][pl], &full[s], k0, nt * BN);
+            else
+              tma_load_2d_mc(bdst + rank * (uint32_t)bslice * ROWB, &p.mapB[tau][pl], &full[s],
+                             k0, nt * BN + (int)rank * bslice, mc_mask);
           }
         }
         if (!ok) break;
       }
       // Every issued stage must have landed before the CTA may exit: wait
       // (bounded) on the full barrier of the last S issued stages.
-      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q};
+      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
       volatile int zero = 0;
       w2.abort = &zero;
       for (uint32_t j = it > (uint32_t)S ? it - S : 0u; j < it; ++j)
@@ -287,7 +347,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       uint32_t idesc = (1u << 4) | ((uint32_t)T::AB << 7) | ((uint32_t)T::AB << 10) |
                        ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
       uint32_t it = 0, local = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+      for (int t = cid; t < total; t += ncl, ++local) {
         const int acc = local & 1;
         const uint32_t aph = (local >> 1) & 1u;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, w)) break;
@@ -314,36 +374,50 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
               mma<T::KIND>(dt, a1, b0, idesc, 1u);
             }
           }
-          mma_commit(&empty[s]);
+          if (CS == 1) mma_commit(&empty[s]);
+          else mma_commit_mc(&empty[s], mc_mask);  // frees the stage in every CTA
         }
         if (!ok) break;
         mma_commit(&tfull[acc]);
       }
       // all issued MMAs retire before TMEM is released
       mma_commit(done);
-      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q};
+      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
       volatile int zero = 0;
       w2.abort = &zero;
       mbar_wait(done, 0u, w2);
     }
   } else {
     // ---------------- epilogue ----------------
+    // Warp w drains TMEM lanes 32*(w%4) .. +31 (the rows it may access), all
+    // columns of the tile, 16 at a time; the load of chunk c+1 is in flight
+    // while chunk c is scaled, split and stored.
     const int quad = warp & 3;
     const int row = 32 * quad + lane;
     const int dv = p.sh.dv_out, dh = p.sh.dh_out;
     const int64_t M = p.sh.M, P = p.sh.P, Mlo = M / P;
     uint32_t local = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+    int cached_item = -1;
+    const OpDesc *op = nullptr;
+    const StepItem *si = nullptr;
+    float sc = 1.f;
+    int x = 0, s_in = 0;
+    for (int t = cid; t < total; t += ncl, ++local) {
       const int item = t / tiles_per_item;
       const int rem = t - item * tiles_per_item;
-      const int mt = rem / p.tiles_n, nt = rem - mt * p.tiles_n;
-      const StepItem &si = p.items[item];
-      const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
-      const OpDesc &op = p.ops[si.op_base + tau];
-      const bool unit_in = si.in_rec < 0;
-      const float mu = unit_in ? 1.f : __uint_as_float(p.recs[si.in_rec].maxbits);
-      const int s_in = unit_in ? 0 : p.recs[si.in_rec].exp;
-      const int x = step_scale_exp(mu, __uint_as_float(op.beta_t_bits), p.sh.target);
+      const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
+      const int mt = mg * CS + (int)rank;
+      if (item != cached_item) {
+        cached_item = item;
+        si = &p.items[item];
+        const int tau = (int)((*si->bits >> p.sh.q) & 1ull);
+        op = &p.ops[si->op_base + tau];
+        const bool unit_in = si->in_rec < 0;
+        const float mu = unit_in ? 1.f : __uint_as_float(p.recs[si->in_rec].maxbits);
+        s_in = unit_in ? 0 : p.recs[si->in_rec].exp;
+        x = step_scale_exp(mu, __uint_as_float(op->beta_t_bits), p.sh.target);
+        sc = pow2f(x);
+      }
       const int acc = local & 1;
       const uint32_t aph = (local >> 1) & 1u;
       int ok = 1;
@@ -361,33 +435,45 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
       const bool vec = (dv & 7) == 0;
       const int64_t row_base = m_lo * dh;
+      void *D = si->D;
+      uint32_t ra[16], rb[16];
+      tmem_ld16_issue(tbase, ra);
+      tmem_wait(ra);
       for (int c = 0; c < BN; c += 16) {
+        const bool more = c + 16 < BN;
+        if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), rb);
         float v[16];
-        tmem_ld16(tbase + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
         if (live) {
           const int nc0 = (nt * BN + c) >> 1;
           if (vec) {
             const int hh = nc0 / dv, vv = nc0 - hh * dv;
             const int64_t dest0 = ((row_base + hh) * P + m_hi) * dv + vv;
-            vmax = fmaxf(vmax, store8_g<FMT>(si.D, dest0, p.sh.plane, v, x));
+            vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int nc = nc0 + j;
               const int hh = nc / dv, vv = nc - hh * dv;
               const int64_t dest = ((row_base + hh) * P + m_hi) * dv + vv;
-              float2 o = make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x));
-              float2 stv = store_g<FMT>(si.D, dest, p.sh.plane, o);
-              vmax = fmaxf(vmax, max_abs2(stv));
+              float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
+              store_g<FMT>(D, dest, p.sh.plane, o);
+              vmax = fmaxf(vmax, max_abs2(o));
             }
           }
+        }
+        if (more) {
+          tmem_wait(rb);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) ra[i] = rb[i];
         }
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-      if (lane == 0) atomicMax(&p.recs[si.out_rec].maxbits, __float_as_uint(vmax));
-      if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si.out_rec].exp = s_in + op.b_t + x;
+      if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
+      if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si->out_rec].exp = s_in + op->b_t + x;
     }
   }
 
@@ -396,6 +482,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   // CTA aborted, in which case outstanding MMAs are drained by the commit wait).
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync();  // no CTA leaves while a peer may still signal it
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
@@ -428,16 +515,22 @@ EncodeTiledFn encode_fn() {
 int esz_of(int fmt) { return fmt == FMT_TF32 ? 4 : 2; }
 int np_of(int fmt) { return (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) ? 2 : 1; }
 
-int rowb_for(int Kr, int esz) {
+// Bytes of K per pipeline stage (the swizzle width): 128 where the row
+// length allows and nothing else is asked, else 64.
+int rowb_for(int Kr, int esz, int want = 0) {
   const int bytes = Kr * esz;
-  if (bytes % 128 == 0) return 128;
-  if (bytes == 64) return 64;
+  if (want != 64 && bytes % 128 == 0) return 128;
+  if (bytes % 64 == 0) return 64;
   return 0;
 }
 
 }  // namespace
 
 int tc_Kr_pad(int K) { return 2 * K; }
+
+bool tc_tuning_valid(int kchunk, int cluster) {
+  return (kchunk == 0 || kchunk == 64 || kchunk == 128) && (cluster >= 0 && cluster <= 2);
+}
 int tc_Nr_pad(int N) { return 2 * N; }
 
 bool tc_supports(const StepShape &sh, int fmt) {
@@ -455,16 +548,17 @@ bool tc_supports(const StepShape &sh, int fmt) {
 struct TcLaunchData {
   TcParams prm;
   int rowb;
+  int cs;  // CTAs per cluster (Bt multicast)
 };
 
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
                int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
-               void **out_handle) {
+               int kchunk, int cluster, void **out_handle) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
   const int esz = esz_of(fmt), np = np_of(fmt);
   const int Kr = 2 * sh.K, Nr = 2 * sh.N;
-  const int rowb = rowb_for(Kr, esz);
+  const int rowb = rowb_for(Kr, esz, kchunk);
   if (!rowb) return -2;
   auto *d = new TcLaunchData();
   std::memset(&d->prm, 0, sizeof(TcParams));
@@ -493,11 +587,15 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
     }
   }
   const int BN = Nr >= 256 ? 256 : Nr;
+  const int tiles_m = (int)((sh.M + BM - 1) / BM);
+  // Two CTAs per cluster share (multicast) the Bt tile when each half is a
+  // whole number of 8-row swizzle groups and the 128-row tiles pair up.
+  d->cs = ((BN / 2) % 8 == 0 && tiles_m % 2 == 0 && cluster != 1) ? 2 : 1;
   for (int t = 0; t < 2; ++t)
     for (int pl = 0; pl < np; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)Kr, (cuuint64_t)Nr};
       cuuint64_t strides[1] = {(cuuint64_t)Kr * esz};
-      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)BN};
+      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)(BN / d->cs)};
       cuuint32_t es[2] = {1, 1};
       CUresult r = enc(&d->prm.mapB[t][pl], dt, 2, const_cast<void *>(b_ptr[t][pl]), dims,
                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -525,18 +623,60 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
 
 void tc_release(void *h) { delete (TcLaunchData *)h; }
 
-template <int FMT, int ROWB>
-static cudaError_t launch_one(const TcParams &prm, int grid, size_t smem, cudaStream_t s) {
-  auto kern = k_contract_tc<FMT, ROWB>;
-  static bool attr_set = false;
-  if (!attr_set) {
+template <int FMT, int ROWB, int CS>
+static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaStream_t s) {
+  auto kern = k_contract_tc<FMT, ROWB, CS>;
+  static int max_clusters = -1;  // co-resident clusters at the largest smem size
+  if (max_clusters < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    cudaLaunchConfig_t q = {};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = CS;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3(CS * 64);
+    q.blockDim = dim3(THREADS);
+    q.dynamicSmemBytes = 227 * 1024;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, (void *)kern, &q);
+    if (e != cudaSuccess || n <= 0) {
+      (void)cudaGetLastError();
+      n = 0;
+    }
+    max_clusters = n;
   }
-  kern<<<grid, THREADS, smem, s>>>(prm);
-  return cudaGetLastError();
+  // units = SMs available; one CTA per SM, clusters of CS
+  int clusters = units / CS;
+  if (max_clusters > 0 && clusters > max_clusters) clusters = max_clusters;
+  if (clusters < 1) clusters = 1;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(clusters * CS);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, prm);
+}
+
+template <int FMT>
+static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cs, int units, size_t smem,
+                              cudaStream_t s) {
+  if (rowb == 128)
+    return cs == 2 ? launch_one<FMT, 128, 2>(prm, units, smem, s)
+                   : launch_one<FMT, 128, 1>(prm, units, smem, s);
+  return cs == 2 ? launch_one<FMT, 64, 2>(prm, units, smem, s)
+                 : launch_one<FMT, 64, 1>(prm, units, smem, s);
 }
 
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
@@ -550,19 +690,19 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
   prm.recs = d_recs;
   prm.st = st;
   prm.watchdog_ns = watchdog_ns;
-  const int total = n_items * prm.tiles_m * prm.tiles_n;
-  int grid = total < sm_count ? total : sm_count;
-  if (grid < 1) return cudaSuccess;
+  const int cs = d->cs;
+  const int cluster_tiles = n_items * ((prm.tiles_m + cs - 1) / cs) * prm.tiles_n;
+  if (cluster_tiles < 1) return cudaSuccess;
+  int units = cluster_tiles * cs < sm_count ? cluster_tiles * cs : sm_count;
   const int np = np_of(prm.sh.fmt);
   const size_t smem = (size_t)prm.stages * np * (BM + prm.BN) * d->rowb + 1024 +
-                      (2 * prm.stages + 4) * 8 + 16;
-  const bool r128 = d->rowb == 128;
+                      (2 * prm.stages + 5) * 8 + 16;
   switch (prm.sh.fmt) {
-    case FMT_BF16: return r128 ? launch_one<FMT_BF16, 128>(prm, grid, smem, s) : launch_one<FMT_BF16, 64>(prm, grid, smem, s);
-    case FMT_FP16: return r128 ? launch_one<FMT_FP16, 128>(prm, grid, smem, s) : launch_one<FMT_FP16, 64>(prm, grid, smem, s);
-    case FMT_BF16X2: return r128 ? launch_one<FMT_BF16X2, 128>(prm, grid, smem, s) : launch_one<FMT_BF16X2, 64>(prm, grid, smem, s);
-    case FMT_FP16X2: return r128 ? launch_one<FMT_FP16X2, 128>(prm, grid, smem, s) : launch_one<FMT_FP16X2, 64>(prm, grid, smem, s);
-    case FMT_TF32: return r128 ? launch_one<FMT_TF32, 128>(prm, grid, smem, s) : launch_one<FMT_TF32, 64>(prm, grid, smem, s);
+    case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cs, units, smem, s);
+    case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cs, units, smem, s);
+    case FMT_BF16X2: return launch_fmt<FMT_BF16X2>(prm, d->rowb, cs, units, smem, s);
+    case FMT_FP16X2: return launch_fmt<FMT_FP16X2>(prm, d->rowb, cs, units, smem, s);
+    case FMT_TF32: return launch_fmt<FMT_TF32>(prm, d->rowb, cs, units, smem, s);
   }
   return cudaErrorInvalidValue;
 }

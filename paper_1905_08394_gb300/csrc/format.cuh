@@ -108,18 +108,27 @@ __device__ __forceinline__ float2 store_g(void *base, int64_t e, int64_t plane, 
 // Store 8 consecutive complex entries dest0 .. dest0+7 (dest0 % 8 == 0) from
 // 16 floats (re, im interleaved) scaled by 2^x, with 16-byte vector stores.
 // Returns the max |stored component|.
+// 2^x as a float, x in [-126, 127] (exact).
+__device__ __forceinline__ float pow2f(int x) { return __int_as_float((127 + x) << 23); }
+
+// Store 8 consecutive complex entries dest0 .. dest0+7 (dest0 % 8 == 0) from
+// 16 floats (re, im interleaved) multiplied by sc (a power of two), with
+// 16-byte vector stores.  Returns the max |scaled component| before rounding
+// to the storage format (step_scale_exp allows for the rounding).
 template <int FMT>
 __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t plane,
-                                          const float (&v)[16], int x) {
+                                          const float (&v)[16], float sc) {
   float m = 0.f;
-  if (FMT == FMT_F32 || FMT == FMT_TF32) {
-    float o[16];
+  float o[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      float t = ldexpf(v[i], x);
-      if (FMT == FMT_TF32) t = round_tf32(t);
-      o[i] = t;
-      m = fmaxf(m, fabsf(t));
+  for (int i = 0; i < 16; ++i) {
+    o[i] = v[i] * sc;
+    m = fmaxf(m, fabsf(o[i]));
+  }
+  if (FMT == FMT_F32 || FMT == FMT_TF32) {
+    if (FMT == FMT_TF32) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) o[i] = round_tf32(o[i]);
     }
     uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<float2 *>(base) + dest0);
 #pragma unroll
@@ -129,12 +138,8 @@ __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t pla
   } else if (FMT == FMT_BF16 || FMT == FMT_FP16) {
     uint32_t w[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float a = ldexpf(v[2 * j], x), b = ldexpf(v[2 * j + 1], x);
-      w[j] = FMT == FMT_BF16 ? pack_bf16(a, b) : pack_f16(a, b);
-      const float2 r = FMT == FMT_BF16 ? unpack_bf16(w[j]) : unpack_f16(w[j]);
-      m = fmaxf(m, max_abs2(r));
-    }
+    for (int j = 0; j < 8; ++j)
+      w[j] = FMT == FMT_BF16 ? pack_bf16(o[2 * j], o[2 * j + 1]) : pack_f16(o[2 * j], o[2 * j + 1]);
     uint4 *d = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(base) + dest0);
     d[0] = make_uint4(w[0], w[1], w[2], w[3]);
     d[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -142,9 +147,15 @@ __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t pla
     uint32_t hi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float2 r = split16<FMT == FMT_BF16X2>(
-          make_float2(ldexpf(v[2 * j], x), ldexpf(v[2 * j + 1], x)), hi[j], lo[j]);
-      m = fmaxf(m, max_abs2(r));
+      if (FMT == FMT_BF16X2) {
+        hi[j] = pack_bf16(o[2 * j], o[2 * j + 1]);
+        const float2 h = unpack_bf16(hi[j]);
+        lo[j] = pack_bf16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
+      } else {
+        hi[j] = pack_f16(o[2 * j], o[2 * j + 1]);
+        const float2 h = unpack_f16(hi[j]);
+        lo[j] = pack_f16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
+      }
     }
     uint32_t *p = reinterpret_cast<uint32_t *>(base);
     uint4 *dh = reinterpret_cast<uint4 *>(p + dest0);
@@ -157,14 +168,16 @@ __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t pla
   return m;
 }
 
-// Power-of-two scale of one absorption step.  The input's stored entries are
-// bounded by mu (max of |Re|, |Im|) and the operand's column sums by beta, so
+// Power-of-two scale of one absorption step.  The input's entries are bounded
+// by mu (max of |Re|, |Im| of the previous step's scaled output, taken before
+// rounding to the storage format; the factor 1 + 2^-7 covers that rounding,
+// at most 2^-8 relative for bf16) and the operand's column sums by beta, so
 // every output entry is bounded by mu*beta; the step multiplies its output by
 // 2^x with x = target - ceil(log2(mu*beta)), which keeps the stored output at
 // most 2^target.  Exact (power of two), deterministic (every CTA computes the
 // same x from the same inputs).
 __device__ __forceinline__ int step_scale_exp(float mu, float beta, int target) {
-  double p = (double)mu * (double)beta;
+  double p = (double)mu * (double)beta * (1.0 + 1.0 / 128.0);
   if (!(p > 0.0) || !isfinite(p)) return 0;
   int e;
   double f = frexp(p, &e);  // p = f * 2^e, f in [0.5, 1)

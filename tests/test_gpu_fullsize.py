@@ -1,0 +1,137 @@
+"""Full-size parity: the 6x6 (1+32+1) batch in the launch configuration that
+bench.py times (512 bitstrings, 8 groups x 64 sharing columns 0-2, prefix
+reuse, 16 lanes), against FP64 oracle amplitudes of 8 of the bitstrings
+(tests/golden/oracle_6x6_d32.json, written by tests/golden/make_oracle_values.py
+from oracle/ only), and the Porter-Thomas statistics of all 512."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from rqc_inputs import workload
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(os.path.join(HERE, "golden", "oracle_6x6_d32.json")) as f:
+        g = json.load(f)
+    circ, bits = workload("6x6_d32")
+    assert [int(bits[i]) for i in g["indices"]] == g["bitstrings"]
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    return circ, bits, g["indices"], ref
+
+
+@pytest.fixture(scope="module")
+def sim(golden, cuda_device):
+    from paper_1905_08394_gb300 import Simulator
+
+    circ = golden[0]
+    s = Simulator(6, 6)
+    s.apply_circuit(circ)
+    yield s
+    s.close()
+
+
+def test_bench_configuration_fp16x3(golden, sim):
+    circ, bits, idx, ref = golden
+    out = sim.amplitudes(bits, precision="fp16x3", prefix_cols=3, prefix_group=64,
+                         max_lanes=16)
+    err = float(np.linalg.norm(out[idx] - ref) / np.linalg.norm(ref))
+    print(f"6x6 d32 fp16x3 batched: normwise rel.err {err:.3e} on 8 oracle bitstrings")
+    assert err < TOL
+    # Porter-Thomas: N |a|^2 ~ Exp(1) for a deep random circuit
+    pt = np.sort((2.0 ** 36) * np.abs(out) ** 2)
+    assert abs(pt.mean() - 1) < 3 / math.sqrt(len(pt))
+    assert abs(np.mean(pt ** 2) - 2) < 0.5
+    # Kolmogorov-Smirnov distance to Exp(1): p > 0.01 needs D < 1.63 / sqrt(n)
+    cdf = 1 - np.exp(-pt)
+    ecdf_hi = np.arange(1, len(pt) + 1) / len(pt)
+    ecdf_lo = np.arange(0, len(pt)) / len(pt)
+    D = max(np.max(ecdf_hi - cdf), np.max(cdf - ecdf_lo))
+    assert D < 1.63 / math.sqrt(len(pt))
+
+
+def test_fp32_path_on_the_oracle_groups(golden, sim):
+    circ, bits, idx, ref = golden
+    sel = np.concatenate([bits[0:64], bits[320:384]])
+    out = sim.amplitudes(sel, precision="fp32", prefix_cols=3, prefix_group=64, max_lanes=16)
+    pos = [0, 21, 42, 63, 64, 85, 106, 127]
+    err = float(np.linalg.norm(out[pos] - ref) / np.linalg.norm(ref))
+    print(f"6x6 d32 fp32 batched: normwise rel.err {err:.3e} on 8 oracle bitstrings")
+    assert err < TOL
+
+
+# ---------------------------------------------------------------------------
+# 7x7 lattice
+# ---------------------------------------------------------------------------
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def sim7_d24(cuda_device):
+    from paper_1905_08394_gb300 import Simulator
+    from rqc_inputs import make_circuit
+
+    s = Simulator(7, 7)
+    s.apply_circuit(make_circuit(7, 7, 24, 5))
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_7x7_d24_amplitudes(sim7_d24, prec):
+    g = _golden("oracle_7x7_d24.json")
+    bits = np.array(g["bitstrings"], dtype=np.uint64)
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    out = sim7_d24.amplitudes(bits, precision=prec)
+    err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+    print(f"7x7 d24 {prec}: normwise rel.err {err:.3e}")
+    assert err < TOL
+
+
+def test_7x7_d24_slices_sum_to_the_amplitude(sim7_d24):
+    from paper_1905_08394_gb300 import slicing
+    from rqc_inputs import make_circuit
+
+    g = _golden("oracle_7x7_d24.json")
+    bits = np.array(g["bitstrings"], dtype=np.uint64)
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    ss = slicing.choose(make_circuit(7, 7, 24, 5), 2 ** 23, seed=5)
+    assert 2 <= len(ss.sliced_cz) <= 10
+    tot = sim7_d24.amplitudes(bits, precision="fp16x3", sliced_cz=ss.sliced_cz)
+    err = float(np.linalg.norm(tot - ref) / np.linalg.norm(ref))
+    print(f"7x7 d24 sum of {ss.n_slices} slices: normwise rel.err {err:.3e}")
+    assert err < TOL
+
+
+def test_7x7_d40_subslices(cuda_device):
+    """The 7x7 (1+40+1) circuit with 84 CZ bits held (sub-slices of the slices
+    the benchmark times): the oracle's values vanish (see the generating
+    script), and so must the GPU's, to within the error the forms allow at
+    the amplitude scale 2^-24.5."""
+    from paper_1905_08394_gb300 import Simulator
+
+    g = _golden("oracle_7x7_d40.json")
+    circ, bits = workload("7x7_d40")
+    assert int(bits[0]) == g["bitstring"]
+    s = Simulator(7, 7)
+    s.apply_circuit(circ)
+    scale = 2.0 ** -24.5
+    for sub in g["subslices"]:
+        ref = complex(*sub["amplitude"])
+        for prec in ("fp32", "fp16x3"):
+            a = s.amplitudes(bits[:1], precision=prec, fixed_cz=g["fixed_cz"],
+                             fixed_s=sub["fixed_s"])[0]
+            print(f"7x7 d40 sub-slice {prec}: gpu {a:.3e} oracle {ref:.3e}")
+            assert abs(a - ref) < TOL * scale
+    s.close()
