@@ -217,10 +217,15 @@ def run_mine(args):
     from paper_1905_08394_gb300 import binding as B
     from rqc_inputs import workload
 
+    from paper_1905_08394_gb300 import distributed as D
+
     world, rank, local, pg = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    circ, bits = workload(WORKLOAD)
+    circ, _ = workload(WORKLOAD)
+    # weak scaling: every rank contracts its own 8 prefix groups of 64 (rank 0
+    # of a one-rank job gets exactly the single-GPU batch); no data exchange
+    bits = D.rank_prefix_batch(6, 6, 3, 8, 64, 4, world, rank)
     n = len(bits)
     sim = Simulator(circ.R, circ.C, device=local)
     sim.apply_circuit(circ)
@@ -262,9 +267,7 @@ def run_mine(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = D.max_over_ranks(ms, pg, device=dev)
     ms_per_step = ms / args.steps
     value = world * n * args.steps / (ms / 1e3)
 

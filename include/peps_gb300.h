@@ -89,7 +89,11 @@ typedef enum {
 enum {
     PEPS_FLAG_REBUILD = 1,  /* re-run the circuit evolution even if unchanged */
     PEPS_FLAG_TIMING = 2,   /* time every contraction launch with CUDA events */
-    PEPS_FLAG_NO_TC = 4     /* run every absorption on the CUDA-core kernel   */
+    PEPS_FLAG_NO_TC = 4,    /* run every absorption on the CUDA-core kernel   */
+    PEPS_FLAG_GRAPH = 8     /* capture the call's launch sequence (evolution
+                               included) into a CUDA graph on the first call
+                               and replay it on later calls with the same
+                               plan; ignored together with PEPS_FLAG_TIMING */
 };
 
 /* Options of an amplitude call.  All-zero means: FP32_SIMT, no prefix reuse,

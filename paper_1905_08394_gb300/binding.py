@@ -38,6 +38,7 @@ PRECISIONS = {"fp32": PEPS_FP32_SIMT, "tf32": PEPS_TF32, "bf16": PEPS_BF16,
 PEPS_FLAG_REBUILD = 1
 PEPS_FLAG_TIMING = 2
 PEPS_FLAG_NO_TC = 4
+PEPS_FLAG_GRAPH = 8
 
 EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_bond_dim",
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",

@@ -121,7 +121,11 @@ struct Plan {
   // host copy of the tables blob (uploaded once)
   std::vector<unsigned char> blob;
 
+  // CUDA graph of the whole launch sequence (PEPS_FLAG_GRAPH)
+  cudaGraphExec_t graph_exec = nullptr;
+
   ~Plan() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
     for (auto &l : launches)
       if (l.tc_handle) tc_release(l.tc_handle);
   }
@@ -904,45 +908,61 @@ static int ensure_events(peps_ctx *c, size_t n) {
   return PEPS_OK;
 }
 
-static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s) {
+// Launch counters of one graph replay (the same sequence as an eager call
+// with the evolution included).
+static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
+  S.launches_evolve = 1 + (int64_t)P.evo.size();
+  if (P.opts.prefix_cols > 0 && P.n > 0) S.launches_finalize++;
+  bool any_tc = false;
+  for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
+  const int64_t ns = (int64_t)P.slice_list.size();
+  S.launches_operand = ns * (2 + (any_tc ? 1 : 0));
+  for (auto &l : P.launches) {
+    if (l.kind == 0) {
+      S.launches_contract += ns;
+      S.contract_flops += ns * l.flops;
+      S.contract_bytes += ns * l.bytes;
+      if (l.tc) {
+        S.launches_contract_tc += ns;
+        S.contract_tc_flops += ns * l.flops;
+        S.contract_tc_bytes += ns * l.bytes;
+      }
+    } else {
+      S.launches_finalize += ns;
+    }
+  }
+  S.launches_total = S.launches_evolve + S.launches_operand + S.launches_contract + S.launches_finalize;
+  return PEPS_OK;
+}
+
+// Enqueue the whole call on `s`: status reset, evolution (if `rebuild`), the
+// prefix-group check, and per slice the operand build, the absorption steps
+// and the final reduction.  With `timing`, CUDA events bracket every
+// contraction launch (their count goes to *n_timed, their kind to timed_tc).
+static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s,
+                            bool rebuild, bool timing, peps_stats &S, size_t *n_timed,
+                            std::vector<char> *timed_tc) {
   char *base = (char *)P.ws;
   DeviceStatus *st = (DeviceStatus *)(base + P.off_status);
-  const bool timing = (P.opts.flags & PEPS_FLAG_TIMING) != 0;
-  peps_stats S{};
-  S.n_steps = P.n_steps;
-  S.n_lanes = P.lanes;
-
-  if (c->sm_count == 0) {
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  }
   const int64_t wd_ns = P.opts.watchdog_ns > 0 ? P.opts.watchdog_ns : 2000000000LL;
-
-  // status + evolution
   CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
-  const bool rebuild = (P.opts.flags & PEPS_FLAG_REBUILD) || c->built_generation != c->generation ||
-                       c->built_ws != P.ws;
   if (rebuild) {
     CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
                                (const int64_t *)(base + P.off_site_lo), c->n, st, s));
     S.launches_evolve++;
     for (auto &eb : P.evo) {
       if (eb.kind == 0)
-        CUDA_TRY(launch_gate1((const Gate1Entry *)(base + P.off_g1) + eb.off, eb.n, eb.max_work / 1, s));
+        CUDA_TRY(launch_gate1((const Gate1Entry *)(base + P.off_g1) + eb.off, eb.n, eb.max_work, s));
       else
         CUDA_TRY(launch_cz((const CzEntry *)(base + P.off_cz) + eb.off, eb.n, eb.max_work, s));
       S.launches_evolve++;
     }
-    c->built_generation = c->generation;
-    c->built_ws = P.ws;
   } else {
     // status block still needs its unit scalars
     CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
                                (const int64_t *)(base + P.off_site_lo), 0, st, s));
     S.launches_evolve++;
   }
-
   if (P.opts.prefix_cols > 0 && P.n > 0) {
     uint64_t mask = 0;
     for (int q = 0; q < c->n; ++q)
@@ -950,7 +970,6 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
     CUDA_TRY(launch_check_groups(d_bits_in, P.n, P.opts.prefix_group, mask, st, s));
     S.launches_finalize++;
   }
-
   double2 *acc = (double2 *)(base + P.off_acc);
   CUDA_TRY(cudaMemsetAsync(acc, 0, std::max<int64_t>(P.n, 1) * sizeof(double2), s));
   Rec *recs = (Rec *)(base + P.off_recs);
@@ -958,30 +977,20 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
   const StepItem *items = (const StepItem *)(base + P.off_items);
   const FinalEntry *fins = (const FinalEntry *)(base + P.off_fin);
   const OpBuildEntry *obe = (const OpBuildEntry *)(base + P.off_opbuild);
-
-  size_t n_timed = 0;
-  if (timing) {
-    size_t nl = 0;
-    for (auto &l : P.launches) nl += l.kind == 0;
-    int rc = ensure_events(c, 2 * nl * P.slice_list.size());
-    if (rc) return rc;
-  }
-  std::vector<char> timed_tc;
-
+  bool any_tc = false;
+  for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   for (size_t si = 0; si < P.slice_list.size(); ++si) {
     if (P.n_recs > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, P.n_recs * sizeof(Rec), s));
     const OpBuildEntry *e = obe + si * P.n_opbuild_per_slice;
     CUDA_TRY(launch_build_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, s));
     S.launches_operand += 2;
-    bool any_tc = false;
-    for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
     if (any_tc) {
       CUDA_TRY(launch_build_tc_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, P.fmt, s));
       S.launches_operand++;
     }
     for (auto &l : P.launches) {
       if (l.kind == 0) {
-        if (timing) CUDA_TRY(cudaEventRecord(c->ev[2 * n_timed], s));
+        if (timing) CUDA_TRY(cudaEventRecord(c->ev[2 * *n_timed], s));
         if (l.tc) {
           CUDA_TRY(launch_contract_tc(l.tc_handle, items + l.items_off, l.n_items, ops, recs,
                                       st, wd_ns, c->sm_count, s));
@@ -992,9 +1001,9 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
           CUDA_TRY(launch_contract_simt(l.shape, items + l.items_off, l.n_items, ops, recs, st, s));
         }
         if (timing) {
-          CUDA_TRY(cudaEventRecord(c->ev[2 * n_timed + 1], s));
-          timed_tc.push_back(l.tc);
-          n_timed++;
+          CUDA_TRY(cudaEventRecord(c->ev[2 * *n_timed + 1], s));
+          timed_tc->push_back(l.tc);
+          ++*n_timed;
         }
         S.launches_contract++;
         S.contract_flops += l.flops;
@@ -1006,6 +1015,67 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
     }
   }
   S.launches_total = S.launches_evolve + S.launches_operand + S.launches_contract + S.launches_finalize;
+  return PEPS_OK;
+}
+
+static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s) {
+  const bool timing = (P.opts.flags & PEPS_FLAG_TIMING) != 0;
+  const bool graph = (P.opts.flags & PEPS_FLAG_GRAPH) != 0 && !timing;
+  peps_stats S{};
+  S.n_steps = P.n_steps;
+  S.n_lanes = P.lanes;
+
+  if (c->sm_count == 0) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+
+  if (graph) {
+    // the graph always contains the evolution, so a replay never depends on
+    // what an earlier call left in the site tensors
+    if (!P.graph_exec) {
+      for (auto &l : P.launches)
+        if (l.kind == 0 && l.tc) CUDA_TRY(tc_warm(l.tc_handle));
+      CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      peps_stats S2{};
+      int rc = enqueue_sequence(c, P, d_bits_in, s, true, false, S2, nullptr, nullptr);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      CUDA_TRY(e);
+      e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      CUDA_TRY(e);
+    }
+    CUDA_TRY(cudaGraphLaunch(P.graph_exec, s));
+    int rc = enqueue_sequence_stats_only(P, S);
+    if (rc) return rc;
+    c->built_generation = c->generation;
+    c->built_ws = P.ws;
+    c->stats = S;
+    return PEPS_OK;
+  }
+
+  const bool rebuild = (P.opts.flags & PEPS_FLAG_REBUILD) || c->built_generation != c->generation ||
+                       c->built_ws != P.ws;
+  size_t n_timed = 0;
+  std::vector<char> timed_tc;
+  if (timing) {
+    size_t nl = 0;
+    for (auto &l : P.launches) nl += l.kind == 0;
+    int rc = ensure_events(c, 2 * nl * P.slice_list.size());
+    if (rc) return rc;
+  }
+  int rc = enqueue_sequence(c, P, d_bits_in, s, rebuild, timing, S, &n_timed, &timed_tc);
+  if (rc) return rc;
+  if (rebuild) {
+    c->built_generation = c->generation;
+    c->built_ws = P.ws;
+  }
   if (timing) {
     CUDA_TRY(cudaStreamSynchronize(s));
     for (size_t i = 0; i < n_timed; ++i) {

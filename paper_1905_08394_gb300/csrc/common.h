@@ -186,6 +186,9 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
                int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
                int kchunk, int cluster, void **out_handle);
 void tc_release(void *handle);
+// One-time set-up of the kernel a handle launches (attributes, occupancy);
+// done before a stream capture so that no such call happens inside it.
+cudaError_t tc_warm(void *handle);
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
                                const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,
                                int64_t watchdog_ns, int sm_count, cudaStream_t s);

@@ -13,15 +13,24 @@
 // planes of A and Bt, three MMAs hi*hi + hi*lo + lo*hi accumulated in FP32),
 // TF32 (kind::tf32, one MMA).
 //
-// Structure: persistent CTAs (one per SM) walk tiles (lane, 128-row M block,
-// N block of up to 256 real columns).  Warp 0 issues TMA loads of A and Bt
-// tiles (128-byte or 64-byte swizzle) into a ring of shared-memory stages,
-// warp 1 issues tcgen05.mma into one of two TMEM accumulators, warps 2..5
-// drain the other accumulator with tcgen05.ld, apply the step's power-of-two
-// scale, split into the storage format and store permuted (the slowest
-// untouched leg moves next to v'), and record the max |entry|.  Every wait is
-// bounded by a %globaltimer budget; on expiry the CTA raises an abort flag,
-// sets the device timeout word, drains and releases TMEM before returning.
+// Structure: persistent CTAs (one per SM) walk tiles (lane, M block, N block
+// of up to 256 real columns).  Warp 0 issues TMA loads of A and Bt tiles
+// (128-byte or 64-byte swizzle) into a ring of shared-memory stages, warp 1
+// issues tcgen05.mma into one of two TMEM accumulators, warps 2..5 drain the
+// other accumulator with tcgen05.ld, apply the step's power-of-two scale,
+// split into the storage format and store permuted (the slowest untouched leg
+// moves next to v'), and record the max |entry|.
+//
+// CG = 2 (the default where the row tiles pair up): a cluster of two CTAs on
+// neighbouring SMs computes a 256-row tile with the 2-SM UMMA
+// (tcgen05.mma.cta_group::2, M = 256).  Each CTA loads its own 128 rows of A
+// and only half of the Bt tile; the even CTA issues the MMAs for both, and
+// the TMA completions of both CTAs arrive on its barriers.  Per SM this
+// halves the Bt bytes ingested per multiply-add, which is what bounds the
+// single-CTA form (the MMA warp waits on operand arrival, not on the
+// epilogue).  Every wait is bounded by a %globaltimer budget; on expiry the
+// CTA raises the abort flag in both CTAs, sets the device timeout word,
+// drains and releases TMEM before returning.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -147,14 +156,45 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-// 2-D tile multicast to the CTAs of `mask`, landing at the same shared-memory
-// offset in each and signalling the mbarrier at the same offset in each.
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                               int c0, int c1, uint16_t mask) {
+// Prefetch a 4-D tile of the tensor into L2 (no shared memory, no barrier).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap *map, int c0, int c1, int c2,
+                                                int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+      "cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+          (uint64_t)map),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// Shared::cluster address of the same shared-memory offset in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(local)), "r"(rank));
+  return r;
+}
+// Arrive on an mbarrier given by its shared::cluster address (any CTA).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   bar_cluster_addr)
+               : "memory");
+}
+// TMA loads of a CTA pair: the data lands in this CTA's shared memory and the
+// completion is counted on the mbarrier at `bar_cluster_addr` (the even CTA's).
+__device__ __forceinline__ void tma_load_4d_cg2(void *dst, const CUtensorMap *map,
+                                                uint32_t bar_cluster_addr, int c0, int c1, int c2,
+                                                int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar_cluster_addr)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_cg2(void *dst, const CUtensorMap *map,
+                                                uint32_t bar_cluster_addr, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar_cluster_addr)
       : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -179,9 +219,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t rowb) {
   return d;
 }
 
-template <int KIND>
+template <int KIND, int CG>
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
+  if (CG == 2) {
+    if (KIND == 0)
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+          "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+          "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    return;
+  }
   if (KIND == 0) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -200,11 +253,12 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
           smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+// Commit of the pair's MMAs: arrives on the mbarrier at this offset in both CTAs.
+__device__ __forceinline__ void mma_commit_cg2(uint64_t *bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
       " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
+      "h"((uint16_t)3)
       : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -238,11 +292,9 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
 // ---------------------------------------------------------------------------
 // Kernel
 // ---------------------------------------------------------------------------
-// CS: CTAs per cluster.  With CS > 1 the CTAs of a cluster take CS
-// neighbouring 128-row tiles of the same lane and N block; each loads 1/CS of
-// the Bt tile and multicasts it to all of them, and each MMA warp's commit
-// frees the stage in all of them (the empty barriers count CS arrivals).
-template <int FMT, int ROWB, int CS>
+// CG: CTAs per MMA.  CG = 1: one CTA per 128-row tile.  CG = 2: a cluster of
+// two CTAs per 256-row tile (2-SM UMMA), see the file comment.
+template <int FMT, int ROWB, int CG>
 __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constant__ TcParams p) {
   using T = FormTraits<FMT>;
   constexpr int NP = T::NP;
@@ -251,11 +303,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   unsigned char *smem =
       (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
 
-  const int BN = p.BN;
+  const int BN = p.BN;              // real output columns per tile (MMA N)
+  const int BNL = BN / CG;          // Bt rows held by this CTA
   const int S = p.stages;
   const uint32_t a_bytes = BM * ROWB;
-  const uint32_t b_bytes = (uint32_t)BN * ROWB;
-  const uint32_t stage_bytes = NP * (a_bytes + b_bytes);
+  const uint32_t b_bytes = (uint32_t)BNL * ROWB;
+  const uint32_t stage_bytes = NP * (a_bytes + b_bytes);  // this CTA's share
   uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes);
   uint64_t *full = bars;
   uint64_t *empty = bars + S;
@@ -266,86 +319,120 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = CG > 1 ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CS);
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 32 * EPI_WARPS);
+      // the pair's epilogue warps (one elected lane each) release an accumulator
+      mbar_init(&tempty[a], CG == 2 ? 2 * EPI_WARPS : 32 * EPI_WARPS);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(p.tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if (CG == 2) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(p.tmem_cols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(p.tmem_cols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync();  // every CTA's barriers exist before any multicast
+  if (CG > 1) cluster_sync();  // both CTAs' barriers exist before any remote signal
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const uint32_t rank = CS > 1 ? cluster_ctarank() : 0u;
-  const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-  const int mgroups = (p.tiles_m + CS - 1) / CS;
-  const int tiles_per_item = mgroups * p.tiles_n;  // cluster tiles
+  const int cid = blockIdx.x / CG, ncl = gridDim.x / CG;
+  const int mgroups = p.tiles_m / CG;               // CG == 2 only when tiles_m is even
+  const int tiles_per_item = mgroups * p.tiles_n;  // tiles of the pair
   const int total = p.n_items * tiles_per_item;
-  const uint16_t mc_mask = (uint16_t)((1u << CS) - 1u);
-  const int bslice = BN / CS;  // Bt rows each CTA loads
   // a row of A holds 2K real entries of ESZ bytes; one stage covers ROWB bytes
   const int kb_count = (2 * p.sh.K * T::ESZ) / ROWB;
-  Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q, CS};
+  Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q, CG};
+  // the even CTA's barriers, as cluster addresses
+  const uint32_t full0 = CG == 2 ? cluster_addr(full, 0) : 0u;
+  const uint32_t tempty0 = CG == 2 ? cluster_addr(tempty, 0) : 0u;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
       uint32_t it = 0;
       for (int t = cid; t < total; t += ncl) {
         const int item = t / tiles_per_item;
         const int rem = t - item * tiles_per_item;
         const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
-        const int mt = mg * CS + (int)rank;  // >= tiles_m: rows past M, loaded as zeros
+        const int mt = mg * CG + (int)rank;
         const StepItem &si = p.items[item];
         const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
+        // The next tile's rows of A come from DRAM: start pulling them into L2
+        // now, a whole tile ahead, so that its TMA loads find them in L2.
+        {
+          const int tn = t + ncl;
+          if (tn < total) {
+            const int item2 = tn / tiles_per_item;
+            const int rem2 = tn - item2 * tiles_per_item;
+            const int mt2 = (rem2 / p.tiles_n) * CG + (int)rank;
+            const int lane2 = p.items[item2].a_lane;
+            for (int kb = 0; kb < kb_count; ++kb)
+              for (int pl = 0; pl < NP; ++pl)
+                tma_prefetch_4d(&p.mapA, kb * (ROWB / T::ESZ), mt2 * BM, pl, lane2);
+          }
+        }
         bool ok = true;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, w)) { ok = false; break; }
           unsigned char *st = smem + (size_t)s * stage_bytes;
-          mbar_expect_tx(&full[s], stage_bytes);
           const int k0 = kb * (ROWB / T::ESZ);
-          for (int pl = 0; pl < NP; ++pl) {
-            tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
-            unsigned char *bdst = st + NP * a_bytes + pl * b_bytes;
-            if (CS == 1)
-              tma_load_2d(bdst, &p.mapB[tau][pl], &full[s], k0, nt * BN);
-            else
-              tma_load_2d_mc(bdst + rank * (uint32_t)bslice * ROWB, &p.mapB[tau][pl], &full[s],
-                             k0, nt * BN + (int)rank * bslice, mc_mask);
+          if (CG == 1) {
+            mbar_expect_tx(&full[s], stage_bytes);
+            for (int pl = 0; pl < NP; ++pl) {
+              tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
+              tma_load_2d(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl], &full[s], k0,
+                          nt * BN);
+            }
+          } else {
+            // the even CTA's full barrier counts both CTAs' bytes
+            if (leader) mbar_expect_tx(&full[s], 2 * stage_bytes);
+            for (int pl = 0; pl < NP; ++pl) {
+              tma_load_4d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0, mt * BM,
+                              pl, si.a_lane);
+              tma_load_2d_cg2(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl],
+                              full0 + (uint32_t)s * 8u, k0, nt * BN + (int)rank * BNL);
+            }
           }
         }
         if (!ok) break;
       }
-      // Every issued stage must have landed before the CTA may exit: wait
-      // (bounded) on the full barrier of the last S issued stages.
-      Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
-      volatile int zero = 0;
-      w2.abort = &zero;
-      for (uint32_t j = it > (uint32_t)S ? it - S : 0u; j < it; ++j)
-        if (!mbar_wait(&full[j % S], (j / S) & 1u, w2)) break;
+      // Every issued stage must have landed before the pair may exit: the
+      // even CTA waits (bounded) on the full barriers of the last S stages,
+      // which count the loads of both CTAs.
+      if (leader) {
+        Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
+        volatile int zero = 0;
+        w2.abort = &zero;
+        for (uint32_t j = it > (uint32_t)S ? it - S : 0u; j < it; ++j)
+          if (!mbar_wait(&full[j % S], (j / S) & 1u, w2)) break;
+      }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      uint32_t idesc = (1u << 4) | ((uint32_t)T::AB << 7) | ((uint32_t)T::AB << 10) |
-                       ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    // ---------------- MMA issuer (the even CTA) ----------------
+    if (lane == 0 && leader) {
+      const uint32_t idesc = (1u << 4) | ((uint32_t)T::AB << 7) | ((uint32_t)T::AB << 10) |
+                             ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((BM * CG) >> 4) << 24);
       uint32_t it = 0, local = 0;
       for (int t = cid; t < total; t += ncl, ++local) {
         const int acc = local & 1;
@@ -366,29 +453,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
             const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
             const uint64_t a0 = sdesc(sa + 32 * j, ROWB);
             const uint64_t b0 = sdesc(sb + 32 * j, ROWB);
-            mma<T::KIND>(dt, a0, b0, idesc, first);
+            mma<T::KIND, CG>(dt, a0, b0, idesc, first);
             if (NP == 2) {
               const uint64_t a1 = sdesc(sa + a_bytes + 32 * j, ROWB);
               const uint64_t b1 = sdesc(sb + b_bytes + 32 * j, ROWB);
-              mma<T::KIND>(dt, a0, b1, idesc, 1u);
-              mma<T::KIND>(dt, a1, b0, idesc, 1u);
+              mma<T::KIND, CG>(dt, a0, b1, idesc, 1u);
+              mma<T::KIND, CG>(dt, a1, b0, idesc, 1u);
             }
           }
-          if (CS == 1) mma_commit(&empty[s]);
-          else mma_commit_mc(&empty[s], mc_mask);  // frees the stage in every CTA
+          if (CG == 1) mma_commit(&empty[s]);
+          else mma_commit_cg2(&empty[s]);  // frees the stage in both CTAs
         }
         if (!ok) break;
-        mma_commit(&tfull[acc]);
+        if (CG == 1) mma_commit(&tfull[acc]);
+        else mma_commit_cg2(&tfull[acc]);   // both CTAs' epilogues may drain
       }
       // all issued MMAs retire before TMEM is released
-      mma_commit(done);
+      if (CG == 1) mma_commit(done);
+      else mma_commit_cg2(done);
       Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
       volatile int zero = 0;
       w2.abort = &zero;
       mbar_wait(done, 0u, w2);
     }
   } else {
-    // ---------------- epilogue ----------------
+    // ---------------- epilogue (both CTAs) ----------------
     // Warp w drains TMEM lanes 32*(w%4) .. +31 (the rows it may access), all
     // columns of the tile, 16 at a time; the load of chunk c+1 is in flight
     // while chunk c is scaled, split and stored.
@@ -406,7 +495,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       const int item = t / tiles_per_item;
       const int rem = t - item * tiles_per_item;
       const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
-      const int mt = mg * CS + (int)rank;
+      const int mt = mg * CG + (int)rank;
       if (item != cached_item) {
         cached_item = item;
         si = &p.items[item];
@@ -470,23 +559,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         }
       }
       tc_fence_before();
-      mbar_arrive(&tempty[acc]);
+      if (CG == 1) {
+        mbar_arrive(&tempty[acc]);
+      } else {
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)acc * 8u);
+      }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
       if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si->out_rec].exp = s_in + op->b_t + x;
     }
   }
 
-  // teardown: everyone done issuing; wait for the last MMAs to retire before
-  // releasing TMEM (the epilogue consumed every committed accumulator, or the
-  // CTA aborted, in which case outstanding MMAs are drained by the commit wait).
+  // teardown: everyone done issuing; the last MMAs have retired (done
+  // barrier) and the last loads have landed (full barriers) before the pair
+  // releases TMEM and leaves.
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync();  // no CTA leaves while a peer may still signal it
+  if (CG > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(p.tmem_cols));
+    if (CG == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(p.tmem_cols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(p.tmem_cols));
   }
 }
 
@@ -548,7 +646,7 @@ bool tc_supports(const StepShape &sh, int fmt) {
 struct TcLaunchData {
   TcParams prm;
   int rowb;
-  int cs;  // CTAs per cluster (Bt multicast)
+  int cg;  // CTAs per MMA: 1, or 2 for the 2-SM UMMA
 };
 
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
@@ -588,14 +686,14 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   }
   const int BN = Nr >= 256 ? 256 : Nr;
   const int tiles_m = (int)((sh.M + BM - 1) / BM);
-  // Two CTAs per cluster share (multicast) the Bt tile when each half is a
-  // whole number of 8-row swizzle groups and the 128-row tiles pair up.
-  d->cs = ((BN / 2) % 8 == 0 && tiles_m % 2 == 0 && cluster != 1) ? 2 : 1;
+  // The 2-SM UMMA when the 128-row tiles pair up and each CTA's half of the
+  // Bt tile is a whole number of 8-row swizzle groups.
+  d->cg = ((BN / 2) % 8 == 0 && tiles_m % 2 == 0 && cluster != 1) ? 2 : 1;
   for (int t = 0; t < 2; ++t)
     for (int pl = 0; pl < np; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)Kr, (cuuint64_t)Nr};
       cuuint64_t strides[1] = {(cuuint64_t)Kr * esz};
-      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)(BN / d->cs)};
+      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)(BN / d->cg)};
       cuuint32_t es[2] = {1, 1};
       CUresult r = enc(&d->prm.mapB[t][pl], dt, 2, const_cast<void *>(b_ptr[t][pl]), dims,
                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -612,7 +710,7 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   int cols = 32;
   while (cols < 2 * BN) cols *= 2;
   d->prm.tmem_cols = cols;
-  const int stage_bytes = np * (BM + BN) * rowb;
+  const int stage_bytes = np * (BM + BN / d->cg) * rowb;  // this CTA's share
   const int budget = 220 * 1024 - 1024 - 256;
   int stages = budget / stage_bytes;
   if (stages > 8) stages = 8;
@@ -623,10 +721,16 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
 
 void tc_release(void *h) { delete (TcLaunchData *)h; }
 
-template <int FMT, int ROWB, int CS>
-static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaStream_t s) {
-  auto kern = k_contract_tc<FMT, ROWB, CS>;
-  static int max_clusters = -1;  // co-resident clusters at the largest smem size
+template <int FMT, int ROWB, int CG>
+static int &max_clusters_of() {
+  static int v = -1;  // co-resident clusters at the largest smem size (-1: not set up)
+  return v;
+}
+
+template <int FMT, int ROWB, int CG>
+static cudaError_t init_kernel() {
+  auto kern = k_contract_tc<FMT, ROWB, CG>;
+  int &max_clusters = max_clusters_of<FMT, ROWB, CG>();
   if (max_clusters < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
@@ -634,10 +738,10 @@ static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaS
     cudaLaunchConfig_t q = {};
     cudaLaunchAttribute qa[1];
     qa[0].id = cudaLaunchAttributeClusterDimension;
-    qa[0].val.clusterDim.x = CS;
+    qa[0].val.clusterDim.x = CG;
     qa[0].val.clusterDim.y = 1;
     qa[0].val.clusterDim.z = 1;
-    q.gridDim = dim3(CS * 64);
+    q.gridDim = dim3(CG * 64);
     q.blockDim = dim3(THREADS);
     q.dynamicSmemBytes = 227 * 1024;
     q.attrs = qa;
@@ -650,17 +754,26 @@ static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaS
     }
     max_clusters = n;
   }
-  // units = SMs available; one CTA per SM, clusters of CS
-  int clusters = units / CS;
+  return cudaSuccess;
+}
+
+template <int FMT, int ROWB, int CG>
+static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaStream_t s) {
+  auto kern = k_contract_tc<FMT, ROWB, CG>;
+  cudaError_t e0 = init_kernel<FMT, ROWB, CG>();
+  if (e0 != cudaSuccess) return e0;
+  const int max_clusters = max_clusters_of<FMT, ROWB, CG>();
+  // units = SMs to use; one CTA per SM, clusters of CG
+  int clusters = units / CG;
   if (max_clusters > 0 && clusters > max_clusters) clusters = max_clusters;
   if (clusters < 1) clusters = 1;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.x = CG;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(clusters * CS);
+  cfg.gridDim = dim3(clusters * CG);
   cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -670,12 +783,30 @@ static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaS
 }
 
 template <int FMT>
-static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cs, int units, size_t smem,
+static cudaError_t warm_fmt(int rowb, int cg) {
+  if (rowb == 128) return cg == 2 ? init_kernel<FMT, 128, 2>() : init_kernel<FMT, 128, 1>();
+  return cg == 2 ? init_kernel<FMT, 64, 2>() : init_kernel<FMT, 64, 1>();
+}
+
+cudaError_t tc_warm(void *handle) {
+  TcLaunchData *d = (TcLaunchData *)handle;
+  switch (d->prm.sh.fmt) {
+    case FMT_BF16: return warm_fmt<FMT_BF16>(d->rowb, d->cg);
+    case FMT_FP16: return warm_fmt<FMT_FP16>(d->rowb, d->cg);
+    case FMT_BF16X2: return warm_fmt<FMT_BF16X2>(d->rowb, d->cg);
+    case FMT_FP16X2: return warm_fmt<FMT_FP16X2>(d->rowb, d->cg);
+    case FMT_TF32: return warm_fmt<FMT_TF32>(d->rowb, d->cg);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int FMT>
+static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cg, int units, size_t smem,
                               cudaStream_t s) {
   if (rowb == 128)
-    return cs == 2 ? launch_one<FMT, 128, 2>(prm, units, smem, s)
+    return cg == 2 ? launch_one<FMT, 128, 2>(prm, units, smem, s)
                    : launch_one<FMT, 128, 1>(prm, units, smem, s);
-  return cs == 2 ? launch_one<FMT, 64, 2>(prm, units, smem, s)
+  return cg == 2 ? launch_one<FMT, 64, 2>(prm, units, smem, s)
                  : launch_one<FMT, 64, 1>(prm, units, smem, s);
 }
 
@@ -690,19 +821,19 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
   prm.recs = d_recs;
   prm.st = st;
   prm.watchdog_ns = watchdog_ns;
-  const int cs = d->cs;
-  const int cluster_tiles = n_items * ((prm.tiles_m + cs - 1) / cs) * prm.tiles_n;
-  if (cluster_tiles < 1) return cudaSuccess;
-  int units = cluster_tiles * cs < sm_count ? cluster_tiles * cs : sm_count;
+  const int cg = d->cg;
+  const int pair_tiles = n_items * (prm.tiles_m / cg) * prm.tiles_n;
+  if (pair_tiles < 1) return cudaSuccess;
+  const int units = pair_tiles * cg < sm_count ? pair_tiles * cg : sm_count;
   const int np = np_of(prm.sh.fmt);
-  const size_t smem = (size_t)prm.stages * np * (BM + prm.BN) * d->rowb + 1024 +
+  const size_t smem = (size_t)prm.stages * np * (BM + prm.BN / cg) * d->rowb + 1024 +
                       (2 * prm.stages + 5) * 8 + 16;
   switch (prm.sh.fmt) {
-    case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cs, units, smem, s);
-    case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cs, units, smem, s);
-    case FMT_BF16X2: return launch_fmt<FMT_BF16X2>(prm, d->rowb, cs, units, smem, s);
-    case FMT_FP16X2: return launch_fmt<FMT_FP16X2>(prm, d->rowb, cs, units, smem, s);
-    case FMT_TF32: return launch_fmt<FMT_TF32>(prm, d->rowb, cs, units, smem, s);
+    case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cg, units, smem, s);
+    case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cg, units, smem, s);
+    case FMT_BF16X2: return launch_fmt<FMT_BF16X2>(prm, d->rowb, cg, units, smem, s);
+    case FMT_FP16X2: return launch_fmt<FMT_FP16X2>(prm, d->rowb, cg, units, smem, s);
+    case FMT_TF32: return launch_fmt<FMT_TF32>(prm, d->rowb, cg, units, smem, s);
   }
   return cudaErrorInvalidValue;
 }

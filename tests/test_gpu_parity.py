@@ -265,3 +265,15 @@ def test_timing_and_launch_counters(sim_factory):
     assert st["launches_contract"] == 25 * 2   # 2 lane chunks of 16, 25 steps
     assert st["launches_evolve"] > 10
     assert st["launches_total"] >= st["launches_contract"] + st["launches_evolve"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_cuda_graph_replay_matches_eager(sim_factory, prec):
+    circ, bits = workload("5x5_d16")
+    sim = sim_factory(circ)
+    eager = sim.amplitudes(bits[:40], precision=prec)
+    g1 = sim.amplitudes(bits[:40], precision=prec, flags=B.PEPS_FLAG_GRAPH)   # capture + replay
+    g2 = sim.amplitudes(bits[:40], precision=prec, flags=B.PEPS_FLAG_GRAPH)   # replay
+    assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
+    st = sim.stats()
+    assert st["launches_contract"] == 25 * 3   # 40 bitstrings in lanes of 16
