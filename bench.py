@@ -51,11 +51,15 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "slices"],
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "profile", "slices", "precision", "small"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
-                         "projected full time from a seeded subset of slices")
+                         "projected full time from a seeded subset of slices; precision: "
+                         "6x6 (1+24+1), every form's amplitudes/s on 4096 bitstrings and its "
+                         "error against the oracle on 64; small: 4x4 (1+8+1) and 5x5 (1+16+1), "
+                         "eager launches vs CUDA-graph replay")
     ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
@@ -427,12 +431,89 @@ def run_slices_case(args):
     sim.close()
 
 
+def _time_calls(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def run_precision_case(args):
+    """6x6 (1+24+1), 4096 seeded bitstrings: throughput of every form and its
+    normwise error against the FP64 oracle on the first 64."""
+    import numpy as np
+    import torch
+
+    from oracle import peps as op
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload("6x6_d24")
+    ref = op.amplitudes(op.build(6, 6, circ.gates), bits[:64])
+    sim = Simulator(6, 6)
+    sim.apply_circuit(circ)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    rows = []
+    for prec in ("fp32", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"):
+        kw = dict(precision=prec, max_lanes=args.lanes, flags=B.PEPS_FLAG_REBUILD)
+        sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, **kw), max(1, args.steps))
+        out = d_out.cpu().numpy()
+        err = float(np.linalg.norm(out[:64] - ref) / np.linalg.norm(ref))
+        pt = float(np.mean((2.0 ** 36) * np.abs(out) ** 2))
+        rows.append({"precision": prec, "amplitudes_per_s": len(bits) / sec, "rel_err": err,
+                     "mean_N_abs2": pt})
+    print(json.dumps({"case": "precision", "workload": "6x6 (1+24+1), 4096 bitstrings",
+                      "oracle_bitstrings": 64, "forms": rows}), flush=True)
+    sim.close()
+
+
+def run_small_case(args):
+    """4x4 (1+8+1) with 64 bitstrings and 5x5 (1+16+1) with 1024: launch-latency
+    bound; eager launch sequence vs the same sequence replayed as a CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    out = []
+    for name, prec in (("4x4_d8", "fp32"), ("5x5_d16", "fp32"), ("5x5_d16", "fp16x3")):
+        circ, bits = workload(name)
+        sim = Simulator(circ.R, circ.C)
+        sim.apply_circuit(circ)
+        d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+        d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+        res = {"workload": name, "precision": prec, "bitstrings": len(bits)}
+        for mode, flags in (("eager", B.PEPS_FLAG_REBUILD), ("graph", B.PEPS_FLAG_GRAPH)):
+            kw = dict(precision=prec, max_lanes=64, flags=flags)
+            sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, **kw), 20)
+            res[mode] = {"amplitudes_per_s": len(bits) / sec, "us_per_call": sec * 1e6,
+                         "launches_per_call": sim.stats()["launches_total"]}
+        out.append(res)
+        sim.close()
+    print(json.dumps({"case": "small", "results": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.case == "profile":
         run_profile_case(args)
     elif args.case == "slices":
         run_slices_case(args)
+    elif args.case == "precision":
+        run_precision_case(args)
+    elif args.case == "small":
+        run_small_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -126,9 +126,16 @@ typedef struct {
     int32_t tc_kchunk;        /* tensor-core tuning: bytes of K per pipeline
                                  stage, 64 or 128 (0 = 128 where the row
                                  length allows); smaller means more stages  */
-    int32_t tc_cluster;       /* tensor-core tuning: CTAs sharing the operand
-                                 tile by multicast, 1 or 2 (0 = 2 where the
+    int32_t tc_cluster;       /* tensor-core tuning: 2 = CTA pairs compute
+                                 256-row tiles with the 2-SM MMA, 1 = one CTA
+                                 per 128-row tile (0 = pairs where the row
                                  tiles pair up)                              */
+    int32_t fuse_rows;        /* contraction order: 0 = absorb the two top and
+                                 the two bottom rows of a column in one step
+                                 each where that costs no more multiply-adds
+                                 (the running tensor between them is never
+                                 stored); 1 = one site per step              */
+    int32_t pad2_;
 } peps_opts;
 
 /* Counters of the last amplitude call (kernel launches are the library's own

@@ -81,6 +81,46 @@ def column_sweep_step_cmacs(R: int, C: int, chi: int) -> list:
     return out
 
 
+def column_sweep_block_cmacs(R: int, C: int, chi: int, fuse: bool = True) -> list:
+    """Like column_sweep_step_cmacs, but with the two top rows and the two
+    bottom rows of a column absorbed in one step each (when R >= 4, the
+    pair costs no more than its two single steps, and it has at least 152
+    output tiles of 128 x 64 or a K no longer than the two singles' K).  A block of rows
+    r0 .. r0+k-1 costs M*K*N with M the product of the untouched horizontal
+    legs (rows above the block carry h', rows below carry h), K the product of
+    the block's incoming horizontal legs times the vertical leg above it, N the
+    product of its outgoing horizontal legs times the vertical leg below it.
+    Returns [(r0, k, cmacs)] in sweep order."""
+    out = []
+    for c in range(C):
+        left = 1 if c == 0 else chi
+        right = 1 if c == C - 1 else chi
+        vdim = lambda r: chi if 0 <= r < R - 1 else 1   # leg between rows r, r+1
+        def mkn(r0, k):
+            M = right ** r0 * left ** (R - r0 - k)
+            return M, left ** k * vdim(r0 - 1), right ** k * vdim(r0 + k - 1)
+
+        def cost(r0, k):
+            M, K, N = mkn(r0, k)
+            return M * K * N
+
+        def parallel_enough(r0):
+            # enough 128 x 64 output tiles, or a K no longer than the singles'
+            M, K, N = mkn(r0, 2)
+            tiles = -(-M // 128) * -(-N // 64)
+            return tiles >= 152 or K <= mkn(r0, 1)[1] + mkn(r0 + 1, 1)[1]
+
+        r = 0
+        while r < R:
+            k = 1
+            if (fuse and R >= 4 and (r == 0 or r == R - 2)
+                    and cost(r, 2) <= cost(r, 1) + cost(r + 1, 1) and parallel_enough(r)):
+                k = 2
+            out.append((r, k, cost(r, k)))
+            r += k
+    return out
+
+
 def column_sweep_cmacs(R: int, C: int, chi: int) -> int:
     """Sum of column_sweep_step_cmacs (boundary steps included)."""
     return sum(column_sweep_step_cmacs(R, C, chi))

@@ -56,6 +56,7 @@ struct Launch {
   StepShape shape;
   bool tc;
   void *tc_handle = nullptr;  // tensor maps of a tcgen05 launch
+  int op_base = 0;            // first OpDesc of the step
   size_t a_base_rel = 0;      // input buffer of item lane 0 (relative to the buffer area)
   int a_lanes = 1;            // lanes addressed through the A tensor map
   int64_t items_off;  // index into the item array
@@ -109,6 +110,11 @@ struct Plan {
   // step shapes
   std::vector<StepShape> steps;
   std::vector<int> step_site;
+  std::vector<int> step_opbase;  // first OpDesc of each step (2^nq variants)
+  int n_ops = 0;
+  int64_t n_obe2_per_slice = 0;
+  int max_kn2 = 0;
+  size_t off_opbuild2 = 0;
 
   // launches (per slice iteration)
   std::vector<Launch> launches;
@@ -145,6 +151,8 @@ struct peps_ctx {
   bool broken = false;
   std::vector<cudaEvent_t> ev;
   int sm_count = 0;
+  cudaStream_t cap_stream = nullptr;  // records CUDA graphs (the caller's stream
+                                      // may be the legacy default stream)
 };
 
 static int edge_h(const peps_ctx *c, int r, int col) { return r * (c->C - 1) + col; }
@@ -170,6 +178,8 @@ extern "C" int peps_create(int R, int C, peps_ctx **out) {
 extern "C" int peps_destroy(peps_ctx *c) {
   if (!c) return fail(PEPS_EINVAL, "peps_destroy: NULL context");
   for (auto e : c->ev) cudaEventDestroy(e);
+  c->plan.reset();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return PEPS_OK;
 }
@@ -300,7 +310,8 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
          a.prefix_cols == b.prefix_cols && a.prefix_group == b.prefix_group &&
          a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
          a.n_slice_ids == b.n_slice_ids && a.n_fixed == b.n_fixed &&
-         a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster;
+         a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster &&
+         a.fuse_rows == b.fuse_rows;
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
@@ -322,6 +333,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   if (o.n_sliced > 0 && !o.sliced_cz) return fail(PEPS_EINVAL, "sliced_cz is NULL");
   if (o.n_slice_ids < 0) return fail(PEPS_EINVAL, "n_slice_ids < 0");
   if (o.n_fixed < 0) return fail(PEPS_EINVAL, "n_fixed < 0");
+  if (o.fuse_rows < 0 || o.fuse_rows > 1) return fail(PEPS_EINVAL, "fuse_rows must be 0 or 1");
   if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster))
     return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128 and tc_cluster 0, 1 or 2");
   if (o.n_fixed > 0 && (!o.fixed_cz || !o.fixed_s)) return fail(PEPS_EINVAL, "fixed_cz / fixed_s is NULL");
@@ -405,60 +417,112 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     return (r < 0 || r >= R - 1) ? 1 : L.dim_v[edge_v(c, r, col)];
   };
 
+  // ---- blocks: the sites each step absorbs ----
+  // One site per step, except that (with fuse_rows == 0) the two top rows and
+  // the two bottom rows of a column are absorbed together when that costs no
+  // more multiply-adds and leaves the step enough output tiles (or no longer
+  // a K) to fill the GPU: the top pair has no incoming vertical leg and the
+  // bottom pair no outgoing one, so the pair's operand is no larger than the
+  // largest single step's and the running tensor between the two rows is never
+  // written.
+  struct Block { int col, r0, nq; };
+  std::vector<Block> blocks;
+  for (int col = 0; col < C; ++col) {
+    const bool fuse = o.fuse_rows == 0 && R >= 4;
+    int r = 0;
+    while (r < R) {
+      int nq = 1;
+      if (fuse && (r == 0 || r == R - 2)) {
+        // cost of the pair vs its two single steps (dims at this column)
+        const int64_t hl0 = rdim_h(r, col - 1), hl1 = rdim_h(r + 1, col - 1);
+        const int64_t hr0 = rdim_h(r, col), hr1 = rdim_h(r + 1, col);
+        const int64_t vin = rdim_v(r - 1, col), vmid = rdim_v(r, col), vout = rdim_v(r + 1, col);
+        const double pair = (double)hl0 * hl1 * vin * hr0 * hr1 * vout;
+        const double single = (double)hl0 * vin * hr0 * vmid * hl1 + (double)hr0 * hl1 * vmid * hr1 * vout;
+        // a pair with few output tiles runs its whole K on a few CTAs: take
+        // it only if its K is no longer than the two single steps' together
+        double Mrest = 1;
+        for (int rr = 0; rr < R; ++rr)
+          if (rr < r) Mrest *= (double)rdim_h(rr, col);
+          else if (rr > r + 1) Mrest *= (double)rdim_h(rr, col - 1);
+        const double tiles = std::ceil(Mrest / 128.0) * std::ceil((double)(hr0 * hr1 * vout) / 64.0);
+        const bool shallow = hl0 * hl1 * vin <= hl0 * vin + hl1 * vmid;
+        if (pair <= single && (tiles >= 152 || shallow) && vmid <= kMaxMid) nq = 2;
+      }
+      blocks.push_back({col, r, nq});
+      r += nq;
+    }
+  }
+
   // ---- step list of the column sweep (legs tracked by identity) ----
-  // leg ids: h-edge (r, col) -> 1000 + r*64 + col ; v-leg -> 2 (dim 1 at the
-  // column ends, so the bottom leg of column c and the top leg of column c+1
-  // share the id).
+  // Before a block of rows r .. r+k-1 the running tensor's legs are, slowest
+  // first, [h_{r+k} .. h_{R-1}, h'_0 .. h'_{r-1}, h_r .. h_{r+k-1}, v]; the
+  // block's store moves the next block's k' legs (the slowest M legs) next to
+  // v', which restores that form.  Leg ids: h-edge (r, col) -> 1000 + r*64 +
+  // col + 1; v-leg -> 2 at the column ends (the bottom leg of column c and the
+  // top leg of column c+1 are both of dim 1 and share the id).
   struct Leg { int id; int64_t dim; };
   std::vector<Leg> legs;
   auto hid = [&](int r, int col) { return 1000 + r * 64 + (col + 1); };
-  for (int j = 1; j < R; ++j) legs.push_back({hid(j, -1), 1});
-  legs.push_back({hid(0, -1), 1});
-  legs.push_back({2, 1});
+  {
+    const int k0 = blocks.empty() ? 1 : blocks[0].nq;
+    for (int j = k0; j < R; ++j) legs.push_back({hid(j, -1), 1});
+    for (int j = 0; j < k0; ++j) legs.push_back({hid(j, -1), 1});
+    legs.push_back({2, 1});
+  }
   P.steps.clear();
   P.step_site.clear();
+  P.step_opbase.clear();
   int64_t cap = 1;
   double flops = 0, bytes = 0;
-  for (int col = 0; col < C; ++col) {
-    for (int r = 0; r < R; ++r) {
-      const size_t nl = legs.size();
-      if (legs[nl - 2].id != hid(r, col - 1))
-        return fail(PEPS_EINVAL, "internal: leg order broken at (%d,%d)", r, col);
-      const int64_t K = legs[nl - 2].dim * legs[nl - 1].dim;
-      int64_t M = 1;
-      for (size_t i = 0; i + 2 < nl; ++i) M *= legs[i].dim;
-      const int64_t dh = rdim_h(r, col), dv = rdim_v(r, col);
-      const int64_t N = dh * dv;
-      const int64_t Pdim = (nl > 2) ? legs[0].dim : 1;
-      if (K > (1 << 20) || N > (1 << 20))
-        return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r, col);
-      StepShape sh{};
-      sh.M = M;
-      sh.K = (int)K;
-      sh.N = (int)N;
-      sh.P = Pdim;
-      sh.dv_out = (int)dv;
-      sh.dh_out = (int)dh;
-      sh.q = r * C + col;
-      sh.fmt = fmt;
-      sh.target = scale_target(fmt);
-      P.steps.push_back(sh);
-      P.step_site.push_back(r * C + col);
-      cap = std::max(cap, std::max(M * K, M * N));
-      flops += 8.0 * (double)M * K * N;
-      bytes += (double)bpe * (double)(M * K + M * N);
-      std::vector<Leg> nlgs;
-      if (nl > 2) {
-        for (size_t i = 1; i + 2 < nl; ++i) nlgs.push_back(legs[i]);
-        nlgs.push_back({hid(r, col), dh});
-        nlgs.push_back(legs[0]);
-        nlgs.push_back({r == R - 1 ? 2 : 3000 + r, dv});
-      } else {
-        nlgs.push_back({hid(r, col), dh});
-        nlgs.push_back({r == R - 1 ? 2 : 3000 + r, dv});
-      }
-      legs.swap(nlgs);
-    }
+  int n_ops_total = 0;
+  for (size_t bi = 0; bi < blocks.size(); ++bi) {
+    const Block &bk = blocks[bi];
+    const int col = bk.col, r0 = bk.r0, k = bk.nq;
+    const int knext = bi + 1 < blocks.size() ? blocks[bi + 1].nq : 0;
+    const size_t nl = legs.size();
+    for (int j = 0; j < k; ++j)
+      if (legs[nl - 1 - k + j].id != hid(r0 + j, col - 1))
+        return fail(PEPS_EINVAL, "internal: leg order broken at (%d,%d)", r0 + j, col);
+    int64_t K = legs[nl - 1].dim;
+    for (int j = 0; j < k; ++j) K *= legs[nl - 1 - k + j].dim;
+    const size_t nM = nl - 1 - k;  // M legs: legs[0 .. nM)
+    int64_t M = 1;
+    for (size_t i = 0; i < nM; ++i) M *= legs[i].dim;
+    int64_t dh = 1;
+    for (int j = 0; j < k; ++j) dh *= rdim_h(r0 + j, col);
+    const int64_t dv = rdim_v(r0 + k - 1, col);
+    const int64_t N = dh * dv;
+    const size_t kmove = std::min<size_t>((size_t)knext, nM);
+    int64_t Pdim = 1;
+    for (size_t i = 0; i < kmove; ++i) Pdim *= legs[i].dim;
+    if (K > (1 << 20) || N > (1 << 20))
+      return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r0, col);
+    StepShape sh{};
+    sh.M = M;
+    sh.K = (int)K;
+    sh.N = (int)N;
+    sh.P = Pdim;
+    sh.dv_out = (int)dv;
+    sh.dh_out = (int)dh;
+    sh.q = r0 * C + col;
+    sh.nq = k;
+    sh.qs = C;
+    sh.fmt = fmt;
+    sh.target = scale_target(fmt);
+    P.steps.push_back(sh);
+    P.step_site.push_back(r0 * C + col);
+    P.step_opbase.push_back(n_ops_total);
+    n_ops_total += 1 << k;
+    cap = std::max(cap, std::max(M * K, M * N));
+    flops += 8.0 * (double)M * K * N;
+    bytes += (double)bpe * (double)(M * K + M * N);
+    std::vector<Leg> nlgs;
+    for (size_t i = kmove; i < nM; ++i) nlgs.push_back(legs[i]);
+    for (int j = 0; j < k; ++j) nlgs.push_back({hid(r0 + j, col), rdim_h(r0 + j, col)});
+    for (size_t i = 0; i < kmove; ++i) nlgs.push_back(legs[i]);
+    nlgs.push_back({r0 + k == R ? 2 : 3000 + r0 + k - 1, dv});
+    legs.swap(nlgs);
   }
   if (cap > ((int64_t)1 << 36)) return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
   P.cap = cap;
@@ -478,7 +542,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
 
   // ---- lanes ----
   const int pc = o.prefix_cols;
-  const int pre_steps = pc * R;
+  // steps of the shared prefix: the blocks of columns 0 .. pc-1
+  int pre_steps = 0;
+  for (const auto &bk : blocks)
+    if (bk.col < pc) ++pre_steps;
   int64_t gs = pc > 0 ? o.prefix_group : std::max<int64_t>(n, 1);
   P.n_groups = (pc > 0 && n > 0) ? (int)(n / gs) : 0;
   int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
@@ -591,18 +658,27 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
   P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
 
-  // operands (restricted dims), two per site
-  const int n_ops = 2 * NQ;
+  // operands (restricted dims): 2^nq variants per step
+  const int n_ops = n_ops_total;
+  P.n_ops = n_ops;
   P.ec_off.assign(n_ops, 0);
   P.bt_off[0].assign(n_ops, 0);
   P.bt_off[1].assign(n_ops, 0);
   P.max_kn = 1;
+  P.max_kn2 = 1;
   const bool want_tc = o.precision != PEPS_FP32_SIMT && !(o.flags & PEPS_FLAG_NO_TC);
+  int64_t n1 = 0, n2 = 0;
   for (int s = 0; s < P.n_steps; ++s) {
     const StepShape &sh = P.steps[s];
-    P.max_kn = std::max<int>(P.max_kn, sh.K * sh.N);
-    for (int t = 0; t < 2; ++t) {
-      const int op = 2 * sh.q + t;
+    if (sh.nq == 1) {
+      P.max_kn = std::max<int>(P.max_kn, sh.K * sh.N);
+      n1 += 2;
+    } else {
+      P.max_kn2 = std::max<int>(P.max_kn2, sh.K * sh.N);
+      n2 += 4;
+    }
+    for (int t = 0; t < (1 << sh.nq); ++t) {
+      const int op = P.step_opbase[s] + t;
       P.ec_off[op] = off;
       off = align_up(off + (size_t)sh.K * sh.N * sizeof(float2), 1024);
       if (want_tc && tc_supports(sh, fmt)) {
@@ -617,9 +693,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     }
   }
   P.off_opdesc = off; off = align_up(off + n_ops * sizeof(OpDesc));
-  P.n_opbuild_per_slice = n_ops;
+  P.n_opbuild_per_slice = n1;
+  P.n_obe2_per_slice = n2;
   P.off_opbuild = off;
-  off = align_up(off + (size_t)n_ops * P.slice_list.size() * sizeof(OpBuildEntry));
+  off = align_up(off + (size_t)std::max<int64_t>(n1, 1) * P.slice_list.size() * sizeof(OpBuildEntry));
+  P.off_opbuild2 = off;
+  off = align_up(off + (size_t)std::max<int64_t>(n2, 1) * P.slice_list.size() * sizeof(OpBuild2Entry));
 
   // records: chains = groups + bitstrings
   P.n_recs = (int)((P.n_groups + n) * P.n_steps);
@@ -651,6 +730,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     ln.tc = want_tc && tc_supports(P.steps[s], fmt);
     ln.a_base_rel = rs[0].a;
     ln.a_lanes = a_lanes;
+    ln.op_base = P.step_opbase[s];
     for (size_t i = 0; i < its.size(); ++i) its[i].a_lane = a_lanes > 1 ? (int)i : 0;
     ln.items_off = (int64_t)items.size();
     ln.n_items = (int)its.size();
@@ -665,7 +745,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       const int chain = g;
       for (int s = 0; s < pre_steps; ++s) {
         StepItem it{};
-        it.op_base = 2 * P.steps[s].q;
+        it.op_base = P.step_opbase[s];
         it.in_rec = s == 0 ? -1 : (int)(chain * NS + s - 1);
         it.out_rec = (int)(chain * NS + s);
         RelItem ri{s == 0 ? 0 : pre_buf((s - 1) % 2), pre_buf(s % 2), s == 0, (int64_t)g * gs};
@@ -681,7 +761,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
             const int64_t i = (int64_t)g * gs + base + l;
             const int64_t ch = P.n_groups + i;
             StepItem it{};
-            it.op_base = 2 * P.steps[s].q;
+            it.op_base = P.step_opbase[s];
             it.in_rec = s == pre_steps ? (int)(chain * NS + pre_steps - 1) : (int)(ch * NS + s - 1);
             it.out_rec = (int)(ch * NS + s);
             RelItem ri{s == pre_steps ? pre_out : lane_buf(l, (s - 1 - pre_steps) % 2),
@@ -715,7 +795,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         for (int l = 0; l < nl; ++l) {
           const int64_t i = base + l;
           StepItem it{};
-          it.op_base = 2 * P.steps[s].q;
+          it.op_base = P.step_opbase[s];
           it.in_rec = s == 0 ? -1 : (int)(i * NS + s - 1);
           it.out_rec = (int)(i * NS + s);
           RelItem ri{s == 0 ? 0 : lane_buf(l, (s - 1) % 2), lane_buf(l, s % 2), s == 0, i};
@@ -768,11 +848,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   for (auto &l : P.launches) {
     if (l.kind != 0 || !l.tc) continue;
     const int q = l.shape.q;
-    const void *bp[2][2];
-    for (int t = 0; t < 2; ++t)
+    const int ob = l.op_base;
+    const void *bp[4][2] = {};
+    for (int t = 0; t < (1 << l.shape.nq); ++t)
       for (int pl = 0; pl < 2; ++pl)
-        bp[t][pl] = P.bt_off[pl][2 * q + t] ? (const void *)(base + P.bt_off[pl][2 * q + t])
-                                             : (const void *)(base + P.bt_off[0][2 * q + t]);
+        bp[t][pl] = P.bt_off[pl][ob + t] ? (const void *)(base + P.bt_off[pl][ob + t])
+                                         : (const void *)(base + P.bt_off[0][ob + t]);
     int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
                         (int64_t)(2 * P.gbuf_bytes), P.plane * 2, bp, o.tc_kchunk, o.tc_cluster,
                         &l.tc_handle);
@@ -783,8 +864,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<OpDesc> ops(n_ops);
   for (int s = 0; s < P.n_steps; ++s) {
     const StepShape &sh = P.steps[s];
-    for (int t = 0; t < 2; ++t) {
-      const int op = 2 * sh.q + t;
+    for (int t = 0; t < (1 << sh.nq); ++t) {
+      const int op = P.step_opbase[s] + t;
       OpDesc d{};
       d.Ec = (const float2 *)(base + P.ec_off[op]);
       d.Bt[0] = P.bt_off[0][op] ? (const void *)(base + P.bt_off[0][op]) : nullptr;
@@ -795,8 +876,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       ops[op] = d;
     }
   }
-  // operand build entries per slice
+  // operand build entries per slice: one per (step, variant)
   std::vector<OpBuildEntry> obe;
+  std::vector<OpBuild2Entry> obe2;
   for (int64_t sid : P.slice_list) {
     // fixed values of every edge for this slice
     std::vector<uint32_t> val_h = fixval_h, val_v = fixval_v;
@@ -804,34 +886,48 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       const CzPos &p = czpos[o.sliced_cz[j]];
       if ((sid >> j) & 1) (p.horiz ? val_h[p.edge] : val_v[p.edge]) |= 1u << p.bit;
     }
-    for (int q = 0; q < NQ; ++q) {
+    // the projected tensor of site q for bit t, legs restricted to the slice
+    auto site_entry = [&](int q, int t, int op) {
       const int r = q / C, col = q % C;
-      for (int t = 0; t < 2; ++t) {
-        OpBuildEntry e{};
-        const int fb = P.final_buf[q];
-        e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
-        e.lo_off = P.site_elems[q];
-        for (int a = 0; a < 4; ++a) e.dims[a] = sd[4 * q + a];
-        // legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
-        auto leg = [&](int a, bool horiz, int rr, int cc) {
-          bool inside = horiz ? (cc >= 0 && cc < C - 1) : (rr >= 0 && rr < R - 1);
-          uint32_t fm = 0, fv = 0;
-          if (inside) {
-            const int eidx = horiz ? edge_h(c, rr, cc) : edge_v(c, rr, cc);
-            fm = horiz ? L.fix_h[eidx] : L.fix_v[eidx];
-            fv = horiz ? val_h[eidx] : val_v[eidx];
-          }
-          e.free_mask[a] = (uint32_t)(e.dims[a] - 1) & ~fm;
-          e.fixed_val[a] = fv;
-          e.rdims[a] = e.dims[a] >> popcount32(fm);
-        };
-        leg(0, true, r, col - 1);
-        leg(1, true, r, col);
-        leg(2, false, r - 1, col);
-        leg(3, false, r, col);
-        e.tau = t;
-        e.op = 2 * q + t;
-        obe.push_back(e);
+      OpBuildEntry e{};
+      const int fb = P.final_buf[q];
+      e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
+      e.lo_off = P.site_elems[q];
+      for (int a = 0; a < 4; ++a) e.dims[a] = sd[4 * q + a];
+      // legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
+      auto leg = [&](int a, bool horiz, int rr, int cc) {
+        bool inside = horiz ? (cc >= 0 && cc < C - 1) : (rr >= 0 && rr < R - 1);
+        uint32_t fm = 0, fv = 0;
+        if (inside) {
+          const int eidx = horiz ? edge_h(c, rr, cc) : edge_v(c, rr, cc);
+          fm = horiz ? L.fix_h[eidx] : L.fix_v[eidx];
+          fv = horiz ? val_h[eidx] : val_v[eidx];
+        }
+        e.free_mask[a] = (uint32_t)(e.dims[a] - 1) & ~fm;
+        e.fixed_val[a] = fv;
+        e.rdims[a] = e.dims[a] >> popcount32(fm);
+      };
+      leg(0, true, r, col - 1);
+      leg(1, true, r, col);
+      leg(2, false, r - 1, col);
+      leg(3, false, r, col);
+      e.tau = t;
+      e.op = op;
+      return e;
+    };
+    for (int s = 0; s < P.n_steps; ++s) {
+      const StepShape &sh = P.steps[s];
+      const int ob = P.step_opbase[s];
+      if (sh.nq == 1) {
+        for (int t = 0; t < 2; ++t) obe.push_back(site_entry(sh.q, t, ob + t));
+      } else {
+        for (int v = 0; v < 4; ++v) {
+          OpBuild2Entry e2{};
+          e2.a = site_entry(sh.q, v & 1, ob + v);
+          e2.b = site_entry(sh.q + C, (v >> 1) & 1, ob + v);
+          e2.op = ob + v;
+          obe2.push_back(e2);
+        }
       }
     }
   }
@@ -849,6 +945,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   put(P.off_cz, cz.data(), cz.size() * sizeof(CzEntry));
   put(P.off_opdesc, ops.data(), ops.size() * sizeof(OpDesc));
   put(P.off_opbuild, obe.data(), obe.size() * sizeof(OpBuildEntry));
+  put(P.off_opbuild2, obe2.data(), obe2.size() * sizeof(OpBuild2Entry));
   put(P.off_items, items.data(), items.size() * sizeof(StepItem));
   put(P.off_fin, fins.data(), fins.size() * sizeof(FinalEntry));
   return PEPS_OK;
@@ -916,7 +1013,7 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   const int64_t ns = (int64_t)P.slice_list.size();
-  S.launches_operand = ns * (2 + (any_tc ? 1 : 0));
+  S.launches_operand = ns * (2 + (P.n_obe2_per_slice > 0 ? 1 : 0) + (any_tc ? 1 : 0));
   for (auto &l : P.launches) {
     if (l.kind == 0) {
       S.launches_contract += ns;
@@ -977,15 +1074,23 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
   const StepItem *items = (const StepItem *)(base + P.off_items);
   const FinalEntry *fins = (const FinalEntry *)(base + P.off_fin);
   const OpBuildEntry *obe = (const OpBuildEntry *)(base + P.off_opbuild);
+  const OpBuild2Entry *obe2 = (const OpBuild2Entry *)(base + P.off_opbuild2);
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   for (size_t si = 0; si < P.slice_list.size(); ++si) {
     if (P.n_recs > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, P.n_recs * sizeof(Rec), s));
     const OpBuildEntry *e = obe + si * P.n_opbuild_per_slice;
+    const OpBuild2Entry *e2 = obe2 + si * P.n_obe2_per_slice;
     CUDA_TRY(launch_build_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, s));
-    S.launches_operand += 2;
+    S.launches_operand++;
+    if (P.n_obe2_per_slice > 0) {
+      CUDA_TRY(launch_build_operands2(e2, (int)P.n_obe2_per_slice, P.max_kn2, ops, s));
+      S.launches_operand++;
+    }
+    CUDA_TRY(launch_operand_bounds(P.n_ops, ops, s));
+    S.launches_operand++;
     if (any_tc) {
-      CUDA_TRY(launch_build_tc_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, P.fmt, s));
+      CUDA_TRY(launch_build_tc_operands(P.n_ops, std::max(P.max_kn, P.max_kn2), ops, P.fmt, s));
       S.launches_operand++;
     }
     for (auto &l : P.launches) {
@@ -1037,11 +1142,13 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
     if (!P.graph_exec) {
       for (auto &l : P.launches)
         if (l.kind == 0 && l.tc) CUDA_TRY(tc_warm(l.tc_handle));
-      CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t cs = c->cap_stream;
+      CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       peps_stats S2{};
-      int rc = enqueue_sequence(c, P, d_bits_in, s, true, false, S2, nullptr, nullptr);
+      int rc = enqueue_sequence(c, P, d_bits_in, cs, true, false, S2, nullptr, nullptr);
       cudaGraph_t g = nullptr;
-      cudaError_t e = cudaStreamEndCapture(s, &g);
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;

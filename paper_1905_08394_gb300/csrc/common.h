@@ -89,20 +89,32 @@ struct StepItem {
   int32_t a_lane;         // lane coordinate of A in the launch's tensor map
 };
 
-// Shape shared by all items of a launch.
+// Shape shared by all items of a launch.  A step absorbs a block of nq
+// vertically adjacent sites (rows r .. r+nq-1 of one column) at once.
 struct StepShape {
   int64_t M;      // product of the untouched h legs
-  int32_t K;      // dim(h_r) * dim(v)
-  int32_t N;      // dim(h'_r) * dim(v')
-  int64_t P;      // dim of the slowest M leg (moved next to v' on store)
+  int32_t K;      // dim(h_r) * ... * dim(h_{r+nq-1}) * dim(v)
+  int32_t N;      // dim(h'_r) * ... * dim(h'_{r+nq-1}) * dim(v')
+  int64_t P;      // product of the dims of the slowest M legs that the next
+                  // block contracts (moved next to v' on store)
   int32_t dv_out; // dim(v')
-  int32_t dh_out; // dim(h'_r)
-  int32_t q;      // site
+  int32_t dh_out; // dim(h'_r) * ... * dim(h'_{r+nq-1})
+  int32_t q;      // first site of the block
   int32_t fmt;    // storage format of A and D
   int64_t plane;  // element offset of the lo plane (FMT_*X2), in 16-bit units
   int32_t target; // scale target exponent
+  int32_t nq;     // sites in the block (their q are q, q + qs, ...)
+  int32_t qs;     // site stride (C)
   int32_t pad_;
 };
+
+// Operand index of a lane for a block: bit j = output bit of the block's
+// j-th site (for one site: tau).
+__host__ __device__ inline int block_variant(uint64_t bits, const StepShape &sh) {
+  int v = 0;
+  for (int j = 0; j < sh.nq; ++j) v |= (int)((bits >> (sh.q + j * sh.qs)) & 1ull) << j;
+  return v;
+}
 
 // Evolution tables.  Site tensors are kept as float-float pairs: a hi plane
 // and a lo plane (value = hi + lo), the lo plane `lo_off` entries after the
@@ -138,6 +150,18 @@ struct OpBuildEntry {
   int32_t op;           // OpDesc index to fill
 };
 
+// largest internal vertical bond of a two-site block operand
+constexpr int kMaxMid = 1024;
+
+// Operand build of a two-site block (rows r, r+1 of a column):
+//   W[(l_a, l_b, u_a), (r_a, r_b, d_b)] = sum_m E_a[l_a, r_a, u_a, m] E_b[l_b, r_b, m, d_b]
+// with E_a = A_a^{tau_a}, E_b = A_b^{tau_b} (restricted legs as for one site).
+struct OpBuild2Entry {
+  OpBuildEntry a, b;
+  int32_t op;
+  int32_t pad_;
+};
+
 struct FinalEntry {     // one output amplitude contribution
   const void *G;        // final 1x1 G of a lane
   int32_t rec;          // its Rec
@@ -165,8 +189,12 @@ cudaError_t launch_gate1(const Gate1Entry *d_entries, int n, int64_t max_half,
 cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStream_t s);
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
                                   OpDesc *d_ops, cudaStream_t s);
-cudaError_t launch_build_tc_operands(const OpBuildEntry *d_entries, int n, int max_kn,
-                                     OpDesc *d_ops, int fmt, cudaStream_t s);
+cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s);
+cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
+                                   OpDesc *d_ops, cudaStream_t s);
+// Tensor-core planes (and their bound) of ops [0, n_ops) from their Ec.
+cudaError_t launch_build_tc_operands(int n_ops, int max_kn, OpDesc *d_ops, int fmt,
+                                     cudaStream_t s);
 cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, int n_items,
                                  const OpDesc *d_ops, Rec *d_recs, const DeviceStatus *st,
                                  cudaStream_t s);
@@ -183,7 +211,7 @@ bool tc_tuning_valid(int kchunk, int cluster);
 // Encode the launch's tensor maps (A over the lanes' input buffers, Bt for
 // tau = 0/1 and each plane); returns 0 and an opaque handle, or < 0.
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
-               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[4][2],
                int kchunk, int cluster, void **out_handle);
 void tc_release(void *handle);
 // One-time set-up of the kernel a handle launches (attributes, occupancy);

@@ -36,8 +36,7 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
 
   const StepItem it = items[blockIdx.z];
   const uint64_t bits = *it.bits;
-  const int tau = (int)((bits >> sh.q) & 1ull);
-  const OpDesc &op = ops[it.op_base + tau];
+  const OpDesc &op = ops[it.op_base + block_variant(bits, sh)];
   const float2 *__restrict__ Ec = op.Ec;
   const int64_t M = sh.M;
   const int K = sh.K, N = sh.N;

@@ -57,7 +57,7 @@ template <> struct FormTraits<FMT_TF32>   { static constexpr int NP = 1, ESZ = 4
 
 struct __align__(64) TcParams {
   CUtensorMap mapA;        // {k, m, plane, lane}
-  CUtensorMap mapB[2][2];  // [tau][plane] {k, n}
+  CUtensorMap mapB[4][2];  // [block variant][plane] {k, n}
   StepShape sh;
   const StepItem *items;
   const OpDesc *ops;
@@ -156,16 +156,6 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-// Prefetch a 4-D tile of the tensor into L2 (no shared memory, no barrier).
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap *map, int c0, int c1, int c2,
-                                                int c3) {
-  asm volatile(
-      "cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-          (uint64_t)map),
-      "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-
 // Shared::cluster address of the same shared-memory offset in CTA `rank`.
 __device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t rank) {
   uint32_t r;
@@ -173,8 +163,11 @@ __device__ __forceinline__ uint32_t cluster_addr(const void *local, uint32_t ran
   return r;
 }
 // Arrive on an mbarrier given by its shared::cluster address (any CTA).
+// Relaxed: the epilogue's arrival only has to follow its own completed TMEM
+// reads (tcgen05.wait::ld, in program order); its global stores are for the
+// next launch, so a release (which waits for them) would stall the epilogue.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(
                    bar_cluster_addr)
                : "memory");
 }
@@ -375,21 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
         const int mt = mg * CG + (int)rank;
         const StepItem &si = p.items[item];
-        const int tau = (int)((*si.bits >> p.sh.q) & 1ull);
-        // The next tile's rows of A come from DRAM: start pulling them into L2
-        // now, a whole tile ahead, so that its TMA loads find them in L2.
-        {
-          const int tn = t + ncl;
-          if (tn < total) {
-            const int item2 = tn / tiles_per_item;
-            const int rem2 = tn - item2 * tiles_per_item;
-            const int mt2 = (rem2 / p.tiles_n) * CG + (int)rank;
-            const int lane2 = p.items[item2].a_lane;
-            for (int kb = 0; kb < kb_count; ++kb)
-              for (int pl = 0; pl < NP; ++pl)
-                tma_prefetch_4d(&p.mapA, kb * (ROWB / T::ESZ), mt2 * BM, pl, lane2);
-          }
-        }
+        const int tau = block_variant(*si.bits, p.sh);
         bool ok = true;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % S;
@@ -499,8 +478,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       if (item != cached_item) {
         cached_item = item;
         si = &p.items[item];
-        const int tau = (int)((*si->bits >> p.sh.q) & 1ull);
-        op = &p.ops[si->op_base + tau];
+        op = &p.ops[si->op_base + block_variant(*si->bits, p.sh)];
         const bool unit_in = si->in_rec < 0;
         const float mu = unit_in ? 1.f : __uint_as_float(p.recs[si->in_rec].maxbits);
         s_in = unit_in ? 0 : p.recs[si->in_rec].exp;
@@ -650,7 +628,7 @@ struct TcLaunchData {
 };
 
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
-               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[2][2],
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[4][2],
                int kchunk, int cluster, void **out_handle) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
@@ -689,7 +667,12 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   // The 2-SM UMMA when the 128-row tiles pair up and each CTA's half of the
   // Bt tile is a whole number of 8-row swizzle groups.
   d->cg = ((BN / 2) % 8 == 0 && tiles_m % 2 == 0 && cluster != 1) ? 2 : 1;
-  for (int t = 0; t < 2; ++t)
+  const int nvar = 1 << sh.nq;
+  if (nvar > 4) {
+    delete d;
+    return -6;
+  }
+  for (int t = 0; t < nvar; ++t)
     for (int pl = 0; pl < np; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)Kr, (cuuint64_t)Nr};
       cuuint64_t strides[1] = {(cuuint64_t)Kr * esz};
@@ -711,7 +694,8 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   while (cols < 2 * BN) cols *= 2;
   d->prm.tmem_cols = cols;
   const int stage_bytes = np * (BM + BN / d->cg) * rowb;  // this CTA's share
-  const int budget = 220 * 1024 - 1024 - 256;
+  // 227 KiB per CTA, less the 1 KiB alignment pad and the barriers
+  const int budget = 227 * 1024 - 1024 - 256;
   int stages = budget / stage_bytes;
   if (stages > 8) stages = 8;
   d->prm.stages = stages;
@@ -843,9 +827,8 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
 // into the form's planes, K-major [Nr][Kr].  Also the bound beta_t.
 // ---------------------------------------------------------------------------
 template <int FMT>
-__global__ void k_build_bt(const OpBuildEntry *__restrict__ entries, OpDesc *ops) {
-  const OpBuildEntry &g = entries[blockIdx.y];
-  OpDesc &op = ops[g.op];
+__global__ void k_build_bt(OpDesc *ops) {
+  OpDesc &op = ops[blockIdx.y];
   if (op.Bt[0] == nullptr) return;
   const int K = op.K, N = op.N;
   const int Kr = 2 * K, Nr = 2 * N;
@@ -882,19 +865,19 @@ __global__ void k_build_bt(const OpBuildEntry *__restrict__ entries, OpDesc *ops
   }
 }
 
-cudaError_t launch_build_tc_operands(const OpBuildEntry *d_entries, int n, int max_kn,
-                                     OpDesc *d_ops, int fmt, cudaStream_t s) {
+cudaError_t launch_build_tc_operands(int n, int max_kn, OpDesc *d_ops, int fmt,
+                                     cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int blocks = (4 * max_kn + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
   dim3 grid(blocks, n);
   switch (fmt) {
-    case FMT_TF32: k_build_bt<FMT_TF32><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
-    case FMT_BF16: k_build_bt<FMT_BF16><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
-    case FMT_FP16: k_build_bt<FMT_FP16><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
-    case FMT_BF16X2: k_build_bt<FMT_BF16X2><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
-    case FMT_FP16X2: k_build_bt<FMT_FP16X2><<<grid, 256, 0, s>>>(d_entries, d_ops); break;
+    case FMT_TF32: k_build_bt<FMT_TF32><<<grid, 256, 0, s>>>(d_ops); break;
+    case FMT_BF16: k_build_bt<FMT_BF16><<<grid, 256, 0, s>>>(d_ops); break;
+    case FMT_FP16: k_build_bt<FMT_FP16><<<grid, 256, 0, s>>>(d_ops); break;
+    case FMT_BF16X2: k_build_bt<FMT_BF16X2><<<grid, 256, 0, s>>>(d_ops); break;
+    case FMT_FP16X2: k_build_bt<FMT_FP16X2><<<grid, 256, 0, s>>>(d_ops); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -26,6 +26,15 @@ __device__ __forceinline__ int deposit_bits(uint32_t v, uint32_t mask) {
   return (int)out;
 }
 
+// Full-index position of E[l][r][u][d] (restricted indices mapped back).
+__device__ __forceinline__ int64_t pos_E(const OpBuildEntry &g, int l_, int r_, int u_, int d_) {
+  const int l = (int)g.fixed_val[0] | deposit_bits(l_, g.free_mask[0]);
+  const int r = (int)g.fixed_val[1] | deposit_bits(r_, g.free_mask[1]);
+  const int u = (int)g.fixed_val[2] | deposit_bits(u_, g.free_mask[2]);
+  const int d = (int)g.fixed_val[3] | deposit_bits(d_, g.free_mask[3]);
+  return ((((int64_t)g.tau * g.dims[0] + l) * g.dims[1] + r) * g.dims[2] + u) * g.dims[3] + d;
+}
+
 __device__ __forceinline__ float2 fetch_E(const OpBuildEntry &g, int k, int n) {
   const int rl = g.rdims[0], rr = g.rdims[1], ru = g.rdims[2], rd = g.rdims[3];
   (void)rl; (void)rr;
@@ -58,27 +67,120 @@ __global__ void k_build_ec(const OpBuildEntry *__restrict__ entries, OpDesc *ops
   }
 }
 
-// beta = max_n sum_k (|Re E_kn| + |Im E_kn|): the factor by which one
-// absorption can grow max(|Re|, |Im|) of the running tensor.
-__global__ void k_beta(const OpBuildEntry *__restrict__ entries, OpDesc *ops) {
-  const OpBuildEntry &g = entries[blockIdx.y];
+// ---- float-float helpers (as in the evolution kernels) ----
+struct ff2 {
+  float hi, lo;
+};
+__device__ __forceinline__ ff2 ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff2 ff_fast(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff2 ffadd(ff2 x, ff2 y) {
+  ff2 s = ff_two_sum(x.hi, y.hi);
+  s.lo += x.lo + y.lo;
+  return ff_fast(s.hi, s.lo);
+}
+__device__ __forceinline__ ff2 ffmul(ff2 x, ff2 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return ff_fast(p, e);
+}
+
+// Two-site block operand W (see OpBuild2Entry), summed over the internal
+// vertical bond in float-float from the float-float site tensors, rounded
+// once to FP32.  k = (l_a * Lb + l_b) * Ua + u_a, n = (r_a * Rb + r_b) * Db + d_b.
+__global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *ops) {
+  const OpBuild2Entry &g = entries[blockIdx.y];
   OpDesc &op = ops[g.op];
-  const int K = g.rdims[0] * g.rdims[2];
-  const int N = g.rdims[1] * g.rdims[3];
-  float best = 0.f;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < K; ++k) {
-      float2 v = op.Ec[(int64_t)k * N + n];
-      s += fabsf(v.x) + fabsf(v.y);
-    }
-    best = fmaxf(best, s);
+  const int La = g.a.rdims[0], Ra = g.a.rdims[1], Ua = g.a.rdims[2], Mid = g.a.rdims[3];
+  const int Lb = g.b.rdims[0], Rb = g.b.rdims[1], Db = g.b.rdims[3];
+  const int K = La * Lb * Ua, N = Ra * Rb * Db;
+  if (blockIdx.x * blockDim.x >= K * N) return;
+  // full index of every restricted value of the shared bond, on both sites
+  __shared__ int mid_a[kMaxMid], mid_b[kMaxMid];
+  for (int m = threadIdx.x; m < Mid; m += blockDim.x) {
+    mid_a[m] = (int)g.a.fixed_val[3] | deposit_bits(m, g.a.free_mask[3]);
+    mid_b[m] = (int)g.b.fixed_val[2] | deposit_bits(m, g.b.free_mask[2]);
   }
-  // Round the bound up slightly so that fp32 summation order cannot make it
-  // smaller than the exact sum.
-  best *= 1.0f + 1.0f / 256.0f;
-  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(&op.beta_c_bits, __float_as_uint(best));
+  __syncthreads();
+  float2 *Ec = const_cast<float2 *>(op.Ec);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    op.beta_c_bits = 0u;
+    op.beta_t_bits = 0u;
+  }
+  const float2 *__restrict__ Aa = g.a.A;
+  const float2 *__restrict__ Ab = g.b.A;
+  const int64_t loa = g.a.lo_off, lob = g.b.lo_off;
+  const int b_du = g.b.dims[3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
+    const int k = i / N, n = i - k * N;
+    const int ua = k % Ua, lb = (k / Ua) % Lb, la = k / (Ua * Lb);
+    const int db = n % Db, rb = (n / Db) % Rb, ra = n / (Db * Rb);
+    const int64_t pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0];   // d leg (fastest) = 0
+    const int64_t pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_du;
+    ff2 re = {0.f, 0.f}, im = {0.f, 0.f};
+    for (int m = 0; m < Mid; ++m) {
+      const int64_t pa = pa0 + mid_a[m], pb = pb0 + (int64_t)mid_b[m] * b_du;
+      const float2 ah = Aa[pa], al = Aa[loa + pa];
+      const float2 bh = Ab[pb], bl = Ab[lob + pb];
+      const ff2 ar = {ah.x, al.x}, ai = {ah.y, al.y}, br = {bh.x, bl.x}, bi = {bh.y, bl.y};
+      re = ffadd(re, ffadd(ffmul(ar, br), ffmul({-ai.hi, -ai.lo}, bi)));
+      im = ffadd(im, ffadd(ffmul(ar, bi), ffmul(ai, br)));
+    }
+    Ec[i] = make_float2(re.hi + re.lo, im.hi + im.lo);
+  }
+}
+
+// beta = max_n sum_k (|Re E_kn| + |Im E_kn|) of every op (the factor by
+// which one absorption can grow max(|Re|, |Im|) of the running tensor); one
+// block row per op, after the builders.  A block takes 32 columns at a time,
+// its 32 warps splitting K; the column sums meet in shared memory.
+__global__ void __launch_bounds__(1024) k_beta_ops(OpDesc *ops) {
+  const OpDesc &op = ops[blockIdx.y];
+  if (op.Ec == nullptr) return;
+  const int K = op.K, N = op.N;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ float part[32][33];
+  float best = 0.f;
+  for (int n0 = blockIdx.x * 32; n0 < N; n0 += gridDim.x * 32) {
+    const int n = n0 + lane;
+    float s = 0.f;
+    if (n < N)
+      for (int k = w; k < K; k += 32) {
+        const float2 v = op.Ec[(int64_t)k * N + n];
+        s += fabsf(v.x) + fabsf(v.y);
+      }
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0) {
+      float t = 0.f;
+      for (int j = 0; j < 32; ++j) t += part[j][lane];
+      best = fmaxf(best, t);
+    }
+    __syncthreads();
+  }
+  if (w == 0) {
+    best *= 1.0f + 1.0f / 256.0f;
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) atomicMax(&ops[blockIdx.y].beta_c_bits, __float_as_uint(best));
+  }
+}
+
+cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
+                                   OpDesc *d_ops, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (max_kn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (blocks < 1) blocks = 1;
+  k_build_ec2<<<dim3(blocks, n), 256, 0, s>>>(d_entries, d_ops);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
@@ -88,9 +190,12 @@ cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
   k_build_ec<<<dim3(blocks, n), 256, 0, s>>>(d_entries, d_ops);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_beta<<<dim3(4, n), 256, 0, s>>>(d_entries, d_ops);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s) {
+  if (n_ops <= 0) return cudaSuccess;
+  k_beta_ops<<<dim3(8, n_ops), 1024, 0, s>>>(d_ops);
   return cudaGetLastError();
 }
 

@@ -87,19 +87,47 @@ def test_bond_dims_follow_cz_counts(R, C, d):
 
 def test_plan_counts_match_cost_model():
     c, h = make(6, 6, 32, 4)
-    o, k = B.make_opts(precision="fp32")
+    o, k = B.make_opts(precision="fp32", fuse_rows=1)
     info = B.peps_plan_info_get(h, 1, o)
     assert info["n_steps"] == 36
     assert info["max_entries"] == 16 ** 7
     assert info["flops_per_chain"] == 8 * cx.column_sweep_cmacs(6, 6, 16)
     # prefix reuse: 8 groups x 64, first 3 columns shared
-    o, k = B.make_opts(precision="fp32", prefix_cols=3, prefix_group=64)
+    o, k = B.make_opts(precision="fp32", prefix_cols=3, prefix_group=64, fuse_rows=1)
     info = B.peps_plan_info_get(h, 512, o)
     steps = cx.column_sweep_step_cmacs(6, 6, 16)
     # the first 3 columns are contracted once per group, the rest per bitstring
     assert info["flops_call"] == 8 * (8 * sum(steps[:18]) + 512 * sum(steps[18:]))
     assert info["n_launches"] == 8 * 18 + 8 * 4 * 18   # 16 lanes per launch
     B.peps_destroy(h)
+
+
+def test_fused_boundary_rows_plan():
+    # the two top and the two bottom rows of each column in one step each
+    c, h = make(6, 6, 32, 4)
+    o1, k1 = B.make_opts(precision="fp16x3", fuse_rows=1)
+    o0, k0 = B.make_opts(precision="fp16x3")
+    single = B.peps_plan_info_get(h, 1, o1)
+    fused = B.peps_plan_info_get(h, 1, o0)
+    blocks = cx.column_sweep_block_cmacs(6, 6, 16)
+    # the last column's bottom pair would be one long dot product: kept single
+    assert [k for _, k, _ in blocks] == [2, 1, 1, 2] * 5 + [2, 1, 1, 1, 1]
+    assert single["n_steps"] == 36 and fused["n_steps"] == len(blocks) == 25
+    assert fused["max_entries"] == single["max_entries"]
+    assert fused["flops_per_chain"] == 8 * sum(m for _, _, m in blocks)
+    assert fused["flops_per_chain"] < single["flops_per_chain"]
+    # the running tensor between the two rows of a pair is never written
+    assert fused["bytes_per_chain"] < 0.65 * single["bytes_per_chain"]
+    B.peps_destroy(h)
+
+
+def test_fusion_needs_four_rows():
+    for R, C in ((2, 5), (3, 4)):
+        c, h = make(R, C, 10, 3)
+        o, k = B.make_opts(precision="fp32")
+        info = B.peps_plan_info_get(h, 1, o)
+        assert info["n_steps"] == R * C
+        B.peps_destroy(h)
 
 
 def test_slicing_plan():

@@ -261,8 +261,13 @@ def test_timing_and_launch_counters(sim_factory):
     sim = sim_factory(circ)
     sim.amplitudes(bits[:32], precision="fp32", flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
     st = sim.stats()
+    ns = sim.plan_info(32, precision="fp32")["n_steps"]
+    assert 10 <= ns < 25   # some boundary row pairs absorbed together
     assert st["contract_ms"] > 0
-    assert st["launches_contract"] == 25 * 2   # 2 lane chunks of 16, 25 steps
+    assert st["launches_contract"] == ns * 2   # 2 lane chunks of 16
+    sim.amplitudes(bits[:32], precision="fp32", fuse_rows=1,
+                   flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
+    assert sim.stats()["launches_contract"] == 25 * 2   # one site per step
     assert st["launches_evolve"] > 10
     assert st["launches_total"] >= st["launches_contract"] + st["launches_evolve"]
 
@@ -276,4 +281,33 @@ def test_cuda_graph_replay_matches_eager(sim_factory, prec):
     g2 = sim.amplitudes(bits[:40], precision=prec, flags=B.PEPS_FLAG_GRAPH)   # replay
     assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
     st = sim.stats()
-    assert st["launches_contract"] == 25 * 3   # 40 bitstrings in lanes of 16
+    ns = sim.plan_info(40, precision=prec)["n_steps"]
+    assert st["launches_contract"] == ns * 3   # 40 bitstrings in lanes of 16
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3", "bf16x3"])
+def test_fused_rows_match_single_sites(sim_factory, prec):
+    # absorbing the boundary row pairs together reorders sums only
+    circ, bits = workload("5x5_d16")
+    bits = bits[:48]
+    sim = sim_factory(circ)
+    ref = op.amplitudes(op.build(5, 5, circ.gates), bits)
+    fused = sim.amplitudes(bits, precision=prec)
+    single = sim.amplitudes(bits, precision=prec, fuse_rows=1)
+    tol = tol_for(prec, 25)
+    assert relerr(fused, ref) < tol and relerr(single, ref) < tol
+    assert relerr(fused, single) < tol
+
+
+def test_fused_rows_with_prefix_and_slices(sim_factory):
+    from rqc_inputs import prefix_group_bitstrings
+
+    circ = make_circuit(6, 5, 12, 11)
+    bits = prefix_group_bitstrings(6, 5, 2, 2, 24, 11)
+    sim = sim_factory(circ)
+    ref = op.amplitudes(op.build(6, 5, circ.gates), bits)
+    for kw in ({}, {"prefix_cols": 2, "prefix_group": 24, "max_lanes": 8},
+               {"sliced_cz": [1, 9, 30]}):
+        for prec in ("fp32", "fp16x3"):
+            a = sim.amplitudes(bits, precision=prec, **kw)
+            assert relerr(a, ref) < SPLIT_TOL, (kw, prec)

@@ -27,7 +27,7 @@ def test_budget_and_planner_agree(name, budget):
     ss = slicing.choose(circ, budget, seed=5)
     assert ss.max_entries <= budget
     h = ctx_for(circ)
-    o, keep = B.make_opts(precision="fp16x3", sliced_cz=ss.sliced_cz, slice_ids=[0])
+    o, keep = B.make_opts(precision="fp16x3", sliced_cz=ss.sliced_cz, slice_ids=[0], fuse_rows=1)
     info = B.peps_plan_info_get(h, 1, o)
     assert info["max_entries"] == ss.max_entries
     assert info["flops_per_chain"] == 8 * sum(ss.step_cmacs)
@@ -44,7 +44,8 @@ def test_sub_slice_as_slice_plus_fixed_bits():
     assert len(sub.sliced_cz) > 62
     h = ctx_for(circ)
     o, keep = B.make_opts(precision="fp16x3", sliced_cz=ss.sliced_cz, slice_ids=[7],
-                          fixed_cz=extra, fixed_s=[1, 0] * (len(extra) // 2) + [1] * (len(extra) % 2))
+                          fixed_cz=extra, fixed_s=[1, 0] * (len(extra) // 2) + [1] * (len(extra) % 2),
+                          fuse_rows=1)
     info = B.peps_plan_info_get(h, 1, o)
     assert info["max_entries"] == sub.max_entries
     assert info["flops_per_chain"] == 8 * sum(sub.step_cmacs)
