@@ -5,8 +5,9 @@ Workload: the 6x6 lattice at depth (1+32+1) (bond dimension 16 on every
 edge), 512 seeded bitstrings in 8 groups of 64 that share the bits of columns
 0-2, whose running tensor after column 2 is computed once per group.  One
 step = the whole path over the batch: circuit evolution (PEPS init, gate
-absorption), projection / operand build, the 36 site absorptions of every
-chain, FP64 reduction.
+absorption), projection / operand build, the 25 absorption steps of every
+chain (36 sites; the two top and two bottom rows of a column are absorbed
+together where that pays), FP64 reduction.
 
 value   amplitudes/s of the mixed-precision path (FP16 hi/lo split, three
         tensor-core products, FP32 accumulate), bitstrings resident in HBM,
@@ -17,7 +18,10 @@ fp32_path  the plain FP32 CUDA-core form on the same GPU (timed on one group
         of 64 bitstrings; the work per amplitude is identical across groups).
 roofline  the tensor-core contraction kernel: algorithmic flops per launch
         (8 real flops per complex multiply-add) / mean launch time from CUDA
-        events recorded by the library around each launch.
+        events recorded by the library around each launch.  `traffic` is the
+        mean DRAM bytes (read + write) per launch of this kernel in a
+        single-pass ncu capture of this bench command; it is reported only
+        while the kernel's sources hash to the captured version.
 cpu_baseline  the CPU FP64 oracle on a bounded sample (see "sample").
 
 --impl reference times the oracle (the reference arm of this build).
@@ -38,6 +42,22 @@ METRIC = "amplitudes/s at 6x6 (1+32+1), mixed vs FP32 path, rel.err <= 1e-5"
 UNIT = "amplitudes/s"
 WORKLOAD = "6x6_d32"
 FLOPS_PER_CMAC = 8
+
+# ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
+# dram__bytes_write.sum; one pass) of `bench.py --no-cpu --fp32-steps 0
+# --steps 1 --warmup 1`: mean over the 1760 k_contract_tc launches.
+TRAFFIC = {"sources_sha256_16": "f7876dc9b0386bc0", "bytes_per_launch": 36.80e9}
+TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
+
+
+def measured_traffic():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1905_08394_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sources_sha256_16"] else None
 
 
 def parse():
@@ -251,7 +271,7 @@ def run_mine(args):
     clocks = Clocks(local)
     clocks.start()
     tc_ms = tc_launches = 0.0
-    tc_flops = 0.0
+    tc_flops = tc_bytes = 0.0
     launches = 0
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
@@ -262,6 +282,7 @@ def run_mine(args):
         tc_ms += st["contract_tc_ms"]
         tc_launches += st["launches_contract_tc"]
         tc_flops += st["contract_tc_flops"]
+        tc_bytes += st["contract_tc_bytes"]
         launches += st["launches_total"]
     ev1.record(stream)
     stream.synchronize()
@@ -327,7 +348,8 @@ def run_mine(args):
     roof = None
     if achieved is not None:
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic(),
+                "algorithmic_bytes": tc_bytes / tc_launches,
                 "kernel": "k_contract_tc (tcgen05, fp16 hi/lo, 3 MMAs per k-step)",
                 "peak_source": f"{src} bf16 dense sustained (fp16 dense rate = bf16 rate)",
                 "issued_frac": 3 * achieved / peak if args.precision in ("fp16x3", "bf16x3") else None,
