@@ -72,14 +72,16 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "slices", "precision", "small"],
+                    choices=["bench", "profile", "slices", "precision", "small", "peaks"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
                          "projected full time from a seeded subset of slices; precision: "
                          "6x6 (1+24+1), every form's amplitudes/s on 4096 bitstrings and its "
                          "error against the oracle on 64; small: 4x4 (1+8+1) and 5x5 (1+16+1), "
-                         "eager launches vs CUDA-graph replay")
+                         "eager launches vs CUDA-graph replay; peaks: this GPU's FP32 FMA "
+                         "and tcgen05 kind::f16 / kind::tf32 rates from the microbenchmarks "
+                         "in libpeps_peaks.so")
     ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
@@ -338,8 +340,15 @@ def run_mine(args):
         e1.record(stream)
         stream.synchronize()
         ms32 = e0.elapsed_time(e1) / args.fp32_steps
+        fl32 = sim.plan_info(64, **kw32)["flops_call"]
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sms * 128 * 2 * 2070e6 / 1e12   # FP32 lanes x 2 flops x max SM clock
         f32 = {"value": 64 / (ms32 / 1e3), "unit": UNIT, "bitstrings": 64,
-               "ms_per_step": ms32, "note": "plain FP32 CUDA-core form, one group of 64"}
+               "ms_per_step": ms32, "note": "plain FP32 CUDA-core form, one group of 64",
+               "roofline": {"bound": "alu", "achieved": fl32 / (ms32 / 1e3) / 1e12,
+                            "peak": alu_peak, "unit": "TFLOP/s",
+                            "frac": fl32 / (ms32 / 1e3) / 1e12 / alu_peak,
+                            "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}}
 
     peaks, src = load_peaks()
     tc_avg_ms = tc_ms / tc_launches if tc_launches else None
@@ -484,6 +493,10 @@ def run_precision_case(args):
     sim.apply_circuit(circ)
     d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
     d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    peaks, src = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     rows = []
     for prec in ("fp32", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"):
         kw = dict(precision=prec, max_lanes=args.lanes, flags=B.PEPS_FLAG_REBUILD)
@@ -491,10 +504,27 @@ def run_precision_case(args):
         out = d_out.cpu().numpy()
         err = float(np.linalg.norm(out[:64] - ref) / np.linalg.norm(ref))
         pt = float(np.mean((2.0 ** 36) * np.abs(out) ** 2))
+        info = sim.plan_info(len(bits), precision=prec, max_lanes=args.lanes)
+        tf = info["flops_call"] / sec / 1e12
+        gbs = info["bytes_call"] / sec / 1e9
+        # the form's own ceilings: its tensor rate (issued = 3x useful for the split
+        # forms), or the FP32 lanes for the CUDA-core form; and HBM for the bytes
+        if prec == "fp32":
+            peak_t = sms * 128 * 2 * 2070e6 / 1e12
+        elif prec == "tf32":
+            peak_t = bf16_peak * 1100.0 / 2250.0
+        else:
+            peak_t = bf16_peak
+        issued = 3 if prec in ("bf16x3", "fp16x3") else 1
         rows.append({"precision": prec, "amplitudes_per_s": len(bits) / sec, "rel_err": err,
-                     "mean_N_abs2": pt})
+                     "mean_N_abs2": pt, "useful_tflops": tf, "algorithmic_gbs": gbs,
+                     "compute_frac": issued * tf / peak_t, "hbm_frac": gbs / hbm_peak})
     print(json.dumps({"case": "precision", "workload": "6x6 (1+24+1), 4096 bitstrings",
-                      "oracle_bitstrings": 64, "forms": rows}), flush=True)
+                      "oracle_bitstrings": 64, "forms": rows,
+                      "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops_sustained": bf16_peak,
+                                "tf32": "bf16 x 1100/2250 (nominal ratio)",
+                                "fp32": "SMs x 128 lanes x 2 flops x 2070 MHz",
+                                "source": src}}), flush=True)
     sim.close()
 
 
@@ -526,6 +556,47 @@ def run_small_case(args):
     print(json.dumps({"case": "small", "results": out}), flush=True)
 
 
+def run_peaks_case(args):
+    """Peak rates measured by this repository's own microbenchmarks: the FP32
+    FMA rate of the CUDA cores and the dense tcgen05 rate for kind::f16 and
+    kind::tf32 (operands in shared memory, no DRAM traffic), with the clocks
+    seen meanwhile and the nominal figures they compare to."""
+    import ctypes as ct
+
+    import torch
+
+    lib = ct.CDLL(os.path.join(ROOT, "paper_1905_08394_gb300", "libpeps_peaks.so"))
+    for f in (lib.peaks_fma_tflops, lib.peaks_mma_tflops):
+        f.restype = ct.c_int
+    torch.cuda.init()
+    props = torch.cuda.get_device_properties(0)
+    clocks = Clocks(0)
+    clocks.start()
+    res = {}
+    for name, call in (("fp32_fma", lambda t, m: lib.peaks_fma_tflops(1000000, t, m)),
+                       ("tcgen05_f16", lambda t, m: lib.peaks_mma_tflops(0, 200000, t, m)),
+                       ("tcgen05_tf32", lambda t, m: lib.peaks_mma_tflops(1, 100000, t, m))):
+        best = 0.0
+        for _ in range(3):
+            t, ms = ct.c_double(0), ct.c_double(0)
+            rc = call(ct.byref(t), ct.byref(ms))
+            if rc != 0:
+                raise RuntimeError(f"{name}: microbenchmark failed ({rc})")
+            best = max(best, t.value)
+        res[name] = best
+    clk = clocks.stop()
+    sms = props.multi_processor_count
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    peaks, src = load_peaks()
+    print(json.dumps({
+        "case": "peaks", "sms": sms, "tflops": res, "clocks": clk,
+        "nominal_tflops": {"fp32_fma": sms * 128 * 2 * mhz * 1e6 / 1e12,
+                           "f16_dense": 2250.0, "tf32_dense": 1100.0},
+        "cublas_bf16_tflops": {"burst": peaks.get("bf16_tflops"),
+                               "sustained": peaks.get("bf16_tflops_sustained"), "source": src},
+    }), flush=True)
+
+
 def main():
     args = parse()
     if args.case == "profile":
@@ -534,6 +605,8 @@ def main():
         run_slices_case(args)
     elif args.case == "precision":
         run_precision_case(args)
+    elif args.case == "peaks":
+        run_peaks_case(args)
     elif args.case == "small":
         run_small_case(args)
     elif args.impl == "reference":

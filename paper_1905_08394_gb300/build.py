@@ -1,6 +1,7 @@
 """Build of libpeps_gb300.so: every CUDA translation unit compiled for sm_103a
 with nvcc (in parallel), linked into one shared library inside the package
-directory.  No cmake, no torch extension machinery."""
+directory.  The peak-rate microbenchmarks (csrc/peaks.cu) go into a library of
+their own, libpeps_peaks.so.  No cmake, no torch extension machinery."""
 from __future__ import annotations
 
 import os
@@ -14,6 +15,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = PKG / "libpeps_gb300.so"
+PEAKS_LIB = PKG / "libpeps_peaks.so"
+PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "evolve.cu", "operands.cu", "contract_simt.cu", "contract_tc.cu",
            "finalize.cu", "noalloc.cu"]
@@ -40,16 +43,18 @@ def _compile(src: str, extra: list[str]) -> Path:
 def build(verbose: bool = False, extra: list[str] | None = None) -> Path:
     BUILD.mkdir(exist_ok=True)
     extra = list(extra or [])
-    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB.with_suffix(".so.tmp")
-    cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcuda"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    if verbose:
-        print(f"built {LIB}", file=sys.stderr)
+    srcs = SOURCES + PEAKS_SOURCES
+    with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+        objs = dict(zip(srcs, ex.map(lambda s: _compile(s, extra), srcs)))
+    for lib, names, libs in ((LIB, SOURCES, ["-lcuda"]), (PEAKS_LIB, PEAKS_SOURCES, [])):
+        tmp = lib.with_suffix(".so.tmp")
+        cmd = [nvcc(), *ARCH, "-shared", "-o", str(tmp), *(str(objs[n]) for n in names), *libs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {lib.name} failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+        if verbose:
+            print(f"built {lib}", file=sys.stderr)
     return LIB
 
 

@@ -29,6 +29,15 @@ def test_library_exports_every_declared_function():
     assert "sm_103a" in B.peps_version()
 
 
+def test_peak_microbenchmark_library_loads():
+    # measurement only (bench.py --case peaks); kept out of the amplitude library
+    import ctypes
+
+    lib = ctypes.CDLL(str(ROOT / "paper_1905_08394_gb300" / "libpeps_peaks.so"))
+    assert hasattr(lib, "peaks_fma_tflops") and hasattr(lib, "peaks_mma_tflops")
+    assert not hasattr(B.load(), "peaks_fma_tflops")
+
+
 def make(R, C, d, seed):
     c = make_circuit(R, C, d, seed)
     h = B.peps_create(R, C)
