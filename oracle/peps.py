@@ -26,6 +26,13 @@ Follows the paper step by step, in plain NumPy (complex128):
   the paper allows when the lattice is wider than tall).  Each absorption is
   one np.tensordot over the legs the running tensor shares with the site.
 
+* Square partition (supplementary, Fig. S2(b) and the "spacesquareeven" /
+  "timesquareeven" equations), for even side lengths: the lattice is split
+  into four quarters; each quarter's projected sites are contracted into one
+  tensor (F_ul, F_ur, F_bl, F_br) whose open legs are the edges it shares with
+  its neighbouring quarters; then F_ul is contracted with F_ur and F_bl with
+  F_br, and the two results with each other.
+
 Slicing (the paper's "cut" technique, named as future work in its
 conclusions): fixing the Schmidt index s of chosen CZ gates replaces that
 gate by its single term U_s (x) V_s with no bond growth; the amplitude is the
@@ -253,6 +260,100 @@ def amplitudes_with_prefix(peps: PEPS, bitstrings, prefix_cols: int) -> np.ndarr
         G, _ = contract(E, R, C, "column", state=cache[key], sites=post_sites)
         out[i] = complex(G.reshape(-1)[0])
     return out
+
+
+def quadrant_sites(R: int, C: int):
+    """The four quarters of an even R x C lattice (supplementary Fig. S2(b)):
+    {"ul", "ur", "bl", "br"} -> their sites in contraction order.  Every
+    quarter is contracted row by row starting from its corner of the lattice
+    (the upper-left quarter's order, mirrored), so the open legs toward the
+    other quarters appear last and every quarter costs the same."""
+    if R % 2 or C % 2:
+        raise ValueError("the square partition needs even side lengths")
+    h, w = R // 2, C // 2
+    out = {}
+    for name, rows, cols in (("ul", range(0, h), range(0, w)),
+                             ("ur", range(0, h), range(C - 1, w - 1, -1)),
+                             ("bl", range(R - 1, h - 1, -1), range(0, w)),
+                             ("br", range(R - 1, h - 1, -1), range(C - 1, w - 1, -1))):
+        out[name] = [r * C + c for r in rows for c in cols]
+    return out
+
+
+def merge(a, b):
+    """Contract two labelled tensors (G, labels) over every label they share."""
+    (ga, la), (gb, lb) = a, b
+    shared = [lab for lab in la if lab in lb]
+    G = np.tensordot(ga, gb, axes=([la.index(s) for s in shared], [lb.index(s) for s in shared]))
+    return G, [lab for lab in la if lab not in shared] + [lab for lab in lb if lab not in shared]
+
+
+def amplitude_quadrant(peps: PEPS, x: int) -> complex:
+    """The amplitude by the square partition of Fig. S2(b): the four quarter
+    tensors, then upper-left with upper-right and bottom-left with
+    bottom-right, then the two halves."""
+    R, C = peps.R, peps.C
+    E = peps.project(x)
+    F = {name: contract(E, R, C, sites=sites) for name, sites in quadrant_sites(R, C).items()}
+    upper = merge(F["ul"], F["ur"])
+    lower = merge(F["bl"], F["br"])
+    G, _ = merge(upper, lower)
+    assert G.size == 1
+    return complex(G.reshape(-1)[0])
+
+
+def amplitudes_quadrant(peps: PEPS, bitstrings) -> np.ndarray:
+    return np.array([amplitude_quadrant(peps, int(x)) for x in bitstrings], dtype=np.complex128)
+
+
+def quadrant_contraction_cmacs(R: int, C: int, dims) -> dict:
+    """Complex multiply-adds of the square partition, counted directly from
+    the bond dimensions dims[(q0, q1)] (no formula): every contraction of two
+    tensors costs prod(legs of the first) x prod(legs of the second not
+    contracted).  Returns {"quarters": .., "merges": .., "largest": entries}."""
+    def legdims(q):
+        r, c = divmod(q, C)
+        out = []
+        for lab in _leg_labels(R, C, q):
+            if lab[0] == "h":
+                a = lab[1] * C + lab[2]
+                out.append((lab, dims[(a, a + 1)]))
+            elif lab[0] == "v":
+                a = lab[1] * C + lab[2]
+                out.append((lab, dims[(a, a + C)]))
+            else:
+                out.append((lab, 1))
+        return out
+
+    def cost(la, lb):
+        shared = [k for k in la if k in lb]
+        c = 1
+        for k in la:
+            c *= la[k]
+        for k in lb:
+            if k not in shared:
+                c *= lb[k]
+        out = {k: v for k, v in la.items() if k not in shared}
+        out.update({k: v for k, v in lb.items() if k not in shared})
+        return c, out
+
+    quarters, largest, F = 0, 1, {}
+    for name, sites in quadrant_sites(R, C).items():
+        G = {}
+        for q in sites:
+            c, G = cost(G, dict(legdims(q)))
+            quarters += c
+            largest = max(largest, int(np.prod(list(G.values()))))
+        F[name] = G
+    merges = 0
+    c, up = cost(F["ul"], F["ur"])
+    merges += c
+    c, lo = cost(F["bl"], F["br"])
+    merges += c
+    largest = max(largest, int(np.prod(list(up.values()))), int(np.prod(list(lo.values()))))
+    c, _ = cost(up, lo)
+    merges += c
+    return {"quarters": quarters, "merges": merges, "largest": largest}
 
 
 def column_contraction_cmacs(R: int, C: int, dims) -> int:

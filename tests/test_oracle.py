@@ -230,6 +230,60 @@ def test_prefix_reuse_equals_plain():
 
 
 # ---------------------------------------------------------------------------
+# Square partition (supplementary Fig. S2(b)): brute force against the state
+# vector, equality with the column sweep, and the paper's complexity.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R,C,d,seed", [(2, 2, 8, 1), (2, 4, 16, 2), (4, 2, 16, 3),
+                                        (4, 4, 8, 4)])
+def test_quadrant_equals_statevector(R, C, d, seed):
+    c = make_circuit(R, C, d, seed)
+    n = R * C
+    x = np.arange(1 << n, dtype=np.uint64) if n <= 12 else uniform_bitstrings(n, 256, seed)
+    ref = sv.amplitudes(n, c.gates, x)
+    a = op.amplitudes_quadrant(op.build(R, C, c.gates), x)
+    assert np.abs(a - ref).max() < 1e-13
+
+
+def test_quadrant_equals_column_sweep_6x6():
+    c = make_circuit(6, 6, 16, 3)
+    x = uniform_bitstrings(36, 4, 3)
+    p = op.build(6, 6, c.gates)
+    a, b = op.amplitudes_quadrant(p, x), op.amplitudes(p, x)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+def test_quadrant_needs_even_sides():
+    with pytest.raises(ValueError):
+        op.quadrant_sites(5, 6)
+
+
+@pytest.mark.parametrize("L,d", [(6, 32), (8, 40), (6, 24)])
+def test_quadrant_cost_matches_the_paper(L, d):
+    # Eq. (timesquareeven): 2^(3 k L / 2 + 1) multiply-adds for the merges, k = ceil(d/8);
+    # Eq. (spacesquareeven): 2^(k L + 1) entries, two quarter-pair tensors of chi^L
+    from paper_1905_08394_gb300 import complexity as cx
+    k = -(-d // 8)
+    chi = 2 ** k
+    dims = {}
+    for r in range(L):
+        for cc in range(L):
+            q = r * L + cc
+            if cc + 1 < L:
+                dims[(q, q + 1)] = chi
+            if r + 1 < L:
+                dims[(q, q + L)] = chi
+    cost = op.quadrant_contraction_cmacs(L, L, dims)
+    # the two pair merges give the formula; the last merge adds chi^L
+    assert cost["merges"] == cx.time_square_even(L, d) + chi ** L
+    assert 2 * cost["largest"] == cx.space_square_even(L, d)
+    # at L = 6 it also undercuts the column sweep's Eq. (time) (at L = 8, k = 5 the
+    # partition saves memory, 2^41 vs 2^45 entries, but not time)
+    if L == 6:
+        assert cost["merges"] + cost["quarters"] < cx.time_generic(L, L, d) / 4
+
+
+# ---------------------------------------------------------------------------
 # Planted mistakes: each must be caught by one of the pins above.
 # ---------------------------------------------------------------------------
 
@@ -268,6 +322,25 @@ def test_planted_wrong_bundling_in_peps_is_caught(monkeypatch):
     x = uniform_bitstrings(9, 64, 4)
     ref = sv.amplitudes(9, c.gates, x)
     a = op.amplitudes(op.build(3, 3, c.gates), x)
+    assert np.abs(a - ref).max() > 1e-3
+
+
+def test_planted_overlapping_quarters_are_caught(monkeypatch):
+    # one site counted in two quarters (and missing from its own)
+    orig = op.quadrant_sites
+
+    def bad(R, C):
+        q = orig(R, C)
+        q["ur"] = q["ur"][:-1] + [q["ul"][0]]
+        return q
+    monkeypatch.setattr(op, "quadrant_sites", bad)
+    c = make_circuit(4, 4, 8, 4)
+    x = uniform_bitstrings(16, 32, 4)
+    ref = sv.amplitudes(16, c.gates, x)
+    try:
+        a = op.amplitudes_quadrant(op.build(4, 4, c.gates), x)
+    except AssertionError:
+        return                      # caught: open legs are left over
     assert np.abs(a - ref).max() > 1e-3
 
 
