@@ -72,7 +72,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "slices", "precision", "small", "peaks"],
+                    choices=["bench", "profile", "slices", "precision", "small", "peaks",
+                             "quadrants"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
@@ -81,7 +82,8 @@ def parse():
                          "error against the oracle on 64; small: 4x4 (1+8+1) and 5x5 (1+16+1), "
                          "eager launches vs CUDA-graph replay; peaks: this GPU's FP32 FMA "
                          "and tcgen05 kind::f16 / kind::tf32 rates from the microbenchmarks "
-                         "in libpeps_peaks.so")
+                         "in libpeps_peaks.so; quadrants: the bench workload by the square "
+                         "partition of the lattice (supplementary Fig. S2(b))")
     ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
@@ -556,6 +558,53 @@ def run_small_case(args):
     print(json.dumps({"case": "small", "results": out}), flush=True)
 
 
+def run_quadrants_case(args):
+    """The bench workload (6x6 (1+32+1), 512 bitstrings in 8 groups of 64
+    sharing columns 0-2) contracted by the square partition: per group the
+    two left quarters and F_l = F_ul F_bl^T, per bitstring the two right
+    quarters, Y = F_br F_l^T and the dot product with F_ur.  Amplitudes/s of
+    the FP16X3 and FP32 forms, and the tensor-core roofline of the merges."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload(WORKLOAD)
+    sim = Simulator(circ.R, circ.C)
+    sim.apply_circuit(circ)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    peaks, src = load_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    clocks = Clocks(0)
+    clocks.start()
+    res = {}
+    for prec, reps in ((args.precision, max(1, args.steps)), ("fp32", 1)):
+        kw = dict(precision=prec, prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
+                  scheme="quadrants")
+        sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, flags=B.PEPS_FLAG_REBUILD,
+                                                        **kw), reps)
+        sim.amplitudes_device(d_bits, d_out, flags=B.PEPS_FLAG_TIMING, **kw)
+        torch.cuda.synchronize()
+        st = sim.stats()
+        info = sim.plan_info(len(bits), **kw)
+        r = {"amplitudes_per_s": len(bits) / sec, "ms_per_call": sec * 1e3,
+             "useful_tflops": info["flops_call"] / sec / 1e12,
+             "launches": st["launches_total"]}
+        if st["launches_contract_tc"]:
+            ach = st["contract_tc_flops"] / (st["contract_tc_ms"] / 1e3) / 1e12
+            r["tc_roofline"] = {"achieved": ach, "peak": bf16, "frac": ach / bf16,
+                                "issued_frac": 3 * ach / bf16 if prec in ("fp16x3", "bf16x3") else None}
+        res[prec] = r
+    clk = clocks.stop()
+    print(json.dumps({"case": "quadrants", "workload": "6x6 (1+32+1), 512 bitstrings = 8 groups "
+                      "x 64 sharing columns 0-2", "results": res, "clocks": clk,
+                      "peak_source": src}), flush=True)
+    sim.close()
+
+
 def run_peaks_case(args):
     """Peak rates measured by this repository's own microbenchmarks: the FP32
     FMA rate of the CUDA cores and the dense tcgen05 rate for kind::f16 and
@@ -607,6 +656,8 @@ def main():
         run_precision_case(args)
     elif args.case == "peaks":
         run_peaks_case(args)
+    elif args.case == "quadrants":
+        run_quadrants_case(args)
     elif args.case == "small":
         run_small_case(args)
     elif args.impl == "reference":

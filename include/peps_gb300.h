@@ -135,8 +135,22 @@ typedef struct {
                                  each where that costs no more multiply-adds
                                  (the running tensor between them is never
                                  stored); 1 = one site per step              */
-    int32_t pad2_;
+    int32_t scheme;           /* PEPS_SCHEME_*: the contraction scheme        */
 } peps_opts;
+
+/* Contraction schemes (supplementary, "exact contraction"):
+ *   COLUMNS   the generic scheme of Fig. S2(a), transposed: one running
+ *             tensor absorbs the lattice column by column (any R x C);
+ *   QUADRANTS the square partition of Fig. S2(b) (even R and C): each
+ *             quarter is contracted from its lattice corner into one tensor
+ *             holding the legs it shares with the other quarters; then the
+ *             left half F_l = F_ul F_bl (once per prefix group when
+ *             prefix_cols = C/2), Y = F_br F_l^T per bitstring, and the
+ *             amplitude = sum Y * F_ur.  prefix_cols must be 0 or C/2. */
+enum {
+    PEPS_SCHEME_COLUMNS = 0,
+    PEPS_SCHEME_QUADRANTS = 1
+};
 
 /* Counters of the last amplitude call (kernel launches are the library's own
  * kernels; times are CUDA-event times on the call's stream). */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,7 +53,8 @@ struct GateRec {
 };
 
 struct Launch {
-  int kind;        // 0 = contraction step, 1 = finalize
+  int kind;        // 0 = contraction step, 1 = finalize, 2 = merge operand from a
+                   // stored tensor, 3 = final dot product (square partition)
   StepShape shape;
   bool tc;
   void *tc_handle = nullptr;  // tensor maps of a tcgen05 launch
@@ -63,6 +65,10 @@ struct Launch {
   int n_items;
   int64_t fin_off;
   int n_fin;
+  int64_t aux_off = 0;  // kind 2: TensorOpEntry index; kind 3: first DotEntry
+  int n_aux = 0;
+  int op = -1;          // kind 2: the OpDesc built
+  int64_t kn = 0;       // kind 2: K * N of that operand
   double flops, bytes;
 };
 
@@ -109,6 +115,18 @@ struct Plan {
 
   // step shapes
   std::vector<StepShape> steps;
+  std::vector<std::array<int, 4>> step_roles;  // physical leg of the roles l, r, u, d
+  int scheme = PEPS_SCHEME_COLUMNS;
+  struct Quarter {
+    int first = 0, count = 0;  // its sweep's steps
+    int64_t batch = 1, rest = 1;  // stored as [batch][rest]
+  } quarter[4];                 // ul, bl, ur, br
+  int s_m1 = -1, s_m2 = -1;     // merge steps F_l = F_ul F_bl, Y = F_br F_l^T
+  int op_m1 = -1, op_m2 = -1;
+  int n_site_ops = 0;           // ops rebuilt from the site tensors per slice
+  int64_t max_kn_merge = 0;
+  size_t off_tops = 0, off_dots = 0, off_partials = 0;
+  int bufs_per_lane = 2;
   std::vector<int> step_site;
   std::vector<int> step_opbase;  // first OpDesc of each step (2^nq variants)
   int n_ops = 0;
@@ -311,7 +329,7 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
          a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
          a.n_slice_ids == b.n_slice_ids && a.n_fixed == b.n_fixed &&
          a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster &&
-         a.fuse_rows == b.fuse_rows;
+         a.fuse_rows == b.fuse_rows && a.scheme == b.scheme;
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
@@ -334,6 +352,13 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   if (o.n_slice_ids < 0) return fail(PEPS_EINVAL, "n_slice_ids < 0");
   if (o.n_fixed < 0) return fail(PEPS_EINVAL, "n_fixed < 0");
   if (o.fuse_rows < 0 || o.fuse_rows > 1) return fail(PEPS_EINVAL, "fuse_rows must be 0 or 1");
+  if (o.scheme != PEPS_SCHEME_COLUMNS && o.scheme != PEPS_SCHEME_QUADRANTS)
+    return fail(PEPS_EINVAL, "unknown contraction scheme %d", o.scheme);
+  const bool quad = o.scheme == PEPS_SCHEME_QUADRANTS;
+  if (quad && (R % 2 || C % 2))
+    return fail(PEPS_EINVAL, "the square partition needs even R and C (got %d x %d)", R, C);
+  if (quad && o.prefix_cols != 0 && o.prefix_cols != C / 2)
+    return fail(PEPS_EINVAL, "with the square partition prefix_cols must be 0 or C/2");
   if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster))
     return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128 and tc_cluster 0, 1 or 2");
   if (o.n_fixed > 0 && (!o.fixed_cz || !o.fixed_s)) return fail(PEPS_EINVAL, "fixed_cz / fixed_s is NULL");
@@ -417,113 +442,293 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     return (r < 0 || r >= R - 1) ? 1 : L.dim_v[edge_v(c, r, col)];
   };
 
-  // ---- blocks: the sites each step absorbs ----
-  // One site per step, except that (with fuse_rows == 0) the two top rows and
-  // the two bottom rows of a column are absorbed together when that costs no
-  // more multiply-adds and leaves the step enough output tiles (or no longer
-  // a K) to fill the GPU: the top pair has no incoming vertical leg and the
-  // bottom pair no outgoing one, so the pair's operand is no larger than the
-  // largest single step's and the running tensor between the two rows is never
-  // written.
   struct Block { int col, r0, nq; };
   std::vector<Block> blocks;
-  for (int col = 0; col < C; ++col) {
-    const bool fuse = o.fuse_rows == 0 && R >= 4;
-    int r = 0;
-    while (r < R) {
-      int nq = 1;
-      if (fuse && (r == 0 || r == R - 2)) {
-        // cost of the pair vs its two single steps (dims at this column)
-        const int64_t hl0 = rdim_h(r, col - 1), hl1 = rdim_h(r + 1, col - 1);
-        const int64_t hr0 = rdim_h(r, col), hr1 = rdim_h(r + 1, col);
-        const int64_t vin = rdim_v(r - 1, col), vmid = rdim_v(r, col), vout = rdim_v(r + 1, col);
-        const double pair = (double)hl0 * hl1 * vin * hr0 * hr1 * vout;
-        const double single = (double)hl0 * vin * hr0 * vmid * hl1 + (double)hr0 * hl1 * vmid * hr1 * vout;
-        // a pair with few output tiles runs its whole K on a few CTAs: take
-        // it only if its K is no longer than the two single steps' together
-        double Mrest = 1;
-        for (int rr = 0; rr < R; ++rr)
-          if (rr < r) Mrest *= (double)rdim_h(rr, col);
-          else if (rr > r + 1) Mrest *= (double)rdim_h(rr, col - 1);
-        const double tiles = std::ceil(Mrest / 128.0) * std::ceil((double)(hr0 * hr1 * vout) / 64.0);
-        const bool shallow = hl0 * hl1 * vin <= hl0 * vin + hl1 * vmid;
-        if (pair <= single && (tiles >= 152 || shallow) && vmid <= kMaxMid) nq = 2;
-      }
-      blocks.push_back({col, r, nq});
-      r += nq;
-    }
-  }
-
-  // ---- step list of the column sweep (legs tracked by identity) ----
-  // Before a block of rows r .. r+k-1 the running tensor's legs are, slowest
-  // first, [h_{r+k} .. h_{R-1}, h'_0 .. h'_{r-1}, h_r .. h_{r+k-1}, v]; the
-  // block's store moves the next block's k' legs (the slowest M legs) next to
-  // v', which restores that form.  Leg ids: h-edge (r, col) -> 1000 + r*64 +
-  // col + 1; v-leg -> 2 at the column ends (the bottom leg of column c and the
-  // top leg of column c+1 are both of dim 1 and share the id).
   struct Leg { int id; int64_t dim; };
-  std::vector<Leg> legs;
-  auto hid = [&](int r, int col) { return 1000 + r * 64 + (col + 1); };
-  {
-    const int k0 = blocks.empty() ? 1 : blocks[0].nq;
-    for (int j = k0; j < R; ++j) legs.push_back({hid(j, -1), 1});
-    for (int j = 0; j < k0; ++j) legs.push_back({hid(j, -1), 1});
-    legs.push_back({2, 1});
-  }
   P.steps.clear();
   P.step_site.clear();
   P.step_opbase.clear();
+  P.step_roles.clear();
+  P.scheme = o.scheme;
   int64_t cap = 1;
   double flops = 0, bytes = 0;
   int n_ops_total = 0;
-  for (size_t bi = 0; bi < blocks.size(); ++bi) {
-    const Block &bk = blocks[bi];
-    const int col = bk.col, r0 = bk.r0, k = bk.nq;
-    const int knext = bi + 1 < blocks.size() ? blocks[bi + 1].nq : 0;
-    const size_t nl = legs.size();
-    for (int j = 0; j < k; ++j)
-      if (legs[nl - 1 - k + j].id != hid(r0 + j, col - 1))
-        return fail(PEPS_EINVAL, "internal: leg order broken at (%d,%d)", r0 + j, col);
-    int64_t K = legs[nl - 1].dim;
-    for (int j = 0; j < k; ++j) K *= legs[nl - 1 - k + j].dim;
-    const size_t nM = nl - 1 - k;  // M legs: legs[0 .. nM)
-    int64_t M = 1;
-    for (size_t i = 0; i < nM; ++i) M *= legs[i].dim;
-    int64_t dh = 1;
-    for (int j = 0; j < k; ++j) dh *= rdim_h(r0 + j, col);
-    const int64_t dv = rdim_v(r0 + k - 1, col);
-    const int64_t N = dh * dv;
-    const size_t kmove = std::min<size_t>((size_t)knext, nM);
-    int64_t Pdim = 1;
-    for (size_t i = 0; i < kmove; ++i) Pdim *= legs[i].dim;
-    if (K > (1 << 20) || N > (1 << 20))
-      return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r0, col);
-    StepShape sh{};
-    sh.M = M;
-    sh.K = (int)K;
-    sh.N = (int)N;
-    sh.P = Pdim;
-    sh.dv_out = (int)dv;
-    sh.dh_out = (int)dh;
-    sh.q = r0 * C + col;
-    sh.nq = k;
-    sh.qs = C;
-    sh.fmt = fmt;
-    sh.target = scale_target(fmt);
-    P.steps.push_back(sh);
-    P.step_site.push_back(r0 * C + col);
-    P.step_opbase.push_back(n_ops_total);
-    n_ops_total += 1 << k;
-    cap = std::max(cap, std::max(M * K, M * N));
-    flops += 8.0 * (double)M * K * N;
-    bytes += (double)bpe * (double)(M * K + M * N);
-    std::vector<Leg> nlgs;
-    for (size_t i = kmove; i < nM; ++i) nlgs.push_back(legs[i]);
-    for (int j = 0; j < k; ++j) nlgs.push_back({hid(r0 + j, col), rdim_h(r0 + j, col)});
-    for (size_t i = 0; i < kmove; ++i) nlgs.push_back(legs[i]);
-    nlgs.push_back({r0 + k == R ? 2 : 3000 + r0 + k - 1, dv});
-    legs.swap(nlgs);
+  if (!quad) {
+    // ---- blocks: the sites each step absorbs ----
+    // One site per step, except that (with fuse_rows == 0) the two top rows and
+    // the two bottom rows of a column are absorbed together when that costs no
+    // more multiply-adds and leaves the step enough output tiles (or no longer
+    // a K) to fill the GPU: the top pair has no incoming vertical leg and the
+    // bottom pair no outgoing one, so the pair's operand is no larger than the
+    // largest single step's and the running tensor between the two rows is never
+    // written.
+    for (int col = 0; col < C; ++col) {
+      const bool fuse = o.fuse_rows == 0 && R >= 4;
+      int r = 0;
+      while (r < R) {
+        int nq = 1;
+        if (fuse && (r == 0 || r == R - 2)) {
+          // cost of the pair vs its two single steps (dims at this column)
+          const int64_t hl0 = rdim_h(r, col - 1), hl1 = rdim_h(r + 1, col - 1);
+          const int64_t hr0 = rdim_h(r, col), hr1 = rdim_h(r + 1, col);
+          const int64_t vin = rdim_v(r - 1, col), vmid = rdim_v(r, col), vout = rdim_v(r + 1, col);
+          const double pair = (double)hl0 * hl1 * vin * hr0 * hr1 * vout;
+          const double single = (double)hl0 * vin * hr0 * vmid * hl1 + (double)hr0 * hl1 * vmid * hr1 * vout;
+          // a pair with few output tiles runs its whole K on a few CTAs: take
+          // it only if its K is no longer than the two single steps' together
+          double Mrest = 1;
+          for (int rr = 0; rr < R; ++rr)
+            if (rr < r) Mrest *= (double)rdim_h(rr, col);
+            else if (rr > r + 1) Mrest *= (double)rdim_h(rr, col - 1);
+          const double tiles = std::ceil(Mrest / 128.0) * std::ceil((double)(hr0 * hr1 * vout) / 64.0);
+          const bool shallow = hl0 * hl1 * vin <= hl0 * vin + hl1 * vmid;
+          if (pair <= single && (tiles >= 152 || shallow) && vmid <= kMaxMid) nq = 2;
+        }
+        blocks.push_back({col, r, nq});
+        r += nq;
+      }
+    }
+
+    // ---- step list of the column sweep (legs tracked by identity) ----
+    // Before a block of rows r .. r+k-1 the running tensor's legs are, slowest
+    // first, [h_{r+k} .. h_{R-1}, h'_0 .. h'_{r-1}, h_r .. h_{r+k-1}, v]; the
+    // block's store moves the next block's k' legs (the slowest M legs) next to
+    // v', which restores that form.  Leg ids: h-edge (r, col) -> 1000 + r*64 +
+    // col + 1; v-leg -> 2 at the column ends (the bottom leg of column c and the
+    // top leg of column c+1 are both of dim 1 and share the id).
+    std::vector<Leg> legs;
+    auto hid = [&](int r, int col) { return 1000 + r * 64 + (col + 1); };
+    {
+      const int k0 = blocks.empty() ? 1 : blocks[0].nq;
+      for (int j = k0; j < R; ++j) legs.push_back({hid(j, -1), 1});
+      for (int j = 0; j < k0; ++j) legs.push_back({hid(j, -1), 1});
+      legs.push_back({2, 1});
+    }
+    for (size_t bi = 0; bi < blocks.size(); ++bi) {
+      const Block &bk = blocks[bi];
+      const int col = bk.col, r0 = bk.r0, k = bk.nq;
+      const int knext = bi + 1 < blocks.size() ? blocks[bi + 1].nq : 0;
+      const size_t nl = legs.size();
+      for (int j = 0; j < k; ++j)
+        if (legs[nl - 1 - k + j].id != hid(r0 + j, col - 1))
+          return fail(PEPS_EINVAL, "internal: leg order broken at (%d,%d)", r0 + j, col);
+      int64_t K = legs[nl - 1].dim;
+      for (int j = 0; j < k; ++j) K *= legs[nl - 1 - k + j].dim;
+      const size_t nM = nl - 1 - k;  // M legs: legs[0 .. nM)
+      int64_t M = 1;
+      for (size_t i = 0; i < nM; ++i) M *= legs[i].dim;
+      int64_t dh = 1;
+      for (int j = 0; j < k; ++j) dh *= rdim_h(r0 + j, col);
+      const int64_t dv = rdim_v(r0 + k - 1, col);
+      const int64_t N = dh * dv;
+      const size_t kmove = std::min<size_t>((size_t)knext, nM);
+      int64_t Pdim = 1;
+      for (size_t i = 0; i < kmove; ++i) Pdim *= legs[i].dim;
+      if (K > (1 << 20) || N > (1 << 20))
+        return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r0, col);
+      StepShape sh{};
+      sh.M = M;
+      sh.K = (int)K;
+      sh.N = (int)N;
+      sh.P = Pdim;
+      sh.dv_out = (int)dv;
+      sh.dh_out = (int)dh;
+      sh.q = r0 * C + col;
+      sh.nq = k;
+      sh.qs = C;
+      sh.fmt = fmt;
+      sh.target = scale_target(fmt);
+      sh.Mr = M;
+      P.steps.push_back(sh);
+      P.step_roles.push_back({0, 1, 2, 3});
+      P.step_site.push_back(r0 * C + col);
+      P.step_opbase.push_back(n_ops_total);
+      n_ops_total += 1 << k;
+      cap = std::max(cap, std::max(M * K, M * N));
+      flops += 8.0 * (double)M * K * N;
+      bytes += (double)bpe * (double)(M * K + M * N);
+      std::vector<Leg> nlgs;
+      for (size_t i = kmove; i < nM; ++i) nlgs.push_back(legs[i]);
+      for (int j = 0; j < k; ++j) nlgs.push_back({hid(r0 + j, col), rdim_h(r0 + j, col)});
+      for (size_t i = 0; i < kmove; ++i) nlgs.push_back(legs[i]);
+      nlgs.push_back({r0 + k == R ? 2 : 3000 + r0 + k - 1, dv});
+      legs.swap(nlgs);
+    }
+
+  } else {
+    // ---- square partition (supplementary Fig. S2(b)) ----
+    // Each quarter is swept column by column in its own coordinates (i, j),
+    // starting from its lattice corner: ul transposed, bl transposed and
+    // flipped in rows, ur flipped in columns, br flipped in both.  A site's
+    // roles (l, r, u, d in the sweep) map to physical legs.  The open legs
+    // toward the neighbouring quarters are: the d legs of the sweep's last
+    // row (they join the batch, slowest, in sweep-column order) and the r legs
+    // of its last column (the rest, in sweep-row order); a quarter tensor is
+    // stored [batch][rest].  With these orientations
+    //   F_ul = [row cut, rows 0..h-1][column cut, columns 0..w-1]
+    //   F_bl = [row cut, rows R-1..h][column cut, columns 0..w-1]
+    //   F_ur = [column cut, columns C-1..w][row cut, rows 0..h-1]
+    //   F_br = [column cut, columns C-1..w][row cut, rows R-1..h]
+    // so F_l = F_ul F_bl^T is [rows 0..h-1][rows R-1..h], Y = F_br F_l^T is
+    // laid out as F_ur, and the amplitude is sum Y * F_ur.
+    struct Orient { int t, fr, fc; };
+    auto to_lattice = [&](const Orient &w, int i, int j, int &r, int &col) {
+      const int r0 = w.t ? j : i, c0 = w.t ? i : j;
+      r = w.fr ? R - 1 - r0 : r0;
+      col = w.fc ? C - 1 - c0 : c0;
+    };
+    auto phys_leg = [](int r, int col, int r2, int c2) -> int {
+      if (r2 == r && c2 == col - 1) return 0;
+      if (r2 == r && c2 == col + 1) return 1;
+      if (c2 == col && r2 == r - 1) return 2;
+      return 3;
+    };
+    auto leg_rdim = [&](int r, int col, int a) -> int64_t {
+      switch (a) {
+        case 0: return rdim_h(r, col - 1);
+        case 1: return rdim_h(r, col);
+        case 2: return rdim_v(r - 1, col);
+        default: return rdim_v(r, col);
+      }
+    };
+    const int h = R / 2, w = C / 2;
+    auto plan_quarter = [&](int qi, Orient ori, int Hs, int Ws) -> int {
+      Plan::Quarter &Q = P.quarter[qi];
+      Q.first = (int)P.steps.size();
+      auto hs = [](int i, int j) { return 1000 + i * 64 + (j + 1); };
+      const int VID = 2;
+      std::vector<Leg> legs;
+      for (int k = 1; k < Hs; ++k) legs.push_back({hs(k, -1), 1});
+      legs.push_back({hs(0, -1), 1});
+      legs.push_back({VID, 1});
+      int64_t B = 1;
+      for (int j = 0; j < Ws; ++j)
+        for (int i = 0; i < Hs; ++i) {
+          int r, col;
+          to_lattice(ori, i, j, r, col);
+          static const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
+          std::array<int, 4> roles{};
+          int64_t rd[4];
+          for (int ro = 0; ro < 4; ++ro) {
+            int r2, c2;
+            to_lattice(ori, i + di[ro], j + dj[ro], r2, c2);
+            roles[ro] = phys_leg(r, col, r2, c2);
+            rd[ro] = leg_rdim(r, col, roles[ro]);
+          }
+          const size_t nl = legs.size();
+          if (legs[nl - 2].id != hs(i, j - 1))
+            return fail(PEPS_EINVAL, "internal: quarter %d leg order broken at (%d,%d)", qi, i, j);
+          const int64_t K = legs[nl - 2].dim * legs[nl - 1].dim;
+          if (K != rd[0] * rd[2])
+            return fail(PEPS_EINVAL, "internal: quarter %d leg dims disagree at (%d,%d)", qi, i, j);
+          const size_t nM = nl - 2;
+          int64_t Mr = 1;
+          for (size_t k = 0; k < nM; ++k) Mr *= legs[k].dim;
+          const int64_t dh = rd[1], dv = rd[3];
+          const bool last = i == Hs - 1;
+          const size_t kmove = std::min<size_t>((i + 1 < Hs || j + 1 < Ws) ? 1 : 0, nM);
+          int64_t Pd = 1;
+          for (size_t k = 0; k < kmove; ++k) Pd *= legs[k].dim;
+          if (K > (1 << 20) || dh * dv > (1 << 20))
+            return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r, col);
+          StepShape sh{};
+          sh.M = B * Mr;
+          sh.K = (int)K;
+          sh.N = (int)(dh * dv);
+          sh.P = Pd;
+          sh.dv_out = (int)dv;
+          sh.dh_out = (int)dh;
+          sh.q = r * C + col;
+          sh.nq = 1;
+          sh.qs = 0;
+          sh.fmt = fmt;
+          sh.target = scale_target(fmt);
+          sh.vb = last ? 1 : 0;
+          sh.Mr = Mr;
+          P.steps.push_back(sh);
+          P.step_roles.push_back(roles);
+          P.step_site.push_back(r * C + col);
+          P.step_opbase.push_back(n_ops_total);
+          n_ops_total += 2;
+          cap = std::max(cap, std::max(sh.M * K, sh.M * (int64_t)sh.N));
+          flops += 8.0 * (double)sh.M * K * sh.N;
+          bytes += (double)bpe * (double)(sh.M * K + sh.M * (int64_t)sh.N);
+          std::vector<Leg> nlgs;
+          for (size_t k = kmove; k < nM; ++k) nlgs.push_back(legs[k]);
+          nlgs.push_back({hs(i, j), dh});
+          for (size_t k = 0; k < kmove; ++k) nlgs.push_back(legs[k]);
+          if (last) {
+            B *= dv;
+            nlgs.push_back({VID, 1});
+          } else {
+            nlgs.push_back({3000 + i * 64 + j, dv});
+          }
+          legs.swap(nlgs);
+        }
+      // the rest legs are the last sweep column's r legs, in sweep-row order
+      if (legs.size() != (size_t)Hs + 1)
+        return fail(PEPS_EINVAL, "internal: quarter %d ends with %zu legs", qi, legs.size());
+      Q.rest = 1;
+      for (int i = 0; i < Hs; ++i) {
+        if (legs[i].id != hs(i, Ws - 1))
+          return fail(PEPS_EINVAL, "internal: quarter %d final leg order", qi);
+        Q.rest *= legs[i].dim;
+      }
+      Q.batch = B;
+      Q.count = (int)P.steps.size() - Q.first;
+      return PEPS_OK;
+    };
+    auto merge_shape = [&](int64_t M, int64_t K, int64_t N) {
+      StepShape sh{};
+      sh.M = M;
+      sh.K = (int)K;
+      sh.N = (int)N;
+      sh.P = 1;
+      sh.dv_out = N % 8 == 0 ? 8 : 1;   // row-major store: dest = m N + n
+      sh.dh_out = (int)(N / sh.dv_out);
+      sh.q = 0;
+      sh.nq = 0;
+      sh.qs = 0;
+      sh.fmt = fmt;
+      sh.target = scale_target(fmt);
+      sh.vb = 0;
+      sh.Mr = M;
+      return sh;
+    };
+    auto add_merge = [&](const StepShape &sh) {
+      if (sh.K > (1 << 20) || sh.N > (1 << 20))
+        return fail(PEPS_EUNSUPPORTED, "quarter merge operand too large (%d x %d)", sh.K, sh.N);
+      P.steps.push_back(sh);
+      P.step_roles.push_back({0, 1, 2, 3});
+      P.step_site.push_back(-1);
+      P.step_opbase.push_back(-1);  // set once the site operands are numbered
+      cap = std::max(cap, std::max(sh.M * (int64_t)sh.K, sh.M * (int64_t)sh.N));
+      flops += 8.0 * (double)sh.M * sh.K * sh.N;
+      bytes += (double)bpe * (double)(sh.M * (int64_t)sh.K + sh.M * (int64_t)sh.N);
+      P.max_kn_merge = std::max<int64_t>(P.max_kn_merge, (int64_t)sh.K * sh.N);
+      return (int)PEPS_OK;
+    };
+    int rc;
+    if ((rc = plan_quarter(0, {1, 0, 0}, w, h))) return rc;   // ul
+    if ((rc = plan_quarter(1, {1, 1, 0}, w, h))) return rc;   // bl
+    const Plan::Quarter &ul = P.quarter[0], &bl = P.quarter[1];
+    if (ul.rest != bl.rest) return fail(PEPS_EINVAL, "internal: ul / bl cut dims differ");
+    P.s_m1 = (int)P.steps.size();
+    if ((rc = add_merge(merge_shape(ul.batch, ul.rest, bl.batch)))) return rc;
+    if ((rc = plan_quarter(2, {0, 0, 1}, h, w))) return rc;   // ur
+    if ((rc = plan_quarter(3, {0, 1, 1}, h, w))) return rc;   // br
+    const Plan::Quarter &ur = P.quarter[2], &br = P.quarter[3];
+    if (br.rest != bl.batch || br.batch != ur.batch || ul.batch != ur.rest)
+      return fail(PEPS_EINVAL, "internal: quarter cut dims differ");
+    P.s_m2 = (int)P.steps.size();
+    if ((rc = add_merge(merge_shape(br.batch, br.rest, ul.batch)))) return rc;
+    P.n_site_ops = n_ops_total;
+    P.op_m1 = n_ops_total++;
+    P.op_m2 = n_ops_total++;
+    P.step_opbase[P.s_m1] = P.op_m1;
+    P.step_opbase[P.s_m2] = P.op_m2;
   }
+  if (!quad) P.n_site_ops = n_ops_total;
   if (cap > ((int64_t)1 << 36)) return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
   P.cap = cap;
   P.n_steps = (int)P.steps.size();
@@ -546,8 +751,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   int pre_steps = 0;
   for (const auto &bk : blocks)
     if (bk.col < pc) ++pre_steps;
-  int64_t gs = pc > 0 ? o.prefix_group : std::max<int64_t>(n, 1);
-  P.n_groups = (pc > 0 && n > 0) ? (int)(n / gs) : 0;
+  // square partition: a group shares the left half (F_l); without prefix
+  // reuse every bitstring is a group of one
+  int64_t gs = pc > 0 ? o.prefix_group : (quad ? 1 : std::max<int64_t>(n, 1));
+  P.n_groups = ((pc > 0 || quad) && n > 0) ? (int)(n / gs) : 0;
+  P.bufs_per_lane = quad ? 4 : 2;
   int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
   lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, gs), 1));
   P.lanes = lanes;
@@ -673,14 +881,14 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     if (sh.nq == 1) {
       P.max_kn = std::max<int>(P.max_kn, sh.K * sh.N);
       n1 += 2;
-    } else {
+    } else if (sh.nq == 2) {
       P.max_kn2 = std::max<int>(P.max_kn2, sh.K * sh.N);
       n2 += 4;
-    }
+    }  // nq == 0: a merge operand, built from a stored tensor during the call
     for (int t = 0; t < (1 << sh.nq); ++t) {
       const int op = P.step_opbase[s] + t;
       P.ec_off[op] = off;
-      off = align_up(off + (size_t)sh.K * sh.N * sizeof(float2), 1024);
+      off = align_up(off + (size_t)sh.K * (size_t)sh.N * sizeof(float2), 1024);
       if (want_tc && tc_supports(sh, fmt)) {
         const size_t planes = (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) ? 2 : 1;
         const size_t esz = (fmt == FMT_TF32) ? 4 : 2;
@@ -715,10 +923,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   struct Pending { int64_t first_item; };
   const int64_t NS = P.n_steps;
   // Relative buffer addresses, resolved once the table sizes are known.
+  const int BPL = P.bufs_per_lane;
   auto lane_buf = [&](int lane, int b) -> size_t {
-    return (size_t)(2 * lane + b) * P.gbuf_bytes;
+    return (size_t)(BPL * lane + b) * P.gbuf_bytes;
   };
-  auto pre_buf = [&](int b) -> size_t { return (size_t)(2 * P.lanes + b) * P.gbuf_bytes; };
+  auto pre_buf = [&](int b) -> size_t { return (size_t)(BPL * P.lanes + b) * P.gbuf_bytes; };
   const size_t REL = (size_t)1 << 62;  // marker: relative to the buffer area
   struct RelItem { size_t a, d; bool a_unit; int64_t bit; };
   std::vector<RelItem> rel;
@@ -740,7 +949,121 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     rel.insert(rel.end(), rs.begin(), rs.end());
     P.launches.push_back(ln);
   };
-  if (pc > 0) {
+  std::vector<TensorOpEntry> tops;
+  std::vector<DotEntry> dots;
+  if (quad) {
+    // per group: ul and bl sweeps, F_bl -> operand, F_l = F_ul F_bl^T, F_l ->
+    // operand; per chunk of member lanes: ur and br sweeps, Y = F_br F_l^T,
+    // amplitude += sum Y * F_ur.  Group buffers 0-1 hold the ul sweep, 2-3 the
+    // bl sweep and then F_l; lane buffers 0-1 the ur sweep, 2-3 the br sweep
+    // and then Y.
+    const Plan::Quarter &ul = P.quarter[0], &bl = P.quarter[1], &ur = P.quarter[2],
+                        &br = P.quarter[3];
+    // steps of one sweep on `nl` lanes: chains ch(l), bitstrings bit(l), buffers
+    // buf(l, 0..1) (ping-pong); returns the buffer index (0/1) of the result
+    auto sweep = [&](const Plan::Quarter &Q, int nl, auto chain_of, auto bit_of, auto buf_of) {
+      for (int k = 0; k < Q.count; ++k) {
+        const int s = Q.first + k;
+        std::vector<StepItem> its;
+        std::vector<RelItem> rs;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t ch = chain_of(l);
+          StepItem it{};
+          it.op_base = P.step_opbase[s];
+          it.in_rec = k == 0 ? -1 : (int)(ch * NS + s - 1);
+          it.out_rec = (int)(ch * NS + s);
+          RelItem ri{k == 0 ? 0 : buf_of(l, (k - 1) % 2), buf_of(l, k % 2), k == 0, bit_of(l)};
+          its.push_back(it);
+          rs.push_back(ri);
+        }
+        add_step_launch(s, its, rs, k == 0 ? 1 : nl);
+      }
+      return (Q.count - 1) % 2;
+    };
+    auto tensor_op = [&](size_t g_rel, int64_t K, int64_t N, int64_t ns, int rec, int op,
+                         int consumer) {
+      TensorOpEntry t{};
+      t.G = (const void *)(REL + g_rel);
+      t.ks = 1;
+      t.ns = ns;
+      t.K = (int)K;
+      t.N = (int)N;
+      t.rec = rec;
+      t.op = op;
+      t.target = scale_target(fmt);
+      Launch ln{};
+      ln.kind = 2;
+      ln.aux_off = (int64_t)tops.size();
+      ln.n_aux = 1;
+      ln.op = op;
+      ln.kn = K * N;
+      ln.shape = P.steps[consumer];
+      ln.tc = want_tc && tc_supports(P.steps[consumer], fmt);
+      ln.flops = ln.bytes = 0;
+      tops.push_back(t);
+      P.launches.push_back(ln);
+    };
+    for (int g = 0; g < P.n_groups; ++g) {
+      const int64_t chain = g, first = (int64_t)g * gs;
+      auto gch = [&](int) { return chain; };
+      auto gbit = [&](int) { return first; };
+      const int bul = sweep(ul, 1, gch, gbit, [&](int, int b) { return pre_buf(b); });
+      const int bbl = sweep(bl, 1, gch, gbit, [&](int, int b) { return pre_buf(2 + b); });
+      const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
+      const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
+      const int rec_l = (int)(chain * NS + P.s_m1);
+      tensor_op(pre_buf(2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
+      {
+        StepItem it{};
+        it.op_base = P.op_m1;
+        it.in_rec = rec_ul;
+        it.out_rec = rec_l;
+        RelItem ri{pre_buf(bul), pre_buf(2 + (bbl ^ 1)), false, first};
+        add_step_launch(P.s_m1, {it}, {ri}, 1);
+      }
+      // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
+      tensor_op(pre_buf(2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2, P.s_m2);
+      for (int64_t base = 0; base < gs; base += P.lanes) {
+        const int nl = (int)std::min<int64_t>(P.lanes, gs - base);
+        auto mch = [&](int l) { return (int64_t)P.n_groups + first + base + l; };
+        auto mbit = [&](int l) { return first + base + l; };
+        const int bur = sweep(ur, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, b); });
+        const int bbr = sweep(br, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, 2 + b); });
+        {
+          std::vector<StepItem> its;
+          std::vector<RelItem> rs;
+          for (int l = 0; l < nl; ++l) {
+            const int64_t ch = mch(l);
+            StepItem it{};
+            it.op_base = P.op_m2;
+            it.in_rec = (int)(ch * NS + br.first + br.count - 1);
+            it.out_rec = (int)(ch * NS + P.s_m2);
+            RelItem ri{lane_buf(l, 2 + bbr), lane_buf(l, 2 + (bbr ^ 1)), false, mbit(l)};
+            its.push_back(it);
+            rs.push_back(ri);
+          }
+          add_step_launch(P.s_m2, its, rs, nl);
+        }
+        Launch dl{};
+        dl.kind = 3;
+        dl.aux_off = (int64_t)dots.size();
+        dl.n_aux = nl;
+        dl.flops = dl.bytes = 0;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t ch = mch(l);
+          DotEntry d{};
+          d.Y = (const void *)(REL + lane_buf(l, 2 + (bbr ^ 1)));
+          d.F = (const void *)(REL + lane_buf(l, bur));
+          d.n = ur.batch * ur.rest;
+          d.rec_y = (int)(ch * NS + P.s_m2);
+          d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
+          d.out_index = (int)mbit(l);
+          dots.push_back(d);
+        }
+        P.launches.push_back(dl);
+      }
+    }
+  } else if (pc > 0) {
     for (int g = 0; g < P.n_groups; ++g) {
       const int chain = g;
       for (int s = 0; s < pre_steps; ++s) {
@@ -821,13 +1144,17 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   }
   P.off_items = off; off = align_up(off + std::max<size_t>(items.size(), 1) * sizeof(StepItem));
   P.off_fin = off; off = align_up(off + std::max<size_t>(fins.size(), 1) * sizeof(FinalEntry));
+  P.off_tops = off; off = align_up(off + std::max<size_t>(tops.size(), 1) * sizeof(TensorOpEntry));
+  P.off_dots = off; off = align_up(off + std::max<size_t>(dots.size(), 1) * sizeof(DotEntry));
+  P.off_partials = off;
+  off = align_up(off + (quad ? (size_t)kDotBlocks * P.lanes * sizeof(double2) : 16));
   P.off_acc = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(double2));
   P.off_bits = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(uint64_t));
   P.off_out = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(peps_c128));
   P.off_tables_end = off;
   off = align_up(off, 4096);
   P.lane_off = off;
-  const int n_gbufs = 2 * P.lanes + (pc > 0 ? 2 : 0);
+  const int n_gbufs = quad ? 4 * P.lanes + 4 : 2 * P.lanes + (pc > 0 ? 2 : 0);
   off += (size_t)n_gbufs * P.gbuf_bytes;
   P.need = off;
   if (!ws) return PEPS_OK;
@@ -845,6 +1172,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     items[i].D = (void *)(base + P.lane_off + rel[i].d);
   }
   for (auto &f : fins) f.G = (const void *)(base + P.lane_off + ((size_t)f.G - REL));
+  for (auto &t : tops) t.G = (const void *)(base + P.lane_off + ((size_t)t.G - REL));
+  for (auto &d : dots) {
+    d.Y = (const void *)(base + P.lane_off + ((size_t)d.Y - REL));
+    d.F = (const void *)(base + P.lane_off + ((size_t)d.F - REL));
+  }
   for (auto &l : P.launches) {
     if (l.kind != 0 || !l.tc) continue;
     const int q = l.shape.q;
@@ -855,7 +1187,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         bp[t][pl] = P.bt_off[pl][ob + t] ? (const void *)(base + P.bt_off[pl][ob + t])
                                          : (const void *)(base + P.bt_off[0][ob + t]);
     int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
-                        (int64_t)(2 * P.gbuf_bytes), P.plane * 2, bp, o.tc_kchunk, o.tc_cluster,
+                        (int64_t)(BPL * P.gbuf_bytes), P.plane * 2, bp, o.tc_kchunk, o.tc_cluster,
                         &l.tc_handle);
     if (rc != 0)
       return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
@@ -887,14 +1219,17 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       if ((sid >> j) & 1) (p.horiz ? val_h[p.edge] : val_v[p.edge]) |= 1u << p.bit;
     }
     // the projected tensor of site q for bit t, legs restricted to the slice
-    auto site_entry = [&](int q, int t, int op) {
+    // roles[ro] = physical leg (0..3 = l, r, u, d) that plays role ro of the
+    // absorbing sweep (identity for the column sweep)
+    auto site_entry = [&](int q, int t, int op, const std::array<int, 4> &roles) {
       const int r = q / C, col = q % C;
       OpBuildEntry e{};
       const int fb = P.final_buf[q];
       e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
       e.lo_off = P.site_elems[q];
-      for (int a = 0; a < 4; ++a) e.dims[a] = sd[4 * q + a];
-      // legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
+      // physical legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
+      int32_t pd[4], prd[4];
+      uint32_t pfm[4], pfv[4];
       auto leg = [&](int a, bool horiz, int rr, int cc) {
         bool inside = horiz ? (cc >= 0 && cc < C - 1) : (rr >= 0 && rr < R - 1);
         uint32_t fm = 0, fv = 0;
@@ -903,14 +1238,26 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           fm = horiz ? L.fix_h[eidx] : L.fix_v[eidx];
           fv = horiz ? val_h[eidx] : val_v[eidx];
         }
-        e.free_mask[a] = (uint32_t)(e.dims[a] - 1) & ~fm;
-        e.fixed_val[a] = fv;
-        e.rdims[a] = e.dims[a] >> popcount32(fm);
+        pd[a] = sd[4 * q + a];
+        pfm[a] = (uint32_t)(pd[a] - 1) & ~fm;
+        pfv[a] = fv;
+        prd[a] = pd[a] >> popcount32(fm);
       };
       leg(0, true, r, col - 1);
       leg(1, true, r, col);
       leg(2, false, r - 1, col);
       leg(3, false, r, col);
+      // element strides of the physical layout [sigma][l][r][u][d]
+      const int64_t pst[4] = {(int64_t)pd[1] * pd[2] * pd[3], (int64_t)pd[2] * pd[3], pd[3], 1};
+      for (int ro = 0; ro < 4; ++ro) {
+        const int a = roles[ro];
+        e.dims[ro] = pd[a];
+        e.rdims[ro] = prd[a];
+        e.free_mask[ro] = pfm[a];
+        e.fixed_val[ro] = pfv[a];
+        e.stride[ro] = pst[a];
+      }
+      e.tau_stride = (int64_t)pd[0] * pd[1] * pd[2] * pd[3];
       e.tau = t;
       e.op = op;
       return e;
@@ -918,13 +1265,14 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     for (int s = 0; s < P.n_steps; ++s) {
       const StepShape &sh = P.steps[s];
       const int ob = P.step_opbase[s];
+      const std::array<int, 4> ident = {0, 1, 2, 3};
       if (sh.nq == 1) {
-        for (int t = 0; t < 2; ++t) obe.push_back(site_entry(sh.q, t, ob + t));
-      } else {
+        for (int t = 0; t < 2; ++t) obe.push_back(site_entry(sh.q, t, ob + t, P.step_roles[s]));
+      } else if (sh.nq == 2) {
         for (int v = 0; v < 4; ++v) {
           OpBuild2Entry e2{};
-          e2.a = site_entry(sh.q, v & 1, ob + v);
-          e2.b = site_entry(sh.q + C, (v >> 1) & 1, ob + v);
+          e2.a = site_entry(sh.q, v & 1, ob + v, ident);
+          e2.b = site_entry(sh.q + C, (v >> 1) & 1, ob + v, ident);
           e2.op = ob + v;
           obe2.push_back(e2);
         }
@@ -948,6 +1296,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   put(P.off_opbuild2, obe2.data(), obe2.size() * sizeof(OpBuild2Entry));
   put(P.off_items, items.data(), items.size() * sizeof(StepItem));
   put(P.off_fin, fins.data(), fins.size() * sizeof(FinalEntry));
+  put(P.off_tops, tops.data(), tops.size() * sizeof(TensorOpEntry));
+  put(P.off_dots, dots.data(), dots.size() * sizeof(DotEntry));
   return PEPS_OK;
 }
 
@@ -1024,6 +1374,10 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
         S.contract_tc_flops += ns * l.flops;
         S.contract_tc_bytes += ns * l.bytes;
       }
+    } else if (l.kind == 2) {
+      S.launches_operand += ns * (l.tc ? 3 : 2);
+    } else if (l.kind == 3) {
+      S.launches_finalize += 2 * ns;
     } else {
       S.launches_finalize += ns;
     }
@@ -1075,6 +1429,9 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
   const FinalEntry *fins = (const FinalEntry *)(base + P.off_fin);
   const OpBuildEntry *obe = (const OpBuildEntry *)(base + P.off_opbuild);
   const OpBuild2Entry *obe2 = (const OpBuild2Entry *)(base + P.off_opbuild2);
+  const TensorOpEntry *tops = (const TensorOpEntry *)(base + P.off_tops);
+  const DotEntry *dots = (const DotEntry *)(base + P.off_dots);
+  double2 *partials = (double2 *)(base + P.off_partials);
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   for (size_t si = 0; si < P.slice_list.size(); ++si) {
@@ -1087,10 +1444,10 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
       CUDA_TRY(launch_build_operands2(e2, (int)P.n_obe2_per_slice, P.max_kn2, ops, s));
       S.launches_operand++;
     }
-    CUDA_TRY(launch_operand_bounds(P.n_ops, ops, s));
+    CUDA_TRY(launch_operand_bounds(P.n_site_ops, ops, s));
     S.launches_operand++;
     if (any_tc) {
-      CUDA_TRY(launch_build_tc_operands(P.n_ops, std::max(P.max_kn, P.max_kn2), ops, P.fmt, s));
+      CUDA_TRY(launch_build_tc_operands(P.n_site_ops, std::max(P.max_kn, P.max_kn2), ops, P.fmt, s));
       S.launches_operand++;
     }
     for (auto &l : P.launches) {
@@ -1113,6 +1470,18 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
         S.launches_contract++;
         S.contract_flops += l.flops;
         S.contract_bytes += l.bytes;
+      } else if (l.kind == 2) {
+        // a merge operand from a stored tensor: Ec, its bound, the planes
+        CUDA_TRY(launch_tensor_operand(tops + l.aux_off, l.kn, P.fmt, P.plane, ops, recs, s));
+        CUDA_TRY(launch_operand_bounds(1, ops + l.op, s));
+        S.launches_operand += 2;
+        if (l.tc) {
+          CUDA_TRY(launch_build_tc_operands(1, (int)l.kn, ops + l.op, P.fmt, s));
+          S.launches_operand++;
+        }
+      } else if (l.kind == 3) {
+        CUDA_TRY(launch_dot(dots + l.aux_off, l.n_aux, P.fmt, P.plane, recs, partials, acc, s));
+        S.launches_finalize += 2;
       } else {
         CUDA_TRY(launch_finalize(fins + l.fin_off, l.n_fin, P.fmt, P.plane, recs, acc, s));
         S.launches_finalize++;

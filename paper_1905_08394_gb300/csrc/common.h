@@ -64,9 +64,10 @@ struct OpDesc {
   const void *Bt[2];    // tensor-core planes [Nr_pad][Kr_pad] (hi, lo), or null
   uint32_t beta_c_bits; // max_n sum_k (|Re E_kn| + |Im E_kn|), float bits
   uint32_t beta_t_bits; // same bound for the scaled tensor-core planes
-  int32_t b_t;          // scale exponent of the tensor-core planes
+  int32_t b_t;          // scale exponent of the tensor-core planes (Bt = Ec 2^b_t)
   int32_t K, N;         // complex dims
-  int32_t pad_;
+  int32_t e_c;          // Ec = E 2^e_c (0 for site operands; a merge operand
+                        // built from a stored tensor carries that tensor's scale)
 };
 
 // Per (lane, step) record: the max |stored entry| of the step's output
@@ -103,9 +104,17 @@ struct StepShape {
   int32_t fmt;    // storage format of A and D
   int64_t plane;  // element offset of the lo plane (FMT_*X2), in 16-bit units
   int32_t target; // scale target exponent
-  int32_t nq;     // sites in the block (their q are q, q + qs, ...)
+  int32_t nq;     // sites in the block (their q are q, q + qs, ...); 0 for
+                  // a merge of two quarter tensors (one operand)
   int32_t qs;     // site stride (C)
-  int32_t pad_;
+  int32_t vb;     // 1: v' is an open leg; it joins the batch (below) and the
+                  // stored output's v leg has dim 1
+  int64_t Mr;     // M = (batch) x Mr: the slowest M legs form a batch (open
+                  // legs of a quarter that are never contracted in its
+                  // sweep); 0 = no batch (Mr = M).  Row m = b * Mr + m_r;
+                  // the P rotation acts on m_r only, and the output is
+                  //   vb = 0: b * (Mr N) + ((m_lo dh' + h') P + m_hi) dv' + v'
+                  //   vb = 1: (b dv' + v') (Mr dh') + (m_lo dh' + h') P + m_hi
 };
 
 // Operand index of a lane for a block: bit j = output bit of the block's
@@ -138,14 +147,20 @@ struct CzEntry {     // one half of a CZ on one site tensor (out of place)
   int32_t pad_;
 };
 
-// Operand build entry (one site, one tau, one slice variant).
+// Operand build entry (one site, one tau, one slice variant).  The four legs
+// are given by their role in the sweep that absorbs the site: l and u are
+// contracted (K = l u), r and d are new (N = r d).  For the column sweep the
+// roles are the physical legs; a quarter swept from another corner or
+// transposed maps them to other physical legs through `stride`.
 struct OpBuildEntry {
   const float2 *A;      // site tensor [2][l][r][u][d] (full dims), hi plane
   int64_t lo_off;       // entries from the hi plane to the lo plane
-  int32_t dims[4];      // full dims l, r, u, d
-  int32_t rdims[4];     // restricted dims
-  uint32_t free_mask[4];// bits of the full index that vary (per leg)
-  uint32_t fixed_val[4];// value of the fixed bits (per leg)
+  int32_t dims[4];      // full dims by role l, r, u, d
+  int32_t rdims[4];     // restricted dims by role
+  uint32_t free_mask[4];// bits of the full index that vary (by role)
+  uint32_t fixed_val[4];// value of the fixed bits (by role)
+  int64_t stride[4];    // element stride of each role's physical leg
+  int64_t tau_stride;   // elements per sigma slice
   int32_t tau;
   int32_t op;           // OpDesc index to fill
 };
@@ -159,6 +174,30 @@ constexpr int kMaxMid = 1024;
 struct OpBuild2Entry {
   OpBuildEntry a, b;
   int32_t op;
+  int32_t pad_;
+};
+
+// Operand of a merge built from a finished quarter (or half) tensor G held in
+// the running-tensor format:  Ec[k][n] = G[k ks + n ns] 2^-target (so that
+// |Ec| <= 1), and e_c of the op = exp(G's record) - target, which carries
+// G's scale into the merge's output exponent.
+struct TensorOpEntry {
+  const void *G;
+  int64_t ks, ns;       // element strides of the operand's K and N indices
+  int32_t K, N;
+  int32_t rec;          // G's record
+  int32_t op;           // OpDesc to fill
+  int32_t target;       // scale target of G's storage
+  int32_t pad_;
+};
+
+// amplitude += sum_i Y[i] F[i] 2^-(S_Y + S_F): the final contraction of the
+// square partition (Y and F in the running-tensor format, same layout).
+struct DotEntry {
+  const void *Y, *F;
+  int64_t n;
+  int32_t rec_y, rec_f;
+  int32_t out_index;
   int32_t pad_;
 };
 
@@ -190,6 +229,12 @@ cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStre
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
                                   OpDesc *d_ops, cudaStream_t s);
 cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s);
+cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int fmt, int64_t plane,
+                                  OpDesc *d_ops, const Rec *d_recs, cudaStream_t s);
+// Blocks per DotEntry; `d_partials` holds kDotBlocks double2 per entry.
+constexpr int kDotBlocks = 256;
+cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
+                       const Rec *d_recs, double2 *d_partials, double2 *d_acc, cudaStream_t s);
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s);
 // Tensor-core planes (and their bound) of ops [0, n_ops) from their Ec.

@@ -108,20 +108,24 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   const float beta = __uint_as_float(op.beta_c_bits);
   const int x = step_scale_exp(mu, beta, sh.target);
   const float sc = pow2f(x);
-  const int64_t Mlo = M / sh.P;
+  const int64_t Mr = sh.Mr > 0 ? sh.Mr : M;
+  const int64_t Mlo = Mr / sh.P;
   const int dv = sh.dv_out, dh = sh.dh_out;
   float vmax = 0.f;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int64_t m = m0 + ty + 16 * i;
     if (m >= M) continue;
-    const int64_t m_hi = m / Mlo, m_lo = m % Mlo;
+    const int64_t b = m / Mr, mr = m - b * Mr;
+    const int64_t m_hi = mr / Mlo, m_lo = mr % Mlo;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
       const int hh = n / dv, vv = n % dv;
-      const int64_t dest = ((m_lo * dh + hh) * sh.P + m_hi) * dv + vv;
+      const int64_t rot = (m_lo * dh + hh) * sh.P + m_hi;
+      const int64_t dest = sh.vb ? (b * dv + vv) * (Mr * dh) + rot
+                                 : b * (Mr * N) + rot * dv + vv;
       const float2 v = make_float2(acc[i][j].x * sc, acc[i][j].y * sc);
       store_g<FMT>(it.D, dest, sh.plane, v);
       vmax = fmaxf(vmax, max_abs2(v));
@@ -129,7 +133,7 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   }
   for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
   if ((tid & 31) == 0) atomicMax(&recs[it.out_rec].maxbits, __float_as_uint(vmax));
-  if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) recs[it.out_rec].exp = s_in + x;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) recs[it.out_rec].exp = s_in + x + op.e_c;
 }
 
 }  // namespace

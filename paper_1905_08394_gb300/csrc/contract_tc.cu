@@ -463,7 +463,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     const int quad = warp & 3;
     const int row = 32 * quad + lane;
     const int dv = p.sh.dv_out, dh = p.sh.dh_out;
-    const int64_t M = p.sh.M, P = p.sh.P, Mlo = M / P;
+    const int64_t M = p.sh.M, P = p.sh.P;
+    const int64_t Mr = p.sh.Mr > 0 ? p.sh.Mr : M, Mlo = Mr / P;
+    const int64_t MrN = Mr * (int64_t)p.sh.N, Mrdh = Mr * (int64_t)dh;
+    const bool vbm = p.sh.vb != 0;
     uint32_t local = 0;
     int cached_item = -1;
     const OpDesc *op = nullptr;
@@ -494,14 +497,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       tc_fence_after();
       const int64_t m = (int64_t)mt * BM + row;
       const bool live = m < M;
-      const int64_t m_hi = live ? m / Mlo : 0, m_lo = live ? m % Mlo : 0;
+      // row m = b * Mr + m_r (b: the batch of open legs, when there is one)
+      const int64_t b = live ? m / Mr : 0, mr = live ? m - b * Mr : 0;
+      const int64_t m_hi = mr / Mlo, m_lo = mr % Mlo;
       float vmax = 0.f;
       const uint32_t tbase = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN);
       // 8 consecutive complex columns per 16-column chunk; contiguous in the
       // permuted destination when dim(v') is a multiple of 8 (then one row
       // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
-      const bool vec = (dv & 7) == 0;
+      const bool vec = (dv & 7) == 0 && !vbm;
       const int64_t row_base = m_lo * dh;
+      const int64_t bofs = b * MrN;
       void *D = si->D;
       uint32_t ra[16], rb[16];
       tmem_ld16_issue(tbase, ra);
@@ -516,14 +522,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           const int nc0 = (nt * BN + c) >> 1;
           if (vec) {
             const int hh = nc0 / dv, vv = nc0 - hh * dv;
-            const int64_t dest0 = ((row_base + hh) * P + m_hi) * dv + vv;
+            const int64_t dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
             vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int nc = nc0 + j;
               const int hh = nc / dv, vv = nc - hh * dv;
-              const int64_t dest = ((row_base + hh) * P + m_hi) * dv + vv;
+              const int64_t rot = (row_base + hh) * P + m_hi;
+              const int64_t dest = vbm ? (b * dv + vv) * Mrdh + rot : bofs + rot * dv + vv;
               float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
               store_g<FMT>(D, dest, p.sh.plane, o);
               vmax = fmaxf(vmax, max_abs2(o));
@@ -545,7 +552,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
-      if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si->out_rec].exp = s_in + op->b_t + x;
+      if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si->out_rec].exp = s_in + op->b_t + x + op->e_c;
     }
   }
 

@@ -38,6 +38,72 @@ cudaError_t launch_finalize(const FinalEntry *d_entries, int n, int fmt, int64_t
   return cudaGetLastError();
 }
 
+// Square partition, last contraction: sum_i Y[i] F[i] for each entry.  Pass
+// 1: block b of entry e sums a fixed slice of the products (FP32 products,
+// FP64 sums) into partials[e][b]; pass 2 adds the partials in order, applies
+// 2^-(S_Y + S_F) and accumulates into the amplitude.  Both passes have a
+// fixed order, so repeated calls give identical results.
+template <int FMT>
+__global__ void __launch_bounds__(256) k_dot(const DotEntry *__restrict__ entries, int64_t plane,
+                                             double2 *partials) {
+  const DotEntry d = entries[blockIdx.y];
+  double re = 0.0, im = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 y = load_g<FMT>(d.Y, i, plane), f = load_g<FMT>(d.F, i, plane);
+    re += (double)(y.x * f.x - y.y * f.y);
+    im += (double)(y.x * f.y + y.y * f.x);
+  }
+  __shared__ double sre[256], sim[256];
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sre[threadIdx.x] += sre[threadIdx.x + w];
+      sim[threadIdx.x] += sim[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(sre[0], sim[0]);
+}
+
+__global__ void k_dot_final(const DotEntry *__restrict__ entries, int n, const Rec *__restrict__ recs,
+                            const double2 *__restrict__ partials, double2 *acc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const DotEntry d = entries[e];
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < kDotBlocks; ++b) {
+    re += partials[(int64_t)e * kDotBlocks + b].x;
+    im += partials[(int64_t)e * kDotBlocks + b].y;
+  }
+  const int S = recs[d.rec_y].exp + recs[d.rec_f].exp;
+  double2 a = acc[d.out_index];
+  a.x += ldexp(re, -S);
+  a.y += ldexp(im, -S);
+  acc[d.out_index] = a;
+}
+
+cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
+                       const Rec *d_recs, double2 *d_partials, double2 *d_acc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const dim3 grid(kDotBlocks, n);
+  switch (fmt) {
+    case FMT_F32: k_dot<FMT_F32><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    case FMT_TF32: k_dot<FMT_TF32><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    case FMT_BF16: k_dot<FMT_BF16><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    case FMT_FP16: k_dot<FMT_FP16><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    case FMT_BF16X2: k_dot<FMT_BF16X2><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    case FMT_FP16X2: k_dot<FMT_FP16X2><<<grid, 256, 0, s>>>(d_entries, plane, d_partials); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_dot_final<<<(n + 127) / 128, 128, 0, s>>>(d_entries, n, d_recs, d_partials, d_acc);
+  return cudaGetLastError();
+}
+
 __global__ void k_store_out(const double2 *__restrict__ acc, peps_c128 *out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {

@@ -26,26 +26,20 @@ __device__ __forceinline__ int deposit_bits(uint32_t v, uint32_t mask) {
   return (int)out;
 }
 
-// Full-index position of E[l][r][u][d] (restricted indices mapped back).
+// Element position of E[l][r][u][d] (legs by role; restricted indices mapped
+// back to full ones, then through each role's physical stride).
 __device__ __forceinline__ int64_t pos_E(const OpBuildEntry &g, int l_, int r_, int u_, int d_) {
   const int l = (int)g.fixed_val[0] | deposit_bits(l_, g.free_mask[0]);
   const int r = (int)g.fixed_val[1] | deposit_bits(r_, g.free_mask[1]);
   const int u = (int)g.fixed_val[2] | deposit_bits(u_, g.free_mask[2]);
   const int d = (int)g.fixed_val[3] | deposit_bits(d_, g.free_mask[3]);
-  return ((((int64_t)g.tau * g.dims[0] + l) * g.dims[1] + r) * g.dims[2] + u) * g.dims[3] + d;
+  return (int64_t)g.tau * g.tau_stride + l * g.stride[0] + r * g.stride[1] + u * g.stride[2] +
+         d * g.stride[3];
 }
 
 __device__ __forceinline__ float2 fetch_E(const OpBuildEntry &g, int k, int n) {
-  const int rl = g.rdims[0], rr = g.rdims[1], ru = g.rdims[2], rd = g.rdims[3];
-  (void)rl; (void)rr;
-  const int l_ = k / ru, u_ = k % ru;
-  const int r_ = n / rd, d_ = n % rd;
-  const int l = (int)g.fixed_val[0] | deposit_bits(l_, g.free_mask[0]);
-  const int r = (int)g.fixed_val[1] | deposit_bits(r_, g.free_mask[1]);
-  const int u = (int)g.fixed_val[2] | deposit_bits(u_, g.free_mask[2]);
-  const int d = (int)g.fixed_val[3] | deposit_bits(d_, g.free_mask[3]);
-  const int64_t e =
-      ((((int64_t)g.tau * g.dims[0] + l) * g.dims[1] + r) * g.dims[2] + u) * g.dims[3] + d;
+  const int ru = g.rdims[2], rd = g.rdims[3];
+  const int64_t e = pos_E(g, k / ru, n / rd, k % ru, n % rd);
   const float2 h = g.A[e], lo = g.A[g.lo_off + e];
   return make_float2(h.x + lo.x, h.y + lo.y);  // float-float -> one FP32 rounding
 }
@@ -118,16 +112,16 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
   const float2 *__restrict__ Aa = g.a.A;
   const float2 *__restrict__ Ab = g.b.A;
   const int64_t loa = g.a.lo_off, lob = g.b.lo_off;
-  const int b_du = g.b.dims[3];
+  const int64_t a_sd = g.a.stride[3], b_su = g.b.stride[2];  // the shared bond on each site
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
     const int k = i / N, n = i - k * N;
     const int ua = k % Ua, lb = (k / Ua) % Lb, la = k / (Ua * Lb);
     const int db = n % Db, rb = (n / Db) % Rb, ra = n / (Db * Rb);
-    const int64_t pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0];   // d leg (fastest) = 0
-    const int64_t pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_du;
+    const int64_t pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
+    const int64_t pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
     ff2 re = {0.f, 0.f}, im = {0.f, 0.f};
     for (int m = 0; m < Mid; ++m) {
-      const int64_t pa = pa0 + mid_a[m], pb = pb0 + (int64_t)mid_b[m] * b_du;
+      const int64_t pa = pa0 + (int64_t)mid_a[m] * a_sd, pb = pb0 + (int64_t)mid_b[m] * b_su;
       const float2 ah = Aa[pa], al = Aa[loa + pa];
       const float2 bh = Ab[pb], bl = Ab[lob + pb];
       const ff2 ar = {ah.x, al.x}, ai = {ah.y, al.y}, br = {bh.x, bl.x}, bi = {bh.y, bl.y};
@@ -171,6 +165,46 @@ __global__ void __launch_bounds__(1024) k_beta_ops(OpDesc *ops) {
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
     if (lane == 0) atomicMax(&ops[blockIdx.y].beta_c_bits, __float_as_uint(best));
   }
+}
+
+// Merge operand from a stored tensor: Ec[k][n] = G[k ks + n ns] 2^-target,
+// e_c = exp(G) - target; the bounds are reset for k_beta_ops.
+template <int FMT>
+__global__ void k_tensor_op(const TensorOpEntry *__restrict__ e, int64_t plane, OpDesc *ops,
+                            const Rec *recs) {
+  const TensorOpEntry g = *e;
+  OpDesc &op = ops[g.op];
+  float2 *Ec = const_cast<float2 *>(op.Ec);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    op.beta_c_bits = 0u;
+    op.beta_t_bits = 0u;
+    op.e_c = recs[g.rec].exp - g.target;
+  }
+  const float sc = pow2f(-g.target);
+  const int64_t total = (int64_t)g.K * g.N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / g.N, n = i - k * g.N;
+    const float2 v = load_g<FMT>(g.G, k * g.ks + n * g.ns, plane);
+    Ec[i] = make_float2(v.x * sc, v.y * sc);
+  }
+}
+
+cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int fmt, int64_t plane,
+                                  OpDesc *d_ops, const Rec *d_recs, cudaStream_t s) {
+  int64_t blocks = (kn + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  switch (fmt) {
+    case FMT_F32: k_tensor_op<FMT_F32><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_TF32: k_tensor_op<FMT_TF32><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_BF16: k_tensor_op<FMT_BF16><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_FP16: k_tensor_op<FMT_FP16><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_BF16X2: k_tensor_op<FMT_BF16X2><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_FP16X2: k_tensor_op<FMT_FP16X2><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,

@@ -139,6 +139,76 @@ def test_fusion_needs_four_rows():
         B.peps_destroy(h)
 
 
+def _bond_dims(h, R, C):
+    dims = {}
+    for r in range(R):
+        for c in range(C):
+            q = r * C + c
+            if c + 1 < C:
+                dims[(q, q + 1)] = B.peps_bond_dim(h, r, c, r, c + 1)
+            if r + 1 < R:
+                dims[(q, q + C)] = B.peps_bond_dim(h, r, c, r + 1, c)
+    return dims
+
+
+@pytest.mark.parametrize("R,C,d,seed", [(6, 6, 32, 4), (4, 4, 8, 1), (6, 6, 16, 3)])
+def test_quadrant_plan_matches_the_oracle_count(R, C, d, seed):
+    # square partition: 4 quarter sweeps + 2 merges; on a square lattice with one
+    # bond dimension the multiply-adds equal the oracle's direct count (quarters
+    # + merges) less the last contraction, which the GPU does as a dot product.
+    # (The GPU merges F_ul with F_bl first and the oracle F_ul with F_ur, which
+    # cost the same only when the quarters are square.)
+    from oracle import peps as op
+    c, h = make(R, C, d, seed)
+    o, k = B.make_opts(precision="fp16x3", scheme="quadrants")
+    info = B.peps_plan_info_get(h, 1, o)
+    assert info["n_steps"] == 4 * (R // 2) * (C // 2) + 2
+    cost = op.quadrant_contraction_cmacs(R, C, _bond_dims(h, R, C))
+    last = 1
+    for (a, b), v in _bond_dims(h, R, C).items():
+        ra, ca = divmod(a, C)
+        rb, cb = divmod(b, C)
+        if (ra < R // 2) != (rb < R // 2):
+            last *= v            # the edges cut by the middle row boundary
+    assert info["flops_per_chain"] == 8 * (cost["quarters"] + cost["merges"] - last)
+    assert info["max_entries"] == cost["largest"]
+    B.peps_destroy(h)
+
+
+def test_quadrant_plan_6x6_d32_sizes_and_prefix_reuse():
+    c, h = make(6, 6, 32, 4)
+    o, k = B.make_opts(precision="fp16x3", scheme="quadrants", prefix_cols=3, prefix_group=64,
+                       max_lanes=16)
+    q = B.peps_plan_info_get(h, 512, o)
+    o2, k2 = B.make_opts(precision="fp16x3", prefix_cols=3, prefix_group=64, max_lanes=16)
+    col = B.peps_plan_info_get(h, 512, o2)
+    assert q["max_entries"] == 2 ** 24 and col["max_entries"] == 2 ** 28
+    # per group: ul, bl, F_l; per bitstring: ur, br, Y = 2^36 multiply-adds
+    assert q["flops_call"] < col["flops_call"] / 6
+    assert q["flops_call"] > 512 * 8 * 2 ** 36
+    B.peps_destroy(h)
+
+
+def test_quadrant_plan_rejects_bad_requests():
+    c, h = make(5, 6, 16, 2)
+    o, k = B.make_opts(precision="fp32", scheme="quadrants")
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 1, o)          # odd side
+    B.peps_destroy(h)
+    c, h = make(4, 6, 16, 2)                   # even rectangles are fine
+    info = B.peps_plan_info_get(h, 1, o)
+    assert info["n_steps"] == 4 * 2 * 3 + 2
+    B.peps_destroy(h)
+    c, h = make(6, 6, 16, 2)
+    o, k = B.make_opts(precision="fp32", scheme="quadrants", prefix_cols=2, prefix_group=4)
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 8, o)          # prefix must be the left half
+    o, k = B.make_opts(precision="fp32", scheme=7)
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 1, o)
+    B.peps_destroy(h)
+
+
 def test_slicing_plan():
     c, h = make(5, 5, 16, 2)
     ncz = B.peps_cz_count(h)

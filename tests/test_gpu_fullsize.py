@@ -58,6 +58,19 @@ def test_bench_configuration_fp16x3(golden, sim):
     assert D < 1.63 / math.sqrt(len(pt))
 
 
+def test_bench_configuration_square_partition(golden, sim):
+    # the same 512 bitstrings by the square partition (quarters of 3 x 3, left
+    # half shared by each group of 64); the amplitude does not depend on the order
+    circ, bits, idx, ref = golden
+    out = sim.amplitudes(bits, precision="fp16x3", prefix_cols=3, prefix_group=64,
+                         max_lanes=16, scheme="quadrants")
+    err = float(np.linalg.norm(out[idx] - ref) / np.linalg.norm(ref))
+    print(f"6x6 d32 fp16x3 square partition: normwise rel.err {err:.3e} on 8 oracle bitstrings")
+    assert err < TOL
+    pt = (2.0 ** 36) * np.abs(out) ** 2
+    assert abs(pt.mean() - 1) < 3 / math.sqrt(len(pt))
+
+
 def test_fp32_path_on_the_oracle_groups(golden, sim):
     circ, bits, idx, ref = golden
     sel = np.concatenate([bits[0:64], bits[320:384]])

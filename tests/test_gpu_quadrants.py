@@ -1,0 +1,131 @@
+"""Parity of the square-partition contraction (supplementary Fig. S2(b)) on the
+GPU, through the C ABI, with the CPU oracles: the state vector where it fits
+(4x4) and the FP64 PEPS column sweep beyond (the amplitude does not depend on
+the contraction order).  Tolerances as in test_gpu_parity: 1e-5 normwise for
+FP32 and FP16X3, a bound from the unit roundoff for the other forms."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import peps as op
+from oracle import statevector as sv
+from paper_1905_08394_gb300 import binding as B
+from rqc_inputs import make_circuit, prefix_group_bitstrings, uniform_bitstrings, workload
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 1e-5
+UNIT_ROUNDOFF = {"bf16": 2.0 ** -8, "tf32": 2.0 ** -11, "fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16}
+QUAD = dict(scheme="quadrants")
+
+
+def tol_for(prec, n_steps):
+    if prec in ("fp32", "fp16x3"):
+        return SPLIT_TOL
+    return 8 * UNIT_ROUNDOFF[prec] * math.sqrt(n_steps)
+
+
+def relerr(a, ref):
+    return float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+
+
+@pytest.fixture(scope="module")
+def sim_factory(cuda_device):
+    from paper_1905_08394_gb300 import Simulator
+
+    made = []
+
+    def make(circ):
+        s = Simulator(circ.R, circ.C, device=cuda_device.index or 0)
+        s.apply_circuit(circ)
+        made.append(s)
+        return s
+
+    yield make
+    for s in made:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3", "tf32", "bf16x3"])
+def test_4x4_d8_against_the_state_vector(sim_factory, prec):
+    circ, bits = workload("4x4_d8")
+    sim = sim_factory(circ)
+    ref = sv.amplitudes(16, circ.gates, bits)
+    out = sim.amplitudes(bits, precision=prec, **QUAD)
+    assert relerr(out, ref) < tol_for(prec, 10)
+
+
+def test_4x4_d16_against_the_state_vector(sim_factory):
+    circ = make_circuit(4, 4, 16, 5)
+    bits = uniform_bitstrings(16, 128, 5)
+    sim = sim_factory(circ)
+    ref = sv.amplitudes(16, circ.gates, bits)
+    for prec in ("fp32", "fp16x3"):
+        assert relerr(sim.amplitudes(bits, precision=prec, **QUAD), ref) < SPLIT_TOL
+
+
+@pytest.fixture(scope="module")
+def d24(sim_factory):
+    circ, bits = workload("6x6_d24")
+    bits = bits[:16]
+    ref = op.amplitudes(op.build(6, 6, circ.gates), bits)
+    return circ, bits, ref, sim_factory(circ)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "bf16x3", "fp16", "fp16x3"])
+def test_6x6_d24_every_form(d24, prec):
+    circ, bits, ref, sim = d24
+    out = sim.amplitudes(bits, precision=prec, **QUAD)
+    assert relerr(out, ref) < tol_for(prec, 38)
+
+
+def test_6x6_d24_agrees_with_the_column_sweep(d24):
+    circ, bits, ref, sim = d24
+    a = sim.amplitudes(bits, precision="fp16x3", **QUAD)
+    b = sim.amplitudes(bits, precision="fp16x3")
+    assert relerr(a, b) < 2 * SPLIT_TOL
+
+
+def test_6x6_d16_prefix_groups_and_lanes(sim_factory):
+    circ = make_circuit(6, 6, 16, 9)
+    bits = prefix_group_bitstrings(6, 6, 3, 3, 12, 9)
+    sim = sim_factory(circ)
+    ref = op.amplitudes(op.build(6, 6, circ.gates), bits)
+    for prec in ("fp32", "fp16x3"):
+        plain = sim.amplitudes(bits, precision=prec, **QUAD)
+        grouped = sim.amplitudes(bits, precision=prec, prefix_cols=3, prefix_group=12,
+                                 max_lanes=5, **QUAD)
+        assert relerr(plain, ref) < SPLIT_TOL and relerr(grouped, ref) < SPLIT_TOL
+
+
+def test_even_rectangle(sim_factory):
+    circ = make_circuit(4, 6, 16, 12)
+    bits = uniform_bitstrings(24, 24, 12)
+    sim = sim_factory(circ)
+    ref = op.amplitudes(op.build(4, 6, circ.gates), bits)
+    assert relerr(sim.amplitudes(bits, precision="fp16x3", **QUAD), ref) < SPLIT_TOL
+
+
+def test_slices_sum_to_the_unsliced_amplitude(sim_factory):
+    circ = make_circuit(6, 6, 16, 13)
+    bits = uniform_bitstrings(36, 6, 13)
+    sim = sim_factory(circ)
+    full = sim.amplitudes(bits, precision="fp32", **QUAD)
+    sliced = [2, 30, 77]
+    tot = sim.amplitudes(bits, precision="fp32", sliced_cz=sliced, **QUAD)
+    assert relerr(tot, full) < 1e-6
+    one = sim.amplitudes(bits, precision="fp32", sliced_cz=sliced, slice_ids=[5], **QUAD)
+    ref = op.amplitudes(op.build(6, 6, circ.gates, sliced=sliced, slice_id=5), bits)
+    assert relerr(one, ref) < SPLIT_TOL
+
+
+def test_graph_replay_is_bit_identical(sim_factory):
+    circ = make_circuit(6, 6, 16, 14)
+    bits = prefix_group_bitstrings(6, 6, 3, 2, 8, 14)
+    sim = sim_factory(circ)
+    kw = dict(precision="fp16x3", prefix_cols=3, prefix_group=8, max_lanes=4, **QUAD)
+    eager = sim.amplitudes(bits, **kw)
+    g1 = sim.amplitudes(bits, flags=B.PEPS_FLAG_GRAPH, **kw)
+    g2 = sim.amplitudes(bits, flags=B.PEPS_FLAG_GRAPH, **kw)
+    assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
