@@ -16,6 +16,9 @@ e2e     the same through the host C-ABI call (pinned host bitstrings copied
         in, amplitudes copied out, inside the timed region).
 fp32_path  the plain FP32 CUDA-core form on the same GPU (timed on one group
         of 64 bitstrings; the work per amplitude is identical across groups).
+square_partition  the same batch contracted by the square partition of the
+        lattice (supplementary Fig. S2(b)): the same amplitudes (to 1e-5) at a
+        fraction of the work.
 roofline  the tensor-core contraction kernel: algorithmic flops per launch
         (8 real flops per complex multiply-add) / mean launch time from CUDA
         events recorded by the library around each launch.  `traffic` is the
@@ -45,19 +48,23 @@ FLOPS_PER_CMAC = 8
 
 # ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
 # dram__bytes_write.sum; one pass) of `bench.py --no-cpu --fp32-steps 0
-# --steps 1 --warmup 1`: mean over the 1760 k_contract_tc launches.
-TRAFFIC = {"sources_sha256_16": "f7876dc9b0386bc0", "bytes_per_launch": 36.80e9}
+# --steps 1 --warmup 1`: mean DRAM bytes per k_contract_tc launch, per
+# contraction scheme (1760 column-sweep launches, 1800 square-partition ones).
+TRAFFIC = {"sources_sha256_16": "879371240c46ce19",
+           "bytes_per_launch": {"columns": 37.95e9, "quadrants": 3.396e9}}
 TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
 
 
-def measured_traffic():
+def measured_traffic(scheme):
     import hashlib
 
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1905_08394_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == TRAFFIC["sources_sha256_16"] else None
+    if h.hexdigest()[:16] != TRAFFIC["sources_sha256_16"]:
+        return None
+    return TRAFFIC["bytes_per_launch"].get(scheme)
 
 
 def parse():
@@ -69,6 +76,12 @@ def parse():
     ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--lanes", type=int, default=16)
     ap.add_argument("--fp32-steps", type=int, default=2)
+    ap.add_argument("--scheme", default="auto", choices=["auto", "columns", "quadrants"],
+                    help="contraction scheme of the timed steps; auto = the faster of the "
+                         "two on this workload, chosen by the autotuner")
+    ap.add_argument("--other-steps", type=int, default=2,
+                    help="timed calls of the scheme not chosen (reported under 'schemes'; "
+                         "0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
@@ -101,10 +114,18 @@ def load_peaks():
 # CPU oracle sample
 # ---------------------------------------------------------------------------
 
-def oracle_sample(seconds: float):
-    """Time the FP64 oracle's column sweep of the batch's first bitstring for
-    about `seconds` and scale by flops to the batched job's flops per
-    amplitude.  Returns (amplitudes/s, description, cores)."""
+def oracle_sample(seconds: float, scheme: str = "columns"):
+    """Time the FP64 oracle on the batch's first bitstring for about `seconds`
+    and scale by flops to the batched job's flops per amplitude, for the given
+    contraction scheme:
+      columns    the oracle's column sweep, cut off after `seconds`; the job
+                 reuses columns 0-2 across each group of 64;
+      quadrants  the oracle's square partition (four quarters, the two pair
+                 merges and the last contraction) of one bitstring, repeated
+                 while time is left; the job builds the left half once per
+                 group of 64 and does one quarter pair, one merge and the dot
+                 product per bitstring.
+    Returns (amplitudes/s, description, cores)."""
     import numpy as np
 
     from oracle import peps as op
@@ -113,31 +134,56 @@ def oracle_sample(seconds: float):
 
     circ, bits = workload(WORKLOAD)
     p = op.build(circ.R, circ.C, circ.gates)
-    E = p.project(int(bits[0]))
-    steps = cx.column_sweep_step_cmacs(circ.R, circ.C, 16)
-    order = op.sweep_order(circ.R, circ.C, "column")
-    G, labels = np.ones((), dtype=np.complex128), []
-    t0 = time.perf_counter()
-    done = 0
-    cmacs = 0
-    for i, q in enumerate(order):
-        G, labels = op.absorb(G, labels, E[q], q, circ.R, circ.C)
-        cmacs += steps[i]
-        done += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
-    per_amp = (8 * sum(steps[:18]) + 512 * sum(steps[18:])) / 512  # prefix reuse, as the GPU job
+    R, C = circ.R, circ.C
+    if scheme == "quadrants":
+        dims = {}
+        for r in range(R):
+            for c in range(C):
+                q = r * C + c
+                if c + 1 < C:
+                    dims[(q, q + 1)] = p.bond_dim(q, q + 1)
+                if r + 1 < R:
+                    dims[(q, q + C)] = p.bond_dim(q, q + C)
+        cost = op.quadrant_contraction_cmacs(R, C, dims)
+        chi_l = 16 ** C            # the last contraction (the GPU's dot product)
+        one = cost["quarters"] + cost["merges"]
+        # per bitstring of the job: half the quarters and half the pair merges
+        # per bitstring plus the same again per group of 64, and the dot
+        per_amp = (cost["quarters"] / 2 + (cost["merges"] - chi_l) / 2) * (1 + 1 / 64) + chi_l
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            op.amplitude_quadrant(p, int(bits[0]))
+            done += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        dt = time.perf_counter() - t0
+        cmacs = done * one
+        what = (f"oracle O3 (numpy complex128 tensordot) square partition of bitstring 0, "
+                f"{done} full amplitude(s)")
+    else:
+        E = p.project(int(bits[0]))
+        steps = cx.column_sweep_step_cmacs(R, C, 16)
+        order = op.sweep_order(R, C, "column")
+        G, labels = np.ones((), dtype=np.complex128), []
+        t0 = time.perf_counter()
+        done = 0
+        cmacs = 0
+        for i, q in enumerate(order):
+            G, labels = op.absorb(G, labels, E[q], q, R, C)
+            cmacs += steps[i]
+            done += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        dt = time.perf_counter() - t0
+        per_amp = (8 * sum(steps[:18]) + 512 * sum(steps[18:])) / 512  # prefix reuse, as the GPU job
+        what = (f"oracle O3 (numpy complex128 tensordot) column sweep of bitstring 0, first {done} "
+                f"of 36 site absorptions")
     rate = (cmacs / dt) / per_amp
-    desc = (f"oracle O3 (numpy complex128 tensordot) column sweep of bitstring 0, first {done} of "
-            f"36 site absorptions ({cmacs * FLOPS_PER_CMAC:.3e} flops in {dt:.1f} s), scaled by "
-            f"{per_amp * FLOPS_PER_CMAC:.3e} flops per amplitude of the batched job")
+    desc = (f"{what} ({cmacs * FLOPS_PER_CMAC:.3e} flops in {dt:.1f} s), scaled by "
+            f"{per_amp * FLOPS_PER_CMAC:.3e} flops per amplitude of the batched job ({scheme})")
     return rate, desc, os.cpu_count()
 
-
-# ---------------------------------------------------------------------------
-# Clocks
-# ---------------------------------------------------------------------------
 
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -196,6 +242,7 @@ class Clocks:
 # Arms
 # ---------------------------------------------------------------------------
 
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -216,10 +263,11 @@ def run_reference(args):
         return
     vals = []
     desc = cores = None
+    scheme = args.scheme if args.scheme != "auto" else "quadrants"
     for _ in range(args.warmup):
-        oracle_sample(max(2.0, args.cpu_seconds / 4))
+        oracle_sample(max(2.0, args.cpu_seconds / 4), scheme)
     for _ in range(args.steps):
-        v, desc, cores = oracle_sample(args.cpu_seconds)
+        v, desc, cores = oracle_sample(args.cpu_seconds, scheme)
         vals.append(v)
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -227,7 +275,7 @@ def run_reference(args):
             "ms_per_step": 512 / value * 1000, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
-                                   "columns 0-2", "seed": 4},
+                                   "columns 0-2", "seed": 4, "scheme": scheme},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -241,7 +289,7 @@ def run_mine(args):
     import numpy as np
     import torch
 
-    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import Simulator, autotune
     from paper_1905_08394_gb300 import binding as B
     from rqc_inputs import workload
 
@@ -258,9 +306,29 @@ def run_mine(args):
     sim = Simulator(circ.R, circ.C, device=local)
     sim.apply_circuit(circ)
     stream = torch.cuda.Stream(device=dev)
-    kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
+    base_kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
     d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
     d_out = torch.empty(n, dtype=torch.complex128, device=dev)
+    peaks, src = load_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    split = args.precision in ("fp16x3", "bf16x3")
+
+    # contraction order: the autotuner times both schemes on this batch
+    tuned = None
+    if args.scheme == "auto":
+        log = []
+        best = autotune.tune(sim, d_bits, d_out, base_kw,
+                             cands=[{"scheme": "columns"}, {"scheme": "quadrants"}], repeats=1,
+                             stream=stream, log=log.append)
+        scheme = best["scheme"]
+        if pg:   # every rank runs the same order (rank 0's choice)
+            t = torch.tensor([0 if scheme == "columns" else 1], device=dev)
+            torch.distributed.broadcast(t, 0, group=pg)
+            scheme = "columns" if int(t.item()) == 0 else "quadrants"
+        tuned = {"chosen": scheme, "trials": log}
+    else:
+        scheme = args.scheme
+    kw = dict(base_kw, scheme=scheme)
     flags = B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING
 
     def step(s):
@@ -300,8 +368,8 @@ def run_mine(args):
     ms_per_step = ms / args.steps
     value = world * n * args.steps / (ms / 1e3)
 
-    # correctness of the timed output on two sampled bitstrings is the job of
-    # tests/; here the result is only read back to be sure it is finite.
+    # correctness of the timed output is the job of tests/ (the same batch, both
+    # schemes, against the oracle); here it is only read back to be sure it is finite.
     out = d_out.cpu().numpy()
     finite = bool(np.isfinite(out).all())
 
@@ -327,10 +395,51 @@ def run_mine(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * n * e2e_steps / e2e_s
 
-    # FP32 CUDA-core form on one group of 64
+    def roofline_of(flops, ms_tc, nl, nbytes_alg, which):
+        if not nl:
+            return None
+        avg = ms_tc / nl
+        ach = (flops / nl) / (avg / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": measured_traffic(which),
+                "algorithmic_bytes": nbytes_alg / nl,
+                "kernel": "k_contract_tc (tcgen05, fp16 hi/lo, 3 MMAs per k-step)",
+                "peak_source": f"{src} bf16 dense sustained (fp16 dense rate = bf16 rate)",
+                "issued_frac": 3 * ach / peak if split else None,
+                "mean_launch_ms": avg, "launches": int(nl)}
+
+    roof = roofline_of(tc_flops, tc_ms, tc_launches, tc_bytes, scheme)
+    schemes = {scheme: {"value": value, "ms_per_step": ms_per_step,
+                        "flops_per_step": sim.plan_info(n, **kw)["flops_call"]}}
+
+    # the other contraction order on the same batch, for comparison
+    other = "quadrants" if scheme == "columns" else "columns"
+    if args.other_steps > 0:
+        kwo = dict(base_kw, scheme=other)
+        sim.amplitudes_device(d_bits, d_out, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kwo)
+        stream.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.other_steps):
+            sim.amplitudes_device(d_bits, d_out, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kwo)
+        q1.record(stream)
+        stream.synchronize()
+        mso = q0.elapsed_time(q1) / args.other_steps
+        sim.amplitudes_device(d_bits, d_out, stream=stream, flags=B.PEPS_FLAG_TIMING, **kwo)
+        stream.synchronize()
+        sto = sim.stats()
+        schemes[other] = {"value": world * n / (mso / 1e3), "ms_per_step": mso,
+                          "steps": args.other_steps,
+                          "flops_per_step": sim.plan_info(n, **kwo)["flops_call"],
+                          "roofline": roofline_of(sto["contract_tc_flops"], sto["contract_tc_ms"],
+                                                  sto["launches_contract_tc"],
+                                                  sto["contract_tc_bytes"], other)}
+
+    # FP32 CUDA-core form on one group of 64, same contraction order
     f32 = None
     if args.fp32_steps > 0:
-        kw32 = dict(precision="fp32", prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
+        kw32 = dict(precision="fp32", prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
+                    scheme=scheme)
         d_b64 = d_bits[:64].contiguous()
         d_o64 = torch.empty(64, dtype=torch.complex128, device=dev)
         sim.amplitudes_device(d_b64, d_o64, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kw32)
@@ -346,29 +455,16 @@ def run_mine(args):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         alu_peak = sms * 128 * 2 * 2070e6 / 1e12   # FP32 lanes x 2 flops x max SM clock
         f32 = {"value": 64 / (ms32 / 1e3), "unit": UNIT, "bitstrings": 64,
-               "ms_per_step": ms32, "note": "plain FP32 CUDA-core form, one group of 64",
+               "ms_per_step": ms32, "scheme": scheme,
+               "note": "plain FP32 CUDA-core form, one group of 64",
                "roofline": {"bound": "alu", "achieved": fl32 / (ms32 / 1e3) / 1e12,
                             "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": fl32 / (ms32 / 1e3) / 1e12 / alu_peak,
                             "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}}
 
-    peaks, src = load_peaks()
-    tc_avg_ms = tc_ms / tc_launches if tc_launches else None
-    achieved = (tc_flops / tc_launches) / (tc_avg_ms / 1e3) / 1e12 if tc_avg_ms else None
-    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    roof = None
-    if achieved is not None:
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": measured_traffic(),
-                "algorithmic_bytes": tc_bytes / tc_launches,
-                "kernel": "k_contract_tc (tcgen05, fp16 hi/lo, 3 MMAs per k-step)",
-                "peak_source": f"{src} bf16 dense sustained (fp16 dense rate = bf16 rate)",
-                "issued_frac": 3 * achieved / peak if args.precision in ("fp16x3", "bf16x3") else None,
-                "mean_launch_ms": tc_avg_ms, "launches": int(tc_launches)}
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, desc, cores = oracle_sample(args.cpu_seconds)
+        v, desc, cores = oracle_sample(args.cpu_seconds, scheme)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
     if rank == 0:
@@ -379,12 +475,14 @@ def run_mine(args):
                 "data": "synthetic",
                 "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
                                        "columns 0-2, prefix reuse", "seed": 4,
-                           "precision": args.precision, "lanes": args.lanes,
-                           "l2": "inputs larger than L2 (running tensor 2 GiB per lane)"},
+                           "precision": args.precision, "lanes": args.lanes, "scheme": scheme,
+                           "autotune": tuned,
+                           "l2": "inputs larger than L2 (2 GiB running tensor per lane for "
+                                 "columns, 128 MiB quarter tensors x 4 per lane for quadrants)"},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 16 * n},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "fp32_path": f32, "clocks": clk, "finite": finite}
+                "fp32_path": f32, "schemes": schemes, "clocks": clk, "finite": finite}
         print(json.dumps(line), flush=True)
     sim.close()
     if pg:

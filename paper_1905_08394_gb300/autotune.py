@@ -1,9 +1,10 @@
-"""Autotuner for the contraction launches: times candidate tile configurations
-(K bytes per pipeline stage, operand multicast across a CTA pair, lanes per
-launch) on the caller's own workload and keeps the fastest.  Results are
-cached in a JSON file keyed by the workload signature.  Every candidate runs
-the same kernels on the same data; only launch shapes differ, so the
-amplitudes agree to rounding and the choice is purely about speed.
+"""Autotuner for the contraction: times candidate configurations on the
+caller's own workload and keeps the fastest.  The candidates vary the
+contraction order (the column sweep, or the square partition of the
+supplementary Fig. S2(b) on even lattices) and the tile configuration (K bytes
+per pipeline stage, CTA pairs, lanes per launch).  Results are cached in a
+JSON file keyed by the workload signature.  Every candidate computes the same
+amplitudes (to rounding), so the choice is purely about speed.
 """
 from __future__ import annotations
 
@@ -23,14 +24,16 @@ def signature(sim, n: int, kw: dict) -> str:
                 dims.append(sim.bond_dim(r, c, r, c + 1))
             if r + 1 < sim.R:
                 dims.append(sim.bond_dim(r, c, r + 1, c))
-    keys = ("precision", "prefix_cols", "prefix_group", "sliced_cz")
+    keys = ("precision", "prefix_cols", "prefix_group", "sliced_cz", "scheme")
     rest = {k: (list(kw[k]) if k == "sliced_cz" else kw[k]) for k in keys if k in kw and kw[k] is not None}
     return json.dumps({"R": sim.R, "C": sim.C, "dims": dims, "n": n, **rest}, sort_keys=True)
 
 
-def candidates(lanes=(8, 16, 32), kchunk=(128, 64), cluster=(1, 2)):
-    for l, k, c in itertools.product(lanes, kchunk, cluster):
-        yield {"max_lanes": l, "tc_kchunk": k, "tc_cluster": c}
+def candidates(lanes=(8, 16, 32), kchunk=(128, 64), cluster=(1, 2), schemes=("columns",)):
+    """The product of the given choices; pass schemes=("columns", "quadrants")
+    on an even lattice to let the contraction order be tuned as well."""
+    for sc, l, k, c in itertools.product(schemes, lanes, kchunk, cluster):
+        yield {"scheme": sc, "max_lanes": l, "tc_kchunk": k, "tc_cluster": c}
 
 
 def tune(sim, d_bits, d_out, kw: dict, cands=None, repeats: int = 2, cache: str = DEFAULT_CACHE,

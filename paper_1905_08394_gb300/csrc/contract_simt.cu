@@ -28,7 +28,7 @@ constexpr int TN = 4;    // columns per thread (strided by 16)
 constexpr int THREADS = 256;
 
 template <int FMT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2)
 k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
                 const OpDesc *__restrict__ ops, Rec *__restrict__ recs) {
   __shared__ float2 As[2][BK][BM];
@@ -109,6 +109,7 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   const int x = step_scale_exp(mu, beta, sh.target);
   const float sc = pow2f(x);
   const int64_t Mr = sh.Mr > 0 ? sh.Mr : M;
+  const bool batched = Mr != M;
   const int64_t Mlo = Mr / sh.P;
   const int dv = sh.dv_out, dh = sh.dh_out;
   float vmax = 0.f;
@@ -116,8 +117,8 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   for (int i = 0; i < TM; ++i) {
     const int64_t m = m0 + ty + 16 * i;
     if (m >= M) continue;
-    const int64_t b = m / Mr, mr = m - b * Mr;
-    const int64_t m_hi = mr / Mlo, m_lo = mr % Mlo;
+    const int64_t b = batched ? m / Mr : 0, mr = m - b * Mr;
+    const int64_t m_hi = mr / Mlo, m_lo = mr - m_hi * Mlo;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;

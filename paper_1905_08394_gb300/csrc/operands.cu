@@ -229,7 +229,8 @@ cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_
 
 cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s) {
   if (n_ops <= 0) return cudaSuccess;
-  k_beta_ops<<<dim3(8, n_ops), 1024, 0, s>>>(d_ops);
+  // 32 columns per block and pass; 128 blocks cover N = 4096 in one pass
+  k_beta_ops<<<dim3(n_ops == 1 ? 128 : 8, n_ops), 1024, 0, s>>>(d_ops);
   return cudaGetLastError();
 }
 

@@ -129,3 +129,25 @@ def test_graph_replay_is_bit_identical(sim_factory):
     g1 = sim.amplitudes(bits, flags=B.PEPS_FLAG_GRAPH, **kw)
     g2 = sim.amplitudes(bits, flags=B.PEPS_FLAG_GRAPH, **kw)
     assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
+
+
+def test_autotune_chooses_an_order_and_caches_it(sim_factory, tmp_path):
+    import torch
+
+    from paper_1905_08394_gb300 import autotune
+
+    circ = make_circuit(6, 6, 16, 15)
+    bits = prefix_group_bitstrings(6, 6, 3, 2, 12, 15)
+    sim = sim_factory(circ)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    kw = dict(precision="fp16x3", prefix_cols=3, prefix_group=12, max_lanes=4)
+    cache = str(tmp_path / "tune.json")
+    cands = [{"scheme": "columns"}, {"scheme": "quadrants"}]
+    best = autotune.tune(sim, d_bits, d_out, kw, cands=cands, repeats=1, cache=cache)
+    assert best in cands
+    again = autotune.tune(sim, d_bits, d_out, kw, cands=cands, repeats=1, cache=cache)
+    assert again == best
+    ref = op.amplitudes(op.build(6, 6, circ.gates), bits)
+    out = sim.amplitudes(bits, **kw, **best)
+    assert relerr(out, ref) < SPLIT_TOL
