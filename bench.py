@@ -491,7 +491,9 @@ def run_mine(args):
 
 
 def run_profile_case(args):
-    """One amplitude (bitstring 0) of the workload through one lane."""
+    """One amplitude (bitstring 0) of the workload through one lane, by the
+    given contraction scheme (auto = the square partition, which the
+    autotuner picks on this workload)."""
     import numpy as np
 
     from paper_1905_08394_gb300 import Simulator
@@ -500,9 +502,10 @@ def run_profile_case(args):
     circ, bits = workload(WORKLOAD)
     sim = Simulator(circ.R, circ.C)
     sim.apply_circuit(circ)
-    out = sim.amplitudes(bits[:1], precision=args.precision, max_lanes=1)
+    scheme = "quadrants" if args.scheme == "auto" else args.scheme
+    out = sim.amplitudes(bits[:1], precision=args.precision, max_lanes=1, scheme=scheme)
     st = sim.stats()
-    print(json.dumps({"case": "profile", "amplitude": [out[0].real, out[0].imag],
+    print(json.dumps({"case": "profile", "scheme": scheme, "amplitude": [out[0].real, out[0].imag],
                       "launches": st["launches_total"], "tc_launches": st["launches_contract_tc"],
                       "finite": bool(np.isfinite(out).all())}))
     sim.close()
