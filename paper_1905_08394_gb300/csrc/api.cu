@@ -597,74 +597,121 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       Q.first = (int)P.steps.size();
       auto hs = [](int i, int j) { return 1000 + i * 64 + (j + 1); };
       const int VID = 2;
-      std::vector<Leg> legs;
-      for (int k = 1; k < Hs; ++k) legs.push_back({hs(k, -1), 1});
-      legs.push_back({hs(0, -1), 1});
-      legs.push_back({VID, 1});
-      int64_t B = 1;
-      for (int j = 0; j < Ws; ++j)
-        for (int i = 0; i < Hs; ++i) {
-          int r, col;
-          to_lattice(ori, i, j, r, col);
-          static const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
-          std::array<int, 4> roles{};
-          int64_t rd[4];
-          for (int ro = 0; ro < 4; ++ro) {
-            int r2, c2;
-            to_lattice(ori, i + di[ro], j + dj[ro], r2, c2);
-            roles[ro] = phys_leg(r, col, r2, c2);
-            rd[ro] = leg_rdim(r, col, roles[ro]);
-          }
-          const size_t nl = legs.size();
-          if (legs[nl - 2].id != hs(i, j - 1))
-            return fail(PEPS_EINVAL, "internal: quarter %d leg order broken at (%d,%d)", qi, i, j);
-          const int64_t K = legs[nl - 2].dim * legs[nl - 1].dim;
-          if (K != rd[0] * rd[2])
-            return fail(PEPS_EINVAL, "internal: quarter %d leg dims disagree at (%d,%d)", qi, i, j);
-          const size_t nM = nl - 2;
-          int64_t Mr = 1;
-          for (size_t k = 0; k < nM; ++k) Mr *= legs[k].dim;
-          const int64_t dh = rd[1], dv = rd[3];
-          const bool last = i == Hs - 1;
-          const size_t kmove = std::min<size_t>((i + 1 < Hs || j + 1 < Ws) ? 1 : 0, nM);
-          int64_t Pd = 1;
-          for (size_t k = 0; k < kmove; ++k) Pd *= legs[k].dim;
-          if (K > (1 << 20) || dh * dv > (1 << 20))
-            return fail(PEPS_EUNSUPPORTED, "site operand too large at (%d,%d)", r, col);
-          StepShape sh{};
-          sh.M = B * Mr;
-          sh.K = (int)K;
-          sh.N = (int)(dh * dv);
-          sh.P = Pd;
-          sh.dv_out = (int)dv;
-          sh.dh_out = (int)dh;
-          sh.q = r * C + col;
-          sh.nq = 1;
-          sh.qs = 0;
-          sh.fmt = fmt;
-          sh.target = scale_target(fmt);
-          sh.vb = last ? 1 : 0;
-          sh.Mr = Mr;
-          P.steps.push_back(sh);
-          P.step_roles.push_back(roles);
-          P.step_site.push_back(r * C + col);
-          P.step_opbase.push_back(n_ops_total);
-          n_ops_total += 2;
-          cap = std::max(cap, std::max(sh.M * K, sh.M * (int64_t)sh.N));
-          flops += 8.0 * (double)sh.M * K * sh.N;
-          bytes += (double)bpe * (double)(sh.M * K + sh.M * (int64_t)sh.N);
-          std::vector<Leg> nlgs;
-          for (size_t k = kmove; k < nM; ++k) nlgs.push_back(legs[k]);
-          nlgs.push_back({hs(i, j), dh});
-          for (size_t k = 0; k < kmove; ++k) nlgs.push_back(legs[k]);
-          if (last) {
-            B *= dv;
-            nlgs.push_back({VID, 1});
-          } else {
-            nlgs.push_back({3000 + i * 64 + j, dv});
-          }
-          legs.swap(nlgs);
+      static const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
+      // per sweep site: lattice index, roles, restricted dims by role
+      struct SiteInfo { int q; std::array<int, 4> roles; int64_t rd[4]; };
+      auto info = [&](int i, int j) {
+        SiteInfo f{};
+        int r, col;
+        to_lattice(ori, i, j, r, col);
+        f.q = r * C + col;
+        for (int ro = 0; ro < 4; ++ro) {
+          int r2, c2;
+          to_lattice(ori, i + di[ro], j + dj[ro], r2, c2);
+          f.roles[ro] = phys_leg(r, col, r2, c2);
+          f.rd[ro] = leg_rdim(r, col, f.roles[ro]);
         }
+        return f;
+      };
+      // blocks: the top two rows of a sweep column in one step where that costs
+      // no more multiply-adds and stays parallel (the rule of the column
+      // sweep); the last row (its open bottom leg joins the batch) stays single
+      struct QBlock { int j, i0, k; };
+      std::vector<QBlock> qb;
+      {
+        int64_t B = 1;
+        for (int j = 0; j < Ws; ++j) {
+          int i = 0;
+          while (i < Hs) {
+            int k = 1;
+            if (o.fuse_rows == 0 && i == 0 && Hs >= 3) {
+              const SiteInfo a0 = info(0, j), a1 = info(1, j);
+              const double hl0 = a0.rd[0], hl1 = a1.rd[0], hr0 = a0.rd[1], hr1 = a1.rd[1];
+              const double vin = a0.rd[2], vmid = a0.rd[3], vout = a1.rd[3];
+              double Mrest = (double)B;
+              for (int ii = 2; ii < Hs; ++ii) Mrest *= (double)info(ii, j).rd[0];
+              const double pair = hl0 * hl1 * vin * hr0 * hr1 * vout;
+              const double single = hl0 * vin * hr0 * vmid * hl1 + hr0 * hl1 * vmid * hr1 * vout;
+              const double tiles = std::ceil(Mrest / 128.0) * std::ceil(hr0 * hr1 * vout / 64.0);
+              const bool shallow = hl0 * hl1 * vin <= hl0 * vin + hl1 * vmid;
+              if (pair <= single && (tiles >= 152 || shallow) && vmid <= kMaxMid) k = 2;
+            }
+            qb.push_back({j, i, k});
+            i += k;
+          }
+          B *= info(Hs - 1, j).rd[3];
+        }
+      }
+      std::vector<Leg> legs;
+      {
+        const int k0 = qb[0].k;
+        for (int k = k0; k < Hs; ++k) legs.push_back({hs(k, -1), 1});
+        for (int k = 0; k < k0; ++k) legs.push_back({hs(k, -1), 1});
+        legs.push_back({VID, 1});
+      }
+      int64_t B = 1;
+      for (size_t bi = 0; bi < qb.size(); ++bi) {
+        const int j = qb[bi].j, i0 = qb[bi].i0, k = qb[bi].k;
+        const int knext = bi + 1 < qb.size() ? qb[bi + 1].k : 0;
+        SiteInfo f[2];
+        for (int t = 0; t < k; ++t) f[t] = info(i0 + t, j);
+        const size_t nl = legs.size();
+        for (int t = 0; t < k; ++t)
+          if (legs[nl - 1 - k + t].id != hs(i0 + t, j - 1))
+            return fail(PEPS_EINVAL, "internal: quarter %d leg order broken at (%d,%d)", qi, i0 + t, j);
+        int64_t K = legs[nl - 1].dim, Kc = f[0].rd[2];
+        for (int t = 0; t < k; ++t) {
+          K *= legs[nl - 1 - k + t].dim;
+          Kc *= f[t].rd[0];
+        }
+        if (K != Kc)
+          return fail(PEPS_EINVAL, "internal: quarter %d leg dims disagree at (%d,%d)", qi, i0, j);
+        const size_t nM = nl - 1 - k;
+        int64_t Mr = 1;
+        for (size_t t = 0; t < nM; ++t) Mr *= legs[t].dim;
+        int64_t dh = 1;
+        for (int t = 0; t < k; ++t) dh *= f[t].rd[1];
+        const int64_t dv = f[k - 1].rd[3];
+        const bool last = i0 + k == Hs;
+        const size_t kmove = std::min<size_t>((size_t)knext, nM);
+        int64_t Pd = 1;
+        for (size_t t = 0; t < kmove; ++t) Pd *= legs[t].dim;
+        if (K > (1 << 20) || dh * dv > (1 << 20))
+          return fail(PEPS_EUNSUPPORTED, "site operand too large at site %d", f[0].q);
+        StepShape sh{};
+        sh.M = B * Mr;
+        sh.K = (int)K;
+        sh.N = (int)(dh * dv);
+        sh.P = Pd;
+        sh.dv_out = (int)dv;
+        sh.dh_out = (int)dh;
+        sh.q = f[0].q;
+        sh.nq = k;
+        sh.qs = k == 2 ? f[1].q - f[0].q : 0;   // lattice offset of the block's second site
+        sh.fmt = fmt;
+        sh.target = scale_target(fmt);
+        sh.vb = last ? 1 : 0;
+        sh.Mr = Mr;
+        P.steps.push_back(sh);
+        P.step_roles.push_back(f[0].roles);   // one orientation: the same for both sites
+        P.step_site.push_back(f[0].q);
+        P.step_opbase.push_back(n_ops_total);
+        n_ops_total += 1 << k;
+        cap = std::max(cap, std::max(sh.M * K, sh.M * (int64_t)sh.N));
+        flops += 8.0 * (double)sh.M * K * sh.N;
+        bytes += (double)bpe * (double)(sh.M * K + sh.M * (int64_t)sh.N);
+        std::vector<Leg> nlgs;
+        for (size_t t = kmove; t < nM; ++t) nlgs.push_back(legs[t]);
+        for (int t = 0; t < k; ++t) nlgs.push_back({hs(i0 + t, j), f[t].rd[1]});
+        for (size_t t = 0; t < kmove; ++t) nlgs.push_back(legs[t]);
+        if (last) {
+          B *= dv;
+          nlgs.push_back({VID, 1});
+        } else {
+          nlgs.push_back({3000 + (i0 + k - 1) * 64 + j, dv});
+        }
+        legs.swap(nlgs);
+      }
       // the rest legs are the last sweep column's r legs, in sweep-row order
       if (legs.size() != (size_t)Hs + 1)
         return fail(PEPS_EINVAL, "internal: quarter %d ends with %zu legs", qi, legs.size());
@@ -1265,14 +1312,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     for (int s = 0; s < P.n_steps; ++s) {
       const StepShape &sh = P.steps[s];
       const int ob = P.step_opbase[s];
-      const std::array<int, 4> ident = {0, 1, 2, 3};
       if (sh.nq == 1) {
         for (int t = 0; t < 2; ++t) obe.push_back(site_entry(sh.q, t, ob + t, P.step_roles[s]));
       } else if (sh.nq == 2) {
+        // the block's sites are q and q + qs (qs = C for the column sweep; a
+        // quarter's orientation can make it -C or +-1), same roles for both
         for (int v = 0; v < 4; ++v) {
           OpBuild2Entry e2{};
-          e2.a = site_entry(sh.q, v & 1, ob + v, ident);
-          e2.b = site_entry(sh.q + C, (v >> 1) & 1, ob + v, ident);
+          e2.a = site_entry(sh.q, v & 1, ob + v, P.step_roles[s]);
+          e2.b = site_entry(sh.q + sh.qs, (v >> 1) & 1, ob + v, P.step_roles[s]);
           e2.op = ob + v;
           obe2.push_back(e2);
         }

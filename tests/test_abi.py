@@ -160,7 +160,7 @@ def test_quadrant_plan_matches_the_oracle_count(R, C, d, seed):
     # cost the same only when the quarters are square.)
     from oracle import peps as op
     c, h = make(R, C, d, seed)
-    o, k = B.make_opts(precision="fp16x3", scheme="quadrants")
+    o, k = B.make_opts(precision="fp16x3", scheme="quadrants", fuse_rows=1)
     info = B.peps_plan_info_get(h, 1, o)
     assert info["n_steps"] == 4 * (R // 2) * (C // 2) + 2
     cost = op.quadrant_contraction_cmacs(R, C, _bond_dims(h, R, C))
@@ -172,6 +172,21 @@ def test_quadrant_plan_matches_the_oracle_count(R, C, d, seed):
             last *= v            # the edges cut by the middle row boundary
     assert info["flops_per_chain"] == 8 * (cost["quarters"] + cost["merges"] - last)
     assert info["max_entries"] == cost["largest"]
+    B.peps_destroy(h)
+
+
+def test_quadrant_sweeps_fuse_their_top_row_pairs():
+    # in each sweep column of a 3 x 3 quarter the top two rows go in one step
+    # (no incoming vertical leg): 6 steps per quarter instead of 9, the same
+    # largest tensor, fewer multiply-adds and about 40 % fewer bytes
+    c, h = make(6, 6, 32, 4)
+    single = B.peps_plan_info_get(h, 1, B.make_opts(precision="fp16x3", scheme="quadrants",
+                                                   fuse_rows=1)[0])
+    fused = B.peps_plan_info_get(h, 1, B.make_opts(precision="fp16x3", scheme="quadrants")[0])
+    assert single["n_steps"] == 38 and fused["n_steps"] == 26
+    assert fused["max_entries"] == single["max_entries"] == 2 ** 24
+    assert fused["flops_per_chain"] <= single["flops_per_chain"]
+    assert fused["bytes_per_chain"] < 0.75 * single["bytes_per_chain"]
     B.peps_destroy(h)
 
 
@@ -196,7 +211,8 @@ def test_quadrant_plan_rejects_bad_requests():
         B.peps_plan_info_get(h, 1, o)          # odd side
     B.peps_destroy(h)
     c, h = make(4, 6, 16, 2)                   # even rectangles are fine
-    info = B.peps_plan_info_get(h, 1, o)
+    o1, k1 = B.make_opts(precision="fp32", scheme="quadrants", fuse_rows=1)
+    info = B.peps_plan_info_get(h, 1, o1)
     assert info["n_steps"] == 4 * 2 * 3 + 2
     B.peps_destroy(h)
     c, h = make(6, 6, 16, 2)
