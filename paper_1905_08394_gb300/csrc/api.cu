@@ -691,6 +691,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         sh.fmt = fmt;
         sh.target = scale_target(fmt);
         sh.vb = last ? 1 : 0;
+        // the open leg's store is contiguous in h' when nothing moves (P = 1):
+        // order the operand's N with v' slowest there
+        sh.nvs = (last && Pd == 1 && k == 1 && dh % 8 == 0) ? 1 : 0;
         sh.Mr = Mr;
         P.steps.push_back(sh);
         P.step_roles.push_back(f[0].roles);   // one orientation: the same for both sites
@@ -1313,7 +1316,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       const StepShape &sh = P.steps[s];
       const int ob = P.step_opbase[s];
       if (sh.nq == 1) {
-        for (int t = 0; t < 2; ++t) obe.push_back(site_entry(sh.q, t, ob + t, P.step_roles[s]));
+        for (int t = 0; t < 2; ++t) {
+          OpBuildEntry e = site_entry(sh.q, t, ob + t, P.step_roles[s]);
+          e.nvs = sh.nvs;
+          obe.push_back(e);
+        }
       } else if (sh.nq == 2) {
         // the block's sites are q and q + qs (qs = C for the column sweep; a
         // quarter's orientation can make it -C or +-1), same roles for both

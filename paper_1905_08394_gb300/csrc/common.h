@@ -109,6 +109,10 @@ struct StepShape {
   int32_t qs;     // site stride (C)
   int32_t vb;     // 1: v' is an open leg; it joins the batch (below) and the
                   // stored output's v leg has dim 1
+  int32_t nvs;    // N order: 0 = (h', v') with v' fastest (the operand's
+                  // n = r*dd + d); 1 = (v', h') with h' fastest (n = d*dr + r),
+                  // used where that makes the store contiguous (vb with P = 1)
+  int32_t pad_;
   int64_t Mr;     // M = (batch) x Mr: the slowest M legs form a batch (open
                   // legs of a quarter that are never contracted in its
                   // sweep); 0 = no batch (Mr = M).  Row m = b * Mr + m_r;
@@ -163,6 +167,8 @@ struct OpBuildEntry {
   int64_t tau_stride;   // elements per sigma slice
   int32_t tau;
   int32_t op;           // OpDesc index to fill
+  int32_t nvs;          // N order of the operand (StepShape::nvs)
+  int32_t pad_;
 };
 
 // largest internal vertical bond of a two-site block operand

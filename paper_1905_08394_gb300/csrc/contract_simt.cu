@@ -123,7 +123,7 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
-      const int hh = n / dv, vv = n % dv;
+      const int hh = sh.nvs ? n % dh : n / dv, vv = sh.nvs ? n / dh : n % dv;
       const int64_t rot = (m_lo * dh + hh) * sh.P + m_hi;
       const int64_t dest = sh.vb ? (b * dv + vv) * (Mr * dh) + rot
                                  : b * (Mr * N) + rot * dv + vv;

@@ -505,7 +505,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       // 8 consecutive complex columns per 16-column chunk; contiguous in the
       // permuted destination when dim(v') is a multiple of 8 (then one row
       // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
-      const bool vec = (dv & 7) == 0 && !vbm;
+      // n = h' dv' + v' (nvs = 0): 8 consecutive n are contiguous when dv' % 8 == 0
+      // (not for vb); n = v' dh' + h' (nvs = 1, vb with P = 1): when dh' % 8 == 0
+      const bool nvs = p.sh.nvs != 0;
+      const bool vec = nvs ? (P == 1 && (dh & 7) == 0) : ((dv & 7) == 0 && !vbm);
       const int64_t row_base = m_lo * dh;
       const int64_t bofs = b * MrN;
       void *D = si->D;
@@ -521,14 +524,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         if (live) {
           const int nc0 = (nt * BN + c) >> 1;
           if (vec) {
-            const int hh = nc0 / dv, vv = nc0 - hh * dv;
-            const int64_t dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
+            int64_t dest0;
+            if (nvs) {
+              const int vv = nc0 / dh, hh = nc0 - vv * dh;   // P = 1: m_hi = 0
+              dest0 = (b * dv + vv) * Mrdh + row_base + hh;
+            } else {
+              const int hh = nc0 / dv, vv = nc0 - hh * dv;
+              dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
+            }
             vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int nc = nc0 + j;
-              const int hh = nc / dv, vv = nc - hh * dv;
+              const int hh = nvs ? nc % dh : nc / dv, vv = nvs ? nc / dh : nc % dv;
               const int64_t rot = (row_base + hh) * P + m_hi;
               const int64_t dest = vbm ? (b * dv + vv) * Mrdh + rot : bofs + rot * dv + vv;
               float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);

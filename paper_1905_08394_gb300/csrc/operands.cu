@@ -38,8 +38,9 @@ __device__ __forceinline__ int64_t pos_E(const OpBuildEntry &g, int l_, int r_, 
 }
 
 __device__ __forceinline__ float2 fetch_E(const OpBuildEntry &g, int k, int n) {
-  const int ru = g.rdims[2], rd = g.rdims[3];
-  const int64_t e = pos_E(g, k / ru, n / rd, k % ru, n % rd);
+  const int ru = g.rdims[2], rr = g.rdims[1], rd = g.rdims[3];
+  const int r_ = g.nvs ? n % rr : n / rd, d_ = g.nvs ? n / rr : n % rd;
+  const int64_t e = pos_E(g, k / ru, r_, k % ru, d_);
   const float2 h = g.A[e], lo = g.A[g.lo_off + e];
   return make_float2(h.x + lo.x, h.y + lo.y);  // float-float -> one FP32 rounding
 }
