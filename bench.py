@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
                     choices=["bench", "profile", "slices", "precision", "small", "peaks",
-                             "quadrants"],
+                             "quadrants", "pt8x8"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
@@ -96,7 +96,9 @@ def parse():
                          "eager launches vs CUDA-graph replay; peaks: this GPU's FP32 FMA "
                          "and tcgen05 kind::f16 / kind::tf32 rates from the microbenchmarks "
                          "in libpeps_peaks.so; quadrants: the bench workload by the square "
-                         "partition of the lattice (supplementary Fig. S2(b))")
+                         "partition of the lattice (supplementary Fig. S2(b)); pt8x8: the "
+                         "paper's workstation experiment, 10000 amplitudes of an 8x8 (1+25+1) "
+                         "circuit and their Porter-Thomas statistics")
     ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
@@ -706,6 +708,57 @@ def run_quadrants_case(args):
     sim.close()
 
 
+def run_pt8x8_case(args):
+    """The paper's workstation experiment: 10000 amplitudes of an 8x8
+    (1+25+1) circuit (uniform seeded bitstrings) by the square partition, and
+    the Porter-Thomas statistics of N |a|^2 (mean 1, second moment 2, and the
+    Kolmogorov-Smirnov distance to Exp(1)).  The paper took under an hour per
+    amplitude on a 2-core PC."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload("8x8_d25")
+    sim = Simulator(8, 8)
+    sim.apply_circuit(circ)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    kw = dict(precision=args.precision, scheme="quadrants")
+    sim.amplitudes_device(d_bits[:64], d_out[:64], flags=B.PEPS_FLAG_REBUILD, **kw)  # warm-up
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.amplitudes_device(d_bits, d_out, flags=B.PEPS_FLAG_REBUILD, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    out = d_out.cpu().numpy()
+    pt = np.sort((2.0 ** 64) * np.abs(out) ** 2)
+    cdf = 1 - np.exp(-pt)
+    n = len(pt)
+    D = float(max(np.max(np.arange(1, n + 1) / n - cdf), np.max(cdf - np.arange(n) / n)))
+    info = sim.plan_info(len(bits), **kw)
+    print(json.dumps({"case": "pt8x8", "workload": "8x8 (1+25+1), seed 6, 10000 uniform bitstrings",
+                      "precision": args.precision, "scheme": "quadrants",
+                      "seconds": sec, "amplitudes_per_s": n / sec,
+                      "useful_tflops": info["flops_call"] / sec / 1e12,
+                      "flops_per_amplitude": info["flops_call"] / n,
+                      "max_entries": info["max_entries"],
+                      "porter_thomas": {"mean_N_abs2": float(pt.mean()),
+                                        "second_moment": float(np.mean(pt ** 2)),
+                                        "ks_distance": D, "ks_p01_threshold": 1.63 / n ** 0.5},
+                      "paper": "under 1 h per amplitude on a PC (2 cores, 2.8 GHz, 16 GB), "
+                               "10000 amplitudes",
+                      "clocks": clk}), flush=True)
+    sim.close()
+
+
 def run_peaks_case(args):
     """Peak rates measured by this repository's own microbenchmarks: the FP32
     FMA rate of the CUDA cores and the dense tcgen05 rate for kind::f16 and
@@ -759,6 +812,8 @@ def main():
         run_peaks_case(args)
     elif args.case == "quadrants":
         run_quadrants_case(args)
+    elif args.case == "pt8x8":
+        run_pt8x8_case(args)
     elif args.case == "small":
         run_small_case(args)
     elif args.impl == "reference":

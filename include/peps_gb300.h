@@ -120,7 +120,15 @@ typedef struct {
     int32_t n_fixed;          /* CZ gates whose Schmidt bit is held at one
                                  value in every slice of the call (evaluates a
                                  sub-slice: a slice with more bits fixed)     */
-    int32_t pad_;
+    int32_t tc_ksplit;        /* tensor cores: accumulate K in this many
+                                 segments (separate FP32 accumulators summed
+                                 with round-to-nearest).  0 = automatic: the
+                                 split forms give their hi*lo and lo*hi products
+                                 an accumulator of their own on steps with K >=
+                                 2048 real, and on every step of a chain longer
+                                 than 32 steps; 1 = one accumulator; 2-4 = that
+                                 many K segments; -1 = separate corrections on
+                                 every step (the last three for measurement) */
     const uint32_t *fixed_cz; /* their ordinals (disjoint from sliced_cz)     */
     const uint8_t *fixed_s;   /* their values, 0 or 1                         */
     int32_t tc_kchunk;        /* tensor-core tuning: bytes of K per pipeline

@@ -60,7 +60,7 @@ class peps_opts(ct.Structure):
                 ("max_lanes", ct.c_int32), ("n_sliced", ct.c_int32),
                 ("sliced_cz", ct.POINTER(ct.c_uint32)), ("slice_ids", ct.POINTER(ct.c_uint64)),
                 ("n_slice_ids", ct.c_int64), ("watchdog_ns", ct.c_int64),
-                ("n_fixed", ct.c_int32), ("pad_", ct.c_int32),
+                ("n_fixed", ct.c_int32), ("tc_ksplit", ct.c_int32),
                 ("fixed_cz", ct.POINTER(ct.c_uint32)), ("fixed_s", ct.POINTER(ct.c_uint8)),
                 ("tc_kchunk", ct.c_int32), ("tc_cluster", ct.c_int32),
                 ("fuse_rows", ct.c_int32), ("scheme", ct.c_int32)]
@@ -178,7 +178,7 @@ def peps_cz_count(h) -> int:
 def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_group: int = 0,
               max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0,
               fixed_cz=None, fixed_s=None, tc_kchunk: int = 0, tc_cluster: int = 0,
-              fuse_rows: int = 0, scheme="columns"):
+              fuse_rows: int = 0, scheme="columns", tc_ksplit: int = 0):
     """peps_opts plus the arrays it points to (keep both alive)."""
     o = peps_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -201,6 +201,7 @@ def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_gro
     o.tc_kchunk = tc_kchunk
     o.tc_cluster = tc_cluster
     o.fuse_rows = fuse_rows
+    o.tc_ksplit = tc_ksplit
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     if fixed_cz is not None and len(fixed_cz):
         f = np.ascontiguousarray(fixed_cz, dtype=np.uint32)

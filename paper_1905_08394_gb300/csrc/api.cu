@@ -329,7 +329,7 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
          a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
          a.n_slice_ids == b.n_slice_ids && a.n_fixed == b.n_fixed &&
          a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster &&
-         a.fuse_rows == b.fuse_rows && a.scheme == b.scheme;
+         a.fuse_rows == b.fuse_rows && a.scheme == b.scheme && a.tc_ksplit == b.tc_ksplit;
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
@@ -352,6 +352,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   if (o.n_slice_ids < 0) return fail(PEPS_EINVAL, "n_slice_ids < 0");
   if (o.n_fixed < 0) return fail(PEPS_EINVAL, "n_fixed < 0");
   if (o.fuse_rows < 0 || o.fuse_rows > 1) return fail(PEPS_EINVAL, "fuse_rows must be 0 or 1");
+  if (o.tc_ksplit < -1 || o.tc_ksplit > 4) return fail(PEPS_EINVAL, "tc_ksplit must be in [-1, 4]");
   if (o.scheme != PEPS_SCHEME_COLUMNS && o.scheme != PEPS_SCHEME_QUADRANTS)
     return fail(PEPS_EINVAL, "unknown contraction scheme %d", o.scheme);
   const bool quad = o.scheme == PEPS_SCHEME_QUADRANTS;
@@ -779,6 +780,26 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     P.step_opbase[P.s_m2] = P.op_m2;
   }
   if (!quad) P.n_site_ops = n_ops_total;
+  // tensor-core accumulation.  An FP32 accumulator that the tensor core adds
+  // into loses about an ulp of its own magnitude per MMA, so adding the split
+  // form's small correction products (hi*lo, lo*hi, 2^-11 of the main ones)
+  // into the main accumulator costs twice the error of the main products
+  // themselves.  Automatic (0): steps with K >= 2048 real (the merges, the
+  // fused bottom pairs) give the corrections an accumulator of their own, and
+  // so does every step of a chain longer than 32 steps (the error adds up
+  // along the chain; a short-K step then keeps its epilogue overlap with half
+  // the tile width).  tc_ksplit = k >= 1 forces k K segments on every step and
+  // no separate corrections; -1 separates them on every step (measurement).
+  const bool long_chain = P.steps.size() > 32;
+  for (auto &sh : P.steps) {
+    if (o.tc_ksplit == 0 || o.tc_ksplit == -1) {
+      sh.ksplit = 1;
+      sh.csep = (o.tc_ksplit == -1 || long_chain || 2LL * sh.K >= 2048) ? 1 : 0;
+    } else {
+      sh.ksplit = o.tc_ksplit;
+      sh.csep = 0;
+    }
+  }
   if (cap > ((int64_t)1 << 36)) return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
   P.cap = cap;
   P.n_steps = (int)P.steps.size();

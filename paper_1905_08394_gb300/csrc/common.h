@@ -112,7 +112,13 @@ struct StepShape {
   int32_t nvs;    // N order: 0 = (h', v') with v' fastest (the operand's
                   // n = r*dd + d); 1 = (v', h') with h' fastest (n = d*dr + r),
                   // used where that makes the store contiguous (vb with P = 1)
-  int32_t pad_;
+  int32_t ksplit; // tensor cores: K segments with separate FP32 accumulators
+                  // (0 or 1 = one); the tensor core's accumulation error grows
+                  // with the number of MMAs summed into one accumulator
+  int32_t csep;   // tensor cores, split forms: the hi*lo and lo*hi products go
+                  // to an accumulator of their own (a third of the updates of
+                  // the main one; their own error is 2^-11 smaller)
+  int32_t pad2_;
   int64_t Mr;     // M = (batch) x Mr: the slowest M legs form a batch (open
                   // legs of a quarter that are never contracted in its
                   // sweep); 0 = no batch (Mr = M).  Row m = b * Mr + m_r;

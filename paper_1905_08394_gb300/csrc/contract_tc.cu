@@ -68,6 +68,13 @@ struct __align__(64) TcParams {
   int BN;
   int stages;
   int tmem_cols;
+  int ksplit;   // K segments accumulated in separate TMEM columns, summed in the
+                // epilogue with round-to-nearest FP32 adds (long-K steps)
+  int csep;     // 1: the split form's correction products (hi*lo, lo*hi) have
+                // their own accumulator after the K segments
+  int nacc;     // accumulators per buffer: ksplit + csep
+  int nbuf;     // accumulator buffers (2: the epilogue of a tile overlaps the
+                // next tile's MMAs)
   int64_t watchdog_ns;
 };
 
@@ -413,13 +420,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       const uint32_t idesc = (1u << 4) | ((uint32_t)T::AB << 7) | ((uint32_t)T::AB << 10) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((BM * CG) >> 4) << 24);
       uint32_t it = 0, local = 0;
+      const int KSP = p.ksplit, NB = p.nbuf;
       for (int t = cid; t < total; t += ncl, ++local) {
-        const int acc = local & 1;
-        const uint32_t aph = (local >> 1) & 1u;
+        const int acc = NB == 2 ? (int)(local & 1) : 0;
+        const uint32_t aph = NB == 2 ? (local >> 1) & 1u : local & 1u;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, w)) break;
         tc_fence_after();
-        const uint32_t dt = tmem_base + (uint32_t)(acc * BN);
+        const uint32_t dbuf = tmem_base + (uint32_t)(acc * BN * p.nacc);
+        const uint32_t dcorr = dbuf + (uint32_t)(KSP * BN);   // used when csep
         bool ok = true;
+        int seg_prev = -1;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % S;
           const uint32_t ph = (it / S) & 1u;
@@ -427,17 +437,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
           const uint32_t sb = sa + NP * a_bytes;
+          // K segment of this stage (each segment has its own accumulator)
+          const int seg = (kb * KSP) / kb_count;
+          const bool seg_start = seg != seg_prev;
+          seg_prev = seg;
+          const uint32_t dt = dbuf + (uint32_t)(seg * BN);
+          const bool cs = NP == 2 && p.csep != 0;
+          const uint32_t dc = cs ? dcorr : dt;
 #pragma unroll
           for (int j = 0; j < KSTEPS; ++j) {
-            const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+            const uint32_t first = (seg_start && j == 0) ? 0u : 1u;
             const uint64_t a0 = sdesc(sa + 32 * j, ROWB);
             const uint64_t b0 = sdesc(sb + 32 * j, ROWB);
             mma<T::KIND, CG>(dt, a0, b0, idesc, first);
             if (NP == 2) {
               const uint64_t a1 = sdesc(sa + a_bytes + 32 * j, ROWB);
               const uint64_t b1 = sdesc(sb + b_bytes + 32 * j, ROWB);
-              mma<T::KIND, CG>(dt, a0, b1, idesc, 1u);
-              mma<T::KIND, CG>(dt, a1, b0, idesc, 1u);
+              const uint32_t cfirst = cs ? ((kb == 0 && j == 0) ? 0u : 1u) : 1u;
+              mma<T::KIND, CG>(dc, a0, b1, idesc, cfirst);
+              mma<T::KIND, CG>(dc, a1, b0, idesc, 1u);
             }
           }
           if (CG == 1) mma_commit(&empty[s]);
@@ -488,8 +506,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         x = step_scale_exp(mu, __uint_as_float(op->beta_t_bits), p.sh.target);
         sc = pow2f(x);
       }
-      const int acc = local & 1;
-      const uint32_t aph = (local >> 1) & 1u;
+      const int acc = p.nbuf == 2 ? (int)(local & 1) : 0;
+      const uint32_t aph = p.nbuf == 2 ? (local >> 1) & 1u : local & 1u;
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&tfull[acc], aph, w) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -501,7 +519,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       const int64_t b = live ? m / Mr : 0, mr = live ? m - b * Mr : 0;
       const int64_t m_hi = mr / Mlo, m_lo = mr % Mlo;
       float vmax = 0.f;
-      const uint32_t tbase = tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN);
+      const int KSP = p.nacc;   // K segments, then the correction accumulator
+      const uint32_t tbase =
+          tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN * KSP);
       // 8 consecutive complex columns per 16-column chunk; contiguous in the
       // permuted destination when dim(v') is a multiple of 8 (then one row
       // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
@@ -521,6 +541,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
+        // the other K segments of these columns, added with FP32 round-to-nearest
+        for (int sg = 1; sg < KSP; ++sg) {
+          uint32_t rc[16];
+          tmem_ld16_issue(tbase + (uint32_t)(sg * BN + c), rc);
+          tmem_wait(rc);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(rc[i]);
+        }
         if (live) {
           const int nc0 = (nt * BN + c) >> 1;
           if (vec) {
@@ -678,7 +706,20 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
       return -3;
     }
   }
-  const int BN = Nr >= 256 ? 256 : Nr;
+  // K segments (long-K steps): at most one per k-chunk, and BN small enough
+  // that KS accumulators are double-buffered within TMEM's 512 columns
+  const int kb_count = (Kr * esz) / rowb;
+  int KS = sh.ksplit > 1 ? sh.ksplit : 1;
+  if (KS > kb_count) KS = kb_count;
+  const int CS = (sh.csep && np == 2) ? 1 : 0;
+  const int NA = KS + CS;
+  // BN: the widest tile whose NA accumulators fit TMEM (double-buffered when
+  // they fit twice)
+  int BN = Nr >= 256 ? 256 : Nr;
+  while (BN > 16 && NA * BN > 512) BN /= 2;
+  // a short K (at most 16 k-chunks) needs the epilogue overlap of two buffers
+  if (kb_count <= 16)
+    while (BN > 16 && 2 * NA * BN > 512) BN /= 2;
   const int tiles_m = (int)((sh.M + BM - 1) / BM);
   // The 2-SM UMMA when the 128-row tiles pair up and each CTA's half of the
   // Bt tile is a whole number of 8-row swizzle groups.
@@ -706,8 +747,12 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   d->prm.BN = BN;
   d->prm.tiles_m = (int)((sh.M + BM - 1) / BM);
   d->prm.tiles_n = Nr / BN;
+  d->prm.ksplit = KS;
+  d->prm.csep = CS;
+  d->prm.nacc = NA;
+  d->prm.nbuf = 2 * BN * NA <= 512 ? 2 : 1;
   int cols = 32;
-  while (cols < 2 * BN) cols *= 2;
+  while (cols < d->prm.nbuf * BN * NA) cols *= 2;
   d->prm.tmem_cols = cols;
   const int stage_bytes = np * (BM + BN / d->cg) * rowb;  // this CTA's share
   // 227 KiB per CTA, less the 1 KiB alignment pad and the barriers

@@ -219,6 +219,9 @@ WORKLOADS = {
     "6x6_d24": dict(R=6, C=6, depth=24, seed=3, bitstrings=4096),
     "6x6_d32": dict(R=6, C=6, depth=32, seed=4, groups=8, per_group=64, prefix_cols=3),
     "7x7_d40": dict(R=7, C=7, depth=40, seed=5, bitstrings=1),
+    # the paper's workstation experiment: 10000 amplitudes of an 8x8 (1+25+1)
+    # circuit against the Porter-Thomas distribution
+    "8x8_d25": dict(R=8, C=8, depth=25, seed=6, bitstrings=10000),
 }
 
 

@@ -110,6 +110,21 @@ def seven_by_seven_d24():
             "seconds": time.time() - t}
 
 
+def eight_by_eight_d25():
+    """The 8x8 lattice at depth (1+25+1) (the paper's workstation experiment;
+    bond dimension 8 on every edge cut by the square partition, 16 on some
+    others): the first 8 of the workload's 10000 bitstrings, by the oracle's
+    square partition (its column sweep would hold 2^30-entry tensors)."""
+    circ, bits = workload("8x8_d25")
+    idx = list(range(8))
+    t = time.time()
+    p = op.build(8, 8, circ.gates)
+    amps = op.amplitudes_quadrant(p, bits[idx])
+    return {"workload": "8x8_d25", "indices": idx, "bitstrings": [int(b) for b in bits[idx]],
+            "amplitudes": [[float(a.real), float(a.imag)] for a in amps],
+            "oracle": "oracle.peps square partition (FP64)", "seconds": time.time() - t}
+
+
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "6x6_d32"
     if which == "6x6_d32":
@@ -118,6 +133,8 @@ if __name__ == "__main__":
         d = seven_by_seven_d24()
     elif which == "7x7_d40":
         d = seven_by_seven_d40_subslices()
+    elif which == "8x8_d25":
+        d = eight_by_eight_d25()
     else:
         raise SystemExit(f"unknown set {which}")
     path = os.path.join(HERE, f"oracle_{which}.json")

@@ -148,3 +148,31 @@ def test_7x7_d40_subslices(cuda_device):
             print(f"7x7 d40 sub-slice {prec}: gpu {a:.3e} oracle {ref:.3e}")
             assert abs(a - ref) < TOL * scale
     s.close()
+
+
+def test_8x8_d25_square_partition(cuda_device):
+    """The paper's workstation experiment: 8x8 (1+25+1).  Amplitudes of 8
+    bitstrings against the oracle's square partition (FP64), and the
+    Porter-Thomas statistics of 2048 amplitudes."""
+    from paper_1905_08394_gb300 import Simulator
+
+    with open(os.path.join(HERE, "golden", "oracle_8x8_d25.json")) as f:
+        g = json.load(f)
+    circ, bits = workload("8x8_d25")
+    assert [int(b) for b in bits[:8]] == g["bitstrings"]
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    sim = Simulator(8, 8)
+    sim.apply_circuit(circ)
+    for prec in ("fp16x3", "fp32"):
+        out = sim.amplitudes(bits[:8], precision=prec, scheme="quadrants")
+        err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+        print(f"8x8 d25 {prec}: normwise rel.err {err:.3e} on 8 oracle bitstrings")
+        assert err < TOL
+    out = sim.amplitudes(bits[:2048], precision="fp16x3", scheme="quadrants")
+    pt = np.sort((2.0 ** 64) * np.abs(out) ** 2)
+    assert abs(pt.mean() - 1) < 3 / math.sqrt(len(pt))
+    assert abs(np.mean(pt ** 2) - 2) < 0.5
+    cdf = 1 - np.exp(-pt)
+    D = max(np.max(np.arange(1, len(pt) + 1) / len(pt) - cdf), np.max(cdf - np.arange(len(pt)) / len(pt)))
+    assert D < 1.63 / math.sqrt(len(pt))
+    sim.close()
