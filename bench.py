@@ -48,10 +48,11 @@ FLOPS_PER_CMAC = 8
 
 # ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
 # dram__bytes_write.sum; one pass) of `bench.py --no-cpu --fp32-steps 0
-# --steps 1 --warmup 1`: mean DRAM bytes per k_contract_tc launch, per
-# contraction scheme (1760 column-sweep launches, 1800 square-partition ones).
-TRAFFIC = {"sources_sha256_16": "879371240c46ce19",
-           "bytes_per_launch": {"columns": 37.95e9, "quadrants": 3.396e9}}
+# --steps 1 --warmup 1 --other-steps 1`: mean DRAM bytes per k_contract_tc
+# launch, per contraction scheme (2200 column-sweep launches in 5 calls, 2640
+# square-partition launches in 6 calls).
+TRAFFIC = {"sources_sha256_16": "391e0a6f6c20e2d3",
+           "bytes_per_launch": {"columns": 37.48e9, "quadrants": 3.579e9}}
 TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
 
 
