@@ -33,6 +33,12 @@ Follows the paper step by step, in plain NumPy (complex128):
   its neighbouring quarters; then F_ul is contracted with F_ur and F_bl with
   F_br, and the two results with each other.
 
+* Marginals (the main text's remark on measuring a subset of qubits):
+  P(x_S) = <psi| Pi_S |psi> is the same network with every site replaced by
+  its double layer D_q = sum_sigma A_q^sigma (x) conj(A_q^sigma), sigma fixed
+  to x_q on measured sites and summed over {0, 1} on the others; every bond
+  becomes the pair (ket index, bra index).
+
 Slicing (the paper's "cut" technique, named as future work in its
 conclusions): fixing the Schmidt index s of chosen CZ gates replaces that
 gate by its single term U_s (x) V_s with no bond growth; the amplitude is the
@@ -260,6 +266,31 @@ def amplitudes_with_prefix(peps: PEPS, bitstrings, prefix_cols: int) -> np.ndarr
         G, _ = contract(E, R, C, "column", state=cache[key], sites=post_sites)
         out[i] = complex(G.reshape(-1)[0])
     return out
+
+
+def double_layer(peps: PEPS, x: int, mask: int):
+    """The double-layer site tensors of P(x_S): D_q[(l,l'),(r,r'),(u,u'),(d,d')]
+    = sum_sigma A^sigma[l,r,u,d] conj(A^sigma[l',r',u',d']), sigma = bit q of x
+    if bit q of mask is set, else summed over 0 and 1.  The pair index is
+    ket * dim + bra."""
+    out = []
+    for q in range(peps.R * peps.C):
+        A = peps.A[q]
+        sig = [(int(x) >> q) & 1] if (mask >> q) & 1 else [0, 1]
+        D = sum(np.einsum("lrud,LRUD->lLrRuUdD", A[s], np.conj(A[s])) for s in sig)
+        dl, dr, du, dd = A.shape[1:]
+        out.append(D.reshape(dl * dl, dr * dr, du * du, dd * dd))
+    return out
+
+
+def marginal(peps: PEPS, x: int, mask: int, sweep: str = "column") -> float:
+    """P(x_S) by contracting the double-layer network (real up to rounding)."""
+    G, _ = contract(double_layer(peps, x, mask), peps.R, peps.C, sweep)
+    return float(G.reshape(-1)[0].real)
+
+
+def marginals(peps: PEPS, bitstrings, mask: int) -> np.ndarray:
+    return np.array([marginal(peps, int(x), mask) for x in bitstrings])
 
 
 def quadrant_sites(R: int, C: int):

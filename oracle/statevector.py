@@ -54,3 +54,16 @@ def amplitudes(n: int, gates, bitstrings) -> np.ndarray:
     psi = run(n, gates)
     idx = np.asarray(bitstrings, dtype=np.uint64).astype(np.int64)
     return psi[idx]
+
+
+def marginals(n: int, gates, bitstrings, mask: int) -> np.ndarray:
+    """Marginal probabilities P(x_S) = sum over the unmeasured bits of |psi_x|^2
+    (the definition), for the measured set S = the set bits of `mask`; the
+    values of the measured bits are taken from each bitstring."""
+    psi = run(n, gates)
+    prob = np.abs(psi) ** 2
+    idx = np.arange(1 << n, dtype=np.int64)
+    out = np.empty(len(bitstrings))
+    for i, x in enumerate(bitstrings):
+        out[i] = prob[(idx & mask) == (int(x) & mask)].sum()
+    return out

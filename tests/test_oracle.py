@@ -284,6 +284,34 @@ def test_quadrant_cost_matches_the_paper(L, d):
 
 
 # ---------------------------------------------------------------------------
+# Marginals: the double-layer contraction against the state vector's sums
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("R,C,d,seed", [(2, 3, 16, 1), (3, 3, 8, 2), (3, 4, 16, 3)])
+def test_double_layer_marginals_equal_statevector_sums(R, C, d, seed):
+    c = make_circuit(R, C, d, seed)
+    n = R * C
+    p = op.build(R, C, c.gates)
+    x = uniform_bitstrings(n, 6, seed)
+    for mask in (0b1, (1 << (n // 2)) - 1, 0b1010101 & ((1 << n) - 1), (1 << n) - 1):
+        ref = sv.marginals(n, c.gates, x, mask)
+        assert np.abs(op.marginals(p, x, mask) - ref).max() < 1e-13
+
+
+def test_marginals_special_cases():
+    c = make_circuit(3, 3, 16, 4)
+    p = op.build(3, 3, c.gates)
+    x = uniform_bitstrings(9, 4, 4)
+    # nothing measured: the norm; everything measured: |amplitude|^2
+    assert np.abs(op.marginals(p, x, 0) - 1).max() < 1e-13
+    assert np.abs(op.marginals(p, x, (1 << 9) - 1) - np.abs(op.amplitudes(p, x)) ** 2).max() < 1e-15
+    # the marginals of all settings of the measured bits sum to 1
+    mask = 0b100010011
+    xs = [sum(((k >> j) & 1) << q for j, q in enumerate([0, 1, 4, 8])) for k in range(16)]
+    assert abs(op.marginals(p, xs, mask).sum() - 1) < 1e-13
+
+
+# ---------------------------------------------------------------------------
 # Planted mistakes: each must be caught by one of the pins above.
 # ---------------------------------------------------------------------------
 
@@ -342,6 +370,23 @@ def test_planted_overlapping_quarters_are_caught(monkeypatch):
     except AssertionError:
         return                      # caught: open legs are left over
     assert np.abs(a - ref).max() > 1e-3
+
+
+def test_planted_missing_conjugate_in_double_layer_is_caught(monkeypatch):
+    def bad(peps, x, mask):
+        out = []
+        for q in range(peps.R * peps.C):
+            A = peps.A[q]
+            sig = [(int(x) >> q) & 1] if (mask >> q) & 1 else [0, 1]
+            D = sum(np.einsum("lrud,LRUD->lLrRuUdD", A[s], A[s]) for s in sig)
+            dl, dr, du, dd = A.shape[1:]
+            out.append(D.reshape(dl * dl, dr * dr, du * du, dd * dd))
+        return out
+    monkeypatch.setattr(op, "double_layer", bad)
+    c = make_circuit(3, 3, 16, 2)
+    x = uniform_bitstrings(9, 4, 2)
+    ref = sv.marginals(9, c.gates, x, 0b111)
+    assert np.abs(op.marginals(op.build(3, 3, c.gates), x, 0b111) - ref).max() > 1e-3
 
 
 def test_planted_transposed_peps_gate_is_caught(monkeypatch):
