@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
                     choices=["bench", "profile", "slices", "precision", "small", "peaks",
-                             "quadrants", "pt8x8"],
+                             "quadrants", "pt8x8", "marginals"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
@@ -99,7 +99,9 @@ def parse():
                          "in libpeps_peaks.so; quadrants: the bench workload by the square "
                          "partition of the lattice (supplementary Fig. S2(b)); pt8x8: the "
                          "paper's workstation experiment, 10000 amplitudes of an 8x8 (1+25+1) "
-                         "circuit and their Porter-Thomas statistics")
+                         "circuit and their Porter-Thomas statistics; marginals: marginal "
+                         "probabilities of the top half's 18 qubits of a 6x6 (1+16+1) "
+                         "circuit (the double-layer network), 512 bitstrings")
     ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
     return ap.parse_args()
 
@@ -760,6 +762,41 @@ def run_pt8x8_case(args):
     sim.close()
 
 
+def run_marginals_case(args):
+    """Marginal probabilities P(x_S) of the 18 qubits in rows 0-2 of a 6x6
+    (1+16+1) circuit (seed 24), for 512 seeded bitstrings: the double-layer
+    network (bond dimension 16, the size of the 6x6 (1+32+1) amplitude)
+    through the same kernels, by both contraction schemes."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import make_circuit, uniform_bitstrings
+
+    circ = make_circuit(6, 6, 16, 24)
+    bits = uniform_bitstrings(36, 512, 24)
+    mask = (1 << 18) - 1
+    sim = Simulator(6, 6)
+    sim.apply_circuit(circ)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
+    res = {}
+    for scheme in ("quadrants", "columns"):
+        kw = dict(precision=args.precision, scheme=scheme, max_lanes=args.lanes, measured_mask=mask)
+        reps = 2 if scheme == "quadrants" else 1
+        sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, flags=B.PEPS_FLAG_REBUILD, **kw), reps)
+        out = d_out.cpu().numpy()
+        info = sim.plan_info(len(bits), **kw)
+        res[scheme] = {"marginals_per_s": len(bits) / sec, "ms_per_call": sec * 1e3,
+                       "useful_tflops": info["flops_call"] / sec / 1e12,
+                       "mean_2^18_P": float(np.mean(out.real) * 2 ** 18),
+                       "max_abs_imag_over_real": float(np.max(np.abs(out.imag)) / np.max(np.abs(out.real)))}
+    print(json.dumps({"case": "marginals", "workload": "6x6 (1+16+1) seed 24, qubits 0-17 measured, "
+                      "512 bitstrings", "precision": args.precision, "results": res}), flush=True)
+    sim.close()
+
+
 def run_peaks_case(args):
     """Peak rates measured by this repository's own microbenchmarks: the FP32
     FMA rate of the CUDA cores and the dense tcgen05 rate for kind::f16 and
@@ -815,6 +852,8 @@ def main():
         run_quadrants_case(args)
     elif args.case == "pt8x8":
         run_pt8x8_case(args)
+    elif args.case == "marginals":
+        run_marginals_case(args)
     elif args.case == "small":
         run_small_case(args)
     elif args.impl == "reference":

@@ -90,10 +90,18 @@ enum {
     PEPS_FLAG_REBUILD = 1,  /* re-run the circuit evolution even if unchanged */
     PEPS_FLAG_TIMING = 2,   /* time every contraction launch with CUDA events */
     PEPS_FLAG_NO_TC = 4,    /* run every absorption on the CUDA-core kernel   */
-    PEPS_FLAG_GRAPH = 8     /* capture the call's launch sequence (evolution
+    PEPS_FLAG_GRAPH = 8,    /* capture the call's launch sequence (evolution
                                included) into a CUDA graph on the first call
                                and replay it on later calls with the same
                                plan; ignored together with PEPS_FLAG_TIMING */
+    PEPS_FLAG_MARGINALS = 16 /* return marginal probabilities P(x_S) =
+                               <psi| Pi_S |psi> instead of amplitudes: S = the
+                               set bits of opts.measured_mask, their values
+                               from each bitstring; the other qubits are summed
+                               over.  Computed as the double-layer network
+                               (every site sum_sigma A^sigma (x) conj(A^sigma),
+                               every bond squared); out[i].re = P, .im ~ 0.
+                               Not with slicing or held CZ bits.          */
 };
 
 /* Options of an amplitude call.  All-zero means: FP32_SIMT, no prefix reuse,
@@ -144,6 +152,8 @@ typedef struct {
                                  (the running tensor between them is never
                                  stored); 1 = one site per step              */
     int32_t scheme;           /* PEPS_SCHEME_*: the contraction scheme        */
+    uint64_t measured_mask;   /* with PEPS_FLAG_MARGINALS: bit q set = qubit q
+                                 is measured                                 */
 } peps_opts;
 
 /* Contraction schemes (supplementary, "exact contraction"):

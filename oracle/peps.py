@@ -319,18 +319,25 @@ def merge(a, b):
     return G, [lab for lab in la if lab not in shared] + [lab for lab in lb if lab not in shared]
 
 
-def amplitude_quadrant(peps: PEPS, x: int) -> complex:
-    """The amplitude by the square partition of Fig. S2(b): the four quarter
-    tensors, then upper-left with upper-right and bottom-left with
-    bottom-right, then the two halves."""
-    R, C = peps.R, peps.C
-    E = peps.project(x)
+def contract_quadrants(E, R: int, C: int) -> complex:
+    """The network of site tensors E by the square partition of Fig. S2(b):
+    the four quarter tensors, then upper-left with upper-right and
+    bottom-left with bottom-right, then the two halves."""
     F = {name: contract(E, R, C, sites=sites) for name, sites in quadrant_sites(R, C).items()}
     upper = merge(F["ul"], F["ur"])
     lower = merge(F["bl"], F["br"])
     G, _ = merge(upper, lower)
     assert G.size == 1
     return complex(G.reshape(-1)[0])
+
+
+def amplitude_quadrant(peps: PEPS, x: int) -> complex:
+    return contract_quadrants(peps.project(x), peps.R, peps.C)
+
+
+def marginal_quadrant(peps: PEPS, x: int, mask: int) -> float:
+    """P(x_S) by the square partition of the double-layer network."""
+    return contract_quadrants(double_layer(peps, x, mask), peps.R, peps.C).real
 
 
 def amplitudes_quadrant(peps: PEPS, bitstrings) -> np.ndarray:

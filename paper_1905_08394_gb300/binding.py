@@ -26,6 +26,8 @@ PEPS_ETIMEOUT = -5
 PEPS_ESTATE = -6
 PEPS_EUNSUPPORTED = -7
 
+PEPS_FLAG_MARGINALS = 16
+
 PEPS_SCHEME_COLUMNS = 0
 PEPS_SCHEME_QUADRANTS = 1
 SCHEMES = {"columns": PEPS_SCHEME_COLUMNS, "quadrants": PEPS_SCHEME_QUADRANTS}
@@ -63,7 +65,8 @@ class peps_opts(ct.Structure):
                 ("n_fixed", ct.c_int32), ("tc_ksplit", ct.c_int32),
                 ("fixed_cz", ct.POINTER(ct.c_uint32)), ("fixed_s", ct.POINTER(ct.c_uint8)),
                 ("tc_kchunk", ct.c_int32), ("tc_cluster", ct.c_int32),
-                ("fuse_rows", ct.c_int32), ("scheme", ct.c_int32)]
+                ("fuse_rows", ct.c_int32), ("scheme", ct.c_int32),
+                ("measured_mask", ct.c_uint64)]
 
 
 class peps_stats(ct.Structure):
@@ -178,8 +181,11 @@ def peps_cz_count(h) -> int:
 def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_group: int = 0,
               max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0,
               fixed_cz=None, fixed_s=None, tc_kchunk: int = 0, tc_cluster: int = 0,
-              fuse_rows: int = 0, scheme="columns", tc_ksplit: int = 0):
-    """peps_opts plus the arrays it points to (keep both alive)."""
+              fuse_rows: int = 0, scheme="columns", tc_ksplit: int = 0,
+              measured_mask=None):
+    """peps_opts plus the arrays it points to (keep both alive).  With
+    measured_mask (an int, bit q = qubit q measured) the call returns the
+    marginal probabilities of the measured bits (PEPS_FLAG_MARGINALS)."""
     o = peps_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.flags = flags
@@ -202,6 +208,9 @@ def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_gro
     o.tc_cluster = tc_cluster
     o.fuse_rows = fuse_rows
     o.tc_ksplit = tc_ksplit
+    if measured_mask is not None:
+        o.flags |= PEPS_FLAG_MARGINALS
+        o.measured_mask = int(measured_mask)
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     if fixed_cz is not None and len(fixed_cz):
         f = np.ascontiguousarray(fixed_cz, dtype=np.uint32)

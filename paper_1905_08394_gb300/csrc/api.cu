@@ -329,7 +329,8 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
          a.max_lanes == b.max_lanes && a.n_sliced == b.n_sliced &&
          a.n_slice_ids == b.n_slice_ids && a.n_fixed == b.n_fixed &&
          a.tc_kchunk == b.tc_kchunk && a.tc_cluster == b.tc_cluster &&
-         a.fuse_rows == b.fuse_rows && a.scheme == b.scheme && a.tc_ksplit == b.tc_ksplit;
+         a.fuse_rows == b.fuse_rows && a.scheme == b.scheme && a.tc_ksplit == b.tc_ksplit &&
+         a.measured_mask == b.measured_mask;
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
@@ -356,6 +357,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   if (o.scheme != PEPS_SCHEME_COLUMNS && o.scheme != PEPS_SCHEME_QUADRANTS)
     return fail(PEPS_EINVAL, "unknown contraction scheme %d", o.scheme);
   const bool quad = o.scheme == PEPS_SCHEME_QUADRANTS;
+  // marginals: the double-layer network, every bond squared (no slicing)
+  const bool dl = (o.flags & PEPS_FLAG_MARGINALS) != 0;
+  if (dl && (o.n_sliced > 0 || o.n_fixed > 0))
+    return fail(PEPS_EINVAL, "marginals do not combine with slicing or held CZ bits");
   if (quad && (R % 2 || C % 2))
     return fail(PEPS_EINVAL, "the square partition needs even R and C (got %d x %d)", R, C);
   if (quad && o.prefix_cols != 0 && o.prefix_cols != C / 2)
@@ -429,12 +434,14 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   auto rdim_h = [&](int r, int col) -> int64_t {
     if (col < 0 || col >= C - 1) return 1;
     const int e = edge_h(c, r, col);
-    return (int64_t)L.dim_h[e] >> popcount32(L.fix_h[e]);
+    const int64_t d = (int64_t)L.dim_h[e] >> popcount32(L.fix_h[e]);
+    return dl ? d * d : d;
   };
   auto rdim_v = [&](int r, int col) -> int64_t {
     if (r < 0 || r >= R - 1) return 1;
     const int e = edge_v(c, r, col);
-    return (int64_t)L.dim_v[e] >> popcount32(L.fix_v[e]);
+    const int64_t d = (int64_t)L.dim_v[e] >> popcount32(L.fix_v[e]);
+    return dl ? d * d : d;
   };
   auto fdim_h = [&](int r, int col) -> int {
     return (col < 0 || col >= C - 1) ? 1 : L.dim_h[edge_h(c, r, col)];
@@ -464,7 +471,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     // largest single step's and the running tensor between the two rows is never
     // written.
     for (int col = 0; col < C; ++col) {
-      const bool fuse = o.fuse_rows == 0 && R >= 4;
+      const bool fuse = o.fuse_rows == 0 && R >= 4 && !dl;
       int r = 0;
       while (r < R) {
         int nq = 1;
@@ -625,7 +632,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           int i = 0;
           while (i < Hs) {
             int k = 1;
-            if (o.fuse_rows == 0 && i == 0 && Hs >= 3) {
+            if (o.fuse_rows == 0 && i == 0 && Hs >= 3 && !dl) {
               const SiteInfo a0 = info(0, j), a1 = info(1, j);
               const double hl0 = a0.rd[0], hl1 = a1.rd[0], hr0 = a0.rd[1], hr1 = a1.rd[1];
               const double vin = a0.rd[2], vmid = a0.rd[3], vout = a1.rd[3];
@@ -1331,6 +1338,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       e.tau_stride = (int64_t)pd[0] * pd[1] * pd[2] * pd[3];
       e.tau = t;
       e.op = op;
+      if (dl) {
+        // double layer: sigma fixed to tau on a measured qubit, summed otherwise
+        e.dl = ((o.measured_mask >> q) & 1ull) ? 1 : 2;
+        for (int ro = 0; ro < 4; ++ro) e.rdims[ro] = e.dims[ro] * e.dims[ro];
+      }
       return e;
     };
     for (int s = 0; s < P.n_steps; ++s) {

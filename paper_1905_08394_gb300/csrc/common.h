@@ -174,7 +174,11 @@ struct OpBuildEntry {
   int32_t tau;
   int32_t op;           // OpDesc index to fill
   int32_t nvs;          // N order of the operand (StepShape::nvs)
-  int32_t pad_;
+  int32_t dl;           // 0: E = A^tau; double layer (marginals): 1 = sum over
+                        // sigma = tau, 2 = over sigma in {0, 1} of A^sigma (x)
+                        // conj(A^sigma).  Then `dims` are the single-layer
+                        // dims and `rdims` their squares; a doubled index is
+                        // ket * dim + bra.
 };
 
 // largest internal vertical bond of a two-site block operand

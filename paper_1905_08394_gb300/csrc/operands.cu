@@ -45,6 +45,31 @@ __device__ __forceinline__ float2 fetch_E(const OpBuildEntry &g, int k, int n) {
   return make_float2(h.x + lo.x, h.y + lo.y);  // float-float -> one FP32 rounding
 }
 
+// Double-layer entry (marginals): sum over the allowed sigma of
+// A^sigma[l,r,u,d] conj(A^sigma[l',r',u',d']) with every role index doubled
+// as ket * dim + bra (no slicing: the full index is the role index).
+__device__ __forceinline__ float2 fetch_E_dl(const OpBuildEntry &g, int k, int n) {
+  const int Ru = g.rdims[2], Rr = g.rdims[1], Rd = g.rdims[3];
+  const int ldl = k / Ru, udl = k % Ru;
+  const int rdl = g.nvs ? n % Rr : n / Rd, ddl = g.nvs ? n / Rr : n % Rd;
+  const int l0 = ldl / g.dims[0], l1 = ldl % g.dims[0];
+  const int r0 = rdl / g.dims[1], r1 = rdl % g.dims[1];
+  const int u0 = udl / g.dims[2], u1 = udl % g.dims[2];
+  const int d0 = ddl / g.dims[3], d1 = ddl % g.dims[3];
+  float re = 0.f, im = 0.f;
+  for (int sg = 0; sg < 2; ++sg) {
+    if (g.dl == 1 && sg != g.tau) continue;
+    const int64_t base = (int64_t)sg * g.tau_stride;
+    const int64_t ek = base + l0 * g.stride[0] + r0 * g.stride[1] + u0 * g.stride[2] + d0 * g.stride[3];
+    const int64_t eb = base + l1 * g.stride[0] + r1 * g.stride[1] + u1 * g.stride[2] + d1 * g.stride[3];
+    const float2 ah = g.A[ek], al = g.A[g.lo_off + ek], bh = g.A[eb], bl = g.A[g.lo_off + eb];
+    const float ar = ah.x + al.x, ai = ah.y + al.y, br = bh.x + bl.x, bi = bh.y + bl.y;
+    re += ar * br + ai * bi;      // a * conj(b)
+    im += ai * br - ar * bi;
+  }
+  return make_float2(re, im);
+}
+
 // One block row per entry; threads cover Ec's K*N entries.
 __global__ void k_build_ec(const OpBuildEntry *__restrict__ entries, OpDesc *ops) {
   const OpBuildEntry &g = entries[blockIdx.y];
@@ -58,7 +83,7 @@ __global__ void k_build_ec(const OpBuildEntry *__restrict__ entries, OpDesc *ops
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
     const int k = i / N, n = i % N;
-    Ec[i] = fetch_E(g, k, n);
+    Ec[i] = g.dl ? fetch_E_dl(g, k, n) : fetch_E(g, k, n);
   }
 }
 

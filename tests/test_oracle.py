@@ -298,6 +298,15 @@ def test_double_layer_marginals_equal_statevector_sums(R, C, d, seed):
         assert np.abs(op.marginals(p, x, mask) - ref).max() < 1e-13
 
 
+def test_double_layer_square_partition():
+    c = make_circuit(4, 4, 8, 5)
+    p = op.build(4, 4, c.gates)
+    x = uniform_bitstrings(16, 3, 5)
+    ref = sv.marginals(16, c.gates, x, 0x0F0F)
+    got = np.array([op.marginal_quadrant(p, int(b), 0x0F0F) for b in x])
+    assert np.abs(got - ref).max() < 1e-13
+
+
 def test_marginals_special_cases():
     c = make_circuit(3, 3, 16, 4)
     p = op.build(3, 3, c.gates)
