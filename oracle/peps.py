@@ -134,6 +134,17 @@ class PEPS:
         self.A[q0] = np.tensordot(U[:, :, s], self.A[q0], axes=([1], [0]))
         self.A[q1] = np.tensordot(V[s], self.A[q1], axes=([1], [0]))
 
+    def apply_2q(self, q0: int, q1: int, G: np.ndarray) -> None:
+        """A general two-qubit gate G[(t0 t1), (s0 s1)] (qubit q0 first) by its
+        operator-Schmidt split (main-text "factorize": SVD, singular values
+        absorbed into U); U goes on the lower-indexed site."""
+        G4 = np.asarray(G, dtype=np.complex128).reshape(2, 2, 2, 2)
+        if q0 > q1:
+            q0, q1 = q1, q0
+            G4 = np.transpose(G4, (1, 0, 3, 2))
+        U, V = svd_split(G4)
+        self.apply_2q_split(q0, q1, U, V)
+
     def apply_cz(self, q0: int, q1: int, split: str = "projector") -> None:
         a, b = min(q0, q1), max(q0, q1)
         if split == "projector":
@@ -177,6 +188,8 @@ def build(R: int, C: int, gates, split: str = "projector", sliced=None, slice_id
             else:
                 p.apply_cz(g.qubits[0], g.qubits[1], split)
             k += 1
+        elif g.kind == "2q":
+            p.apply_2q(g.qubits[0], g.qubits[1], g.U)
         else:
             raise ValueError(g.kind)
     return p

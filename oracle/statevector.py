@@ -35,6 +35,16 @@ def apply_cz(psi: np.ndarray, n: int, q0: int, q1: int) -> None:
     v[:, 1, :, 1, :] *= -1.0
 
 
+def apply_2q(psi: np.ndarray, n: int, q0: int, q1: int, G: np.ndarray) -> None:
+    """psi <- (G acting on qubits q0, q1) psi in place; G[(t0 t1), (s0 s1)]
+    with qubit q0's bit first."""
+    G4 = np.asarray(G, dtype=np.complex128).reshape(2, 2, 2, 2)
+    v = psi.reshape([2] * n)                 # axis n-1-q holds bit q
+    a0, a1 = n - 1 - q0, n - 1 - q1
+    w = np.tensordot(G4, v, axes=([2, 3], [a0, a1]))   # new axes 0, 1 = t0, t1
+    psi[:] = np.moveaxis(w, [0, 1], [a0, a1]).reshape(-1)
+
+
 def run(n: int, gates) -> np.ndarray:
     """Final state of the gate list (objects with .kind, .qubits, .U)."""
     if n > 25:
@@ -45,6 +55,8 @@ def run(n: int, gates) -> np.ndarray:
             apply_1q(psi, n, g.qubits[0], np.asarray(g.U, dtype=np.complex128))
         elif g.kind == "cz":
             apply_cz(psi, n, g.qubits[0], g.qubits[1])
+        elif g.kind == "2q":
+            apply_2q(psi, n, g.qubits[0], g.qubits[1], g.U)
         else:
             raise ValueError(f"unknown gate kind {g.kind}")
     return psi

@@ -80,8 +80,10 @@ CZ_LAYER_ORDER = ("H00", "V00", "H10", "V10", "H01", "V01", "H11", "V11")
 @dataclass(frozen=True)
 class Gate:
     """One gate of the circuit.  kind is "1q" (qubits=(q,), U = 2x2 matrix,
-    row index = output basis state) or "cz" (qubits=(q0, q1) with q0 < q1,
-    nearest neighbours on the lattice, U = None)."""
+    row index = output basis state), "cz" (qubits=(q0, q1) with q0 < q1,
+    nearest neighbours on the lattice, U = None) or "2q" (qubits=(q0, q1)
+    nearest neighbours in either order, U = 4x4 matrix with row index
+    2*tau0 + tau1 and column index 2*sigma0 + sigma1, qubit q0 first)."""
 
     kind: str
     qubits: tuple

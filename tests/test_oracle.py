@@ -284,6 +284,80 @@ def test_quadrant_cost_matches_the_paper(L, d):
 
 
 # ---------------------------------------------------------------------------
+# General two-qubit gates (main-text "factorize": SVD split, chi_o <= 4)
+# ---------------------------------------------------------------------------
+
+PAULI = [np.eye(2), np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]),
+         np.diag([1.0, -1.0])]
+
+
+def g2(a, b, G):
+    return Gate("2q", (a, b), "G", np.asarray(G, dtype=np.complex128))
+
+
+def two_qubit_gates(rng):
+    iswap = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]])
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]])
+    rank3 = (np.kron(PAULI[0], PAULI[0]) + 0.5 * np.kron(PAULI[1], PAULI[1])
+             + 0.25 * np.kron(PAULI[2], PAULI[2]))                 # not unitary; rank 3
+    z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    q, r = np.linalg.qr(z)
+    return [iswap, cnot, rank3, q * (np.diag(r) / np.abs(np.diag(r)))]
+
+
+def circuit_with_2q(R, C, seed):
+    """H on all, then layers of random two-qubit gates on alternating edges
+    (either qubit order), single-qubit gates in between, H on all."""
+    rng = np.random.default_rng(seed)
+    gs = two_qubit_gates(rng)
+    n = R * C
+    gates = [g1(q, GATES["H"]) for q in range(n)]
+    edges = [(r * C + c, r * C + c + 1) for r in range(R) for c in range(C - 1)] + \
+            [(r * C + c, (r + 1) * C + c) for r in range(R - 1) for c in range(C)]
+    for layer in range(3):
+        for k, (a, b) in enumerate(edges):
+            if (k + layer) % 3 == 0:
+                G = gs[(k + layer) % len(gs)]
+                gates.append(g2(a, b, G) if rng.random() < 0.5 else g2(b, a, G))
+        for q in range(n):
+            gates.append(g1(q, rand_unitary(rng)))
+    return gates
+
+
+def test_statevector_2q_gate_order_and_cz():
+    # CZ through the general path equals the CZ routine; swapping the qubit
+    # order of a gate and permuting its matrix gives the same state
+    rng = np.random.default_rng(3)
+    n = 4
+    base = [g1(q, rand_unitary(rng)) for q in range(n)]
+    cz = np.diag([1, 1, 1, -1.0])
+    a = sv.run(n, base + [gcz(1, 2)])
+    b = sv.run(n, base + [g2(1, 2, cz)])
+    assert np.abs(a - b).max() < 1e-15
+    G = two_qubit_gates(rng)[3]
+    Gs = G.reshape(2, 2, 2, 2).transpose(1, 0, 3, 2).reshape(4, 4)
+    assert np.abs(sv.run(n, base + [g2(0, 1, G)]) - sv.run(n, base + [g2(1, 0, Gs)])).max() < 1e-14
+
+
+@pytest.mark.parametrize("R,C,seed", [(2, 2, 1), (2, 3, 2), (3, 3, 3)])
+def test_peps_2q_gates_equal_statevector(R, C, seed):
+    gates = circuit_with_2q(R, C, seed)
+    n = R * C
+    x = np.arange(1 << n, dtype=np.uint64)
+    ref = sv.amplitudes(n, gates, x)
+    a = op.amplitudes(op.build(R, C, gates), x)
+    assert np.abs(a - ref).max() < 1e-13
+
+
+def test_svd_split_ranks():
+    rng = np.random.default_rng(4)
+    iswap, cnot, rank3, rnd = two_qubit_gates(rng)
+    for G, k in ((iswap, 4), (cnot, 2), (rank3, 3), (rnd, 4), (np.diag([1, 1, 1, -1.0]), 2)):
+        U, V = op.svd_split(np.asarray(G, dtype=complex).reshape(2, 2, 2, 2))
+        assert U.shape[2] == k
+
+
+# ---------------------------------------------------------------------------
 # Marginals: the double-layer contraction against the state vector's sums
 # ---------------------------------------------------------------------------
 
