@@ -205,13 +205,26 @@ PEPS_API int peps_apply_1q(peps_ctx *ctx, int r, int c, const peps_c128 U[4]);
  * "factorize" and "twoqubita/b" equations with chi_o = 2). */
 PEPS_API int peps_apply_cz(peps_ctx *ctx, int r0, int c0, int r1, int c1);
 
+/* Absorb a general two-qubit gate on the nearest neighbours (r0,c0), (r1,c1),
+ * in call order with the other gates.  G is 4x4, row-major, in the basis
+ * |t0 t1> with qubit (r0,c0) first: G[(2*t0 + t1)*4 + (2*s0 + s1)].  The
+ * gate is split by its operator-Schmidt decomposition (main text,
+ * "factorize": SVD, singular values absorbed into the factor on the
+ * lower-indexed site; FP64 on the host), and the shared bond grows by the
+ * rank (1..4; CNOT 2, iSWAP and SWAP 4).  Any matrix is accepted (unitarity
+ * is not needed).  Errors: PEPS_ENOTADJ, PEPS_EINVAL (non-finite entries, a
+ * zero matrix), PEPS_EUNSUPPORTED (a bond above 2^20).  CZ gates on an edge
+ * that carries a general gate cannot be sliced or held. */
+PEPS_API int peps_apply_2q(peps_ctx *ctx, int r0, int c0, int r1, int c1, const peps_c128 G[16]);
+
 /* Bond dimension of the edge between neighbours (r0,c0), (r1,c1):
- * 2^(number of CZ gates applied to it) (paper, "chi" bound equation). */
+ * 2^(number of CZ gates applied to it) (paper, "chi" bound equation) times
+ * the ranks of the general two-qubit gates applied to it. */
 PEPS_API int peps_bond_dim(const peps_ctx *ctx, int r0, int c0, int r1, int c1, int64_t *dim);
 
 /* Static description of the contraction an amplitude call would run. */
 typedef struct {
-    int64_t n_steps;          /* site absorptions per chain (= R*C)          */
+    int64_t n_steps;          /* contraction steps per chain                  */
     int64_t max_entries;      /* largest running tensor, complex entries     */
     double flops_per_chain;   /* algorithmic real flops of one full sweep:
                                  8 * sum over steps of M*K*N                 */

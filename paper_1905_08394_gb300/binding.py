@@ -46,7 +46,8 @@ PEPS_FLAG_TIMING = 2
 PEPS_FLAG_NO_TC = 4
 PEPS_FLAG_GRAPH = 8
 
-EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_bond_dim",
+EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_apply_2q",
+            "peps_bond_dim",
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",
             "peps_get_stats", "peps_cz_count", "peps_last_error", "peps_version",
             "peps_plan_info_get", "peps_amplitudes_noalloc")
@@ -116,6 +117,8 @@ def load() -> ct.CDLL:
     lib.peps_destroy.argtypes = [P]
     lib.peps_apply_1q.argtypes = [P, ct.c_int, ct.c_int, ct.POINTER(peps_c128)]
     lib.peps_apply_cz.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, ct.c_int]
+    lib.peps_apply_2q.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
+                                  ct.POINTER(peps_c128)]
     lib.peps_bond_dim.argtypes = [P, ct.c_int, ct.c_int, ct.c_int, ct.c_int,
                                   ct.POINTER(ct.c_int64)]
     lib.peps_workspace_bytes.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
@@ -164,6 +167,14 @@ def peps_apply_1q(h, r: int, c: int, U) -> None:
 
 def peps_apply_cz(h, r0: int, c0: int, r1: int, c1: int) -> None:
     _check(load().peps_apply_cz(h, r0, c0, r1, c1))
+
+
+def peps_apply_2q(h, r0: int, c0: int, r1: int, c1: int, G) -> None:
+    """A general two-qubit gate: G 4x4, rows 2*t0 + t1, columns 2*s0 + s1,
+    qubit (r0, c0) first."""
+    G = np.asarray(G, dtype=np.complex128).reshape(4, 4)
+    arr = (peps_c128 * 16)(*[peps_c128(float(v.real), float(v.imag)) for v in G.reshape(-1)])
+    _check(load().peps_apply_2q(h, r0, c0, r1, c1, arr))
 
 
 def peps_bond_dim(h, r0: int, c0: int, r1: int, c1: int) -> int:

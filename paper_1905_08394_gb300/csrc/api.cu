@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <array>
+#include <complex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -46,10 +47,12 @@ static int fail(int code, const char *fmt, ...) {
 namespace {
 
 struct GateRec {
-  int kind;        // 0 = 1q, 1 = cz
-  int q0, q1;      // q0 < q1 for cz
-  int horiz;       // cz on a horizontal edge (same row)
+  int kind;        // 0 = 1q, 1 = cz, 2 = general two-qubit gate
+  int q0, q1;      // q0 < q1 for cz and general gates
+  int horiz;       // two-qubit gate on a horizontal edge (same row)
   double U[8];     // re, im of U00, U01, U10, U11
+  int chi = 0;     // general gate: Schmidt rank
+  std::complex<double> W0[4][4], W1[4][4];  // [s][2*tau + sigma] on q0 / q1
 };
 
 struct Launch {
@@ -94,7 +97,7 @@ struct Plan {
   int n_steps = 0;
   int lanes = 0;
   int n_groups = 0;
-  size_t off_status = 0, off_site_ptrs = 0, off_site_lo = 0, off_g1 = 0, off_cz = 0, off_opdesc = 0,
+  size_t off_status = 0, off_site_ptrs = 0, off_site_lo = 0, off_g1 = 0, off_cz = 0, off_g2 = 0, off_opdesc = 0,
          off_opbuild = 0, off_recs = 0, off_items = 0, off_fin = 0, off_acc = 0,
          off_bits = 0, off_out = 0, off_tables_end = 0;
   std::vector<size_t> site_buf_off[2];
@@ -105,7 +108,7 @@ struct Plan {
 
   // evolution batches
   struct EvoBatch {
-    int kind;             // 0 = gate1, 1 = cz
+    int kind;             // 0 = gate1, 1 = cz, 2 = general two-qubit gate
     int64_t off;          // first entry
     int n;
     int64_t max_work;
@@ -161,6 +164,8 @@ struct peps_ctx {
   int R = 0, C = 0, n = 0;
   std::vector<GateRec> gates;
   std::vector<int> ncz_h, ncz_v;  // CZ count per horizontal / vertical edge
+  std::vector<int64_t> gmul_h, gmul_v;  // product of the general gates' ranks
+  std::vector<int> ngen_h, ngen_v;      // general gates per edge
   uint64_t generation = 1;
   uint64_t built_generation = 0;
   const void *built_ws = nullptr;
@@ -189,6 +194,10 @@ extern "C" int peps_create(int R, int C, peps_ctx **out) {
   c->n = R * C;
   c->ncz_h.assign(R * std::max(C - 1, 0), 0);
   c->ncz_v.assign(std::max(R - 1, 0) * C, 0);
+  c->gmul_h.assign(c->ncz_h.size(), 1);
+  c->gmul_v.assign(c->ncz_v.size(), 1);
+  c->ngen_h.assign(c->ncz_h.size(), 0);
+  c->ngen_v.assign(c->ncz_v.size(), 0);
   *out = c;
   return PEPS_OK;
 }
@@ -234,8 +243,11 @@ extern "C" int peps_apply_cz(peps_ctx *c, int r0, int c0, int r1, int c1) {
   if (qa > qb) std::swap(qa, qb);
   const int ra = qa / c->C, ca = qa % c->C;
   const bool horiz = r0 == r1;  // by coordinates: on a one-column lattice qb == qa + 1 is vertical
-  int &cnt = horiz ? c->ncz_h[edge_h(c, ra, ca)] : c->ncz_v[edge_v(c, ra, ca)];
-  if (cnt >= 20) return fail(PEPS_EUNSUPPORTED, "peps_apply_cz: more than 20 CZ on one edge");
+  const int e = horiz ? edge_h(c, ra, ca) : edge_v(c, ra, ca);
+  int &cnt = horiz ? c->ncz_h[e] : c->ncz_v[e];
+  const int64_t gm = horiz ? c->gmul_h[e] : c->gmul_v[e];
+  if (((int64_t)1 << (cnt + 1)) * gm > ((int64_t)1 << 20))
+    return fail(PEPS_EUNSUPPORTED, "peps_apply_cz: bond dimension above 2^20 on one edge");
   cnt++;
   GateRec g{};
   g.kind = 1;
@@ -243,6 +255,123 @@ extern "C" int peps_apply_cz(peps_ctx *c, int r0, int c0, int r1, int c1) {
   g.q1 = qb;
   g.horiz = horiz ? 1 : 0;
   c->gates.push_back(g);
+  c->generation++;
+  return PEPS_OK;
+}
+
+// Operator-Schmidt split of a two-qubit gate (main text, "factorize"):
+// M[(t0 s0), (t1 s1)] = G[(t0 t1), (s0 s1)] = sum_k W0_k[t0 s0] W1_k[t1 s1]
+// with W0_k = M v_k and W1_k = conj(v_k), v_k the eigenvectors of M^H M with
+// nonzero eigenvalue (the right singular vectors; the singular values end up
+// in W0, as the paper absorbs them into U).  Cyclic complex Jacobi on the
+// 4x4 Hermitian matrix.  Returns the rank (0 for a zero matrix).
+static int split_2q(const std::complex<double> G[4][4], std::complex<double> W0[4][4],
+                    std::complex<double> W1[4][4]) {
+  typedef std::complex<double> cd;
+  cd M[4][4], H[4][4], V[4][4];
+  for (int t0 = 0; t0 < 2; ++t0)
+    for (int t1 = 0; t1 < 2; ++t1)
+      for (int s0 = 0; s0 < 2; ++s0)
+        for (int s1 = 0; s1 < 2; ++s1) M[2 * t0 + s0][2 * t1 + s1] = G[2 * t0 + t1][2 * s0 + s1];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cd acc = 0;
+      for (int k = 0; k < 4; ++k) acc += std::conj(M[k][i]) * M[k][j];
+      H[i][j] = acc;
+      V[i][j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        tot += std::norm(H[i][j]);
+        if (i != j) off += std::norm(H[i][j]);
+      }
+    if (off <= 1e-32 * tot || tot == 0) break;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 4; ++q) {
+        const double a = std::abs(H[p][q]);
+        if (a == 0) continue;
+        // rotate in the (p, q) plane: H' = J^H H J zeroes H[p][q]
+        const cd ph = H[p][q] / a;
+        const double theta = 0.5 * std::atan2(2 * a, (H[q][q] - H[p][p]).real());
+        const double cs = std::cos(theta), sn = std::sin(theta);
+        // J = [[c, s ph], [-s conj(ph), c]] on columns p, q
+        for (int k = 0; k < 4; ++k) {
+          const cd hkp = H[k][p], hkq = H[k][q];
+          H[k][p] = cs * hkp - sn * std::conj(ph) * hkq;
+          H[k][q] = sn * ph * hkp + cs * hkq;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const cd hpk = H[p][k], hqk = H[q][k];
+          H[p][k] = cs * hpk - sn * ph * hqk;
+          H[q][k] = sn * std::conj(ph) * hpk + cs * hqk;
+        }
+        for (int k = 0; k < 4; ++k) {
+          const cd vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = cs * vkp - sn * std::conj(ph) * vkq;
+          V[k][q] = sn * ph * vkp + cs * vkq;
+        }
+      }
+  }
+  int order[4] = {0, 1, 2, 3};
+  std::sort(order, order + 4, [&](int x, int y) { return H[x][x].real() > H[y][y].real(); });
+  const double lmax = H[order[0]][order[0]].real();
+  int chi = 0;
+  for (int r = 0; r < 4; ++r) {
+    const int k = order[r];
+    if (!(lmax > 0) || H[k][k].real() <= 1e-24 * lmax) break;
+    for (int i = 0; i < 4; ++i) {
+      cd acc = 0;
+      for (int j = 0; j < 4; ++j) acc += M[i][j] * V[j][k];
+      W0[chi][i] = acc;
+      W1[chi][i] = std::conj(V[i][k]);
+    }
+    ++chi;
+  }
+  return chi;
+}
+
+extern "C" int peps_apply_2q(peps_ctx *c, int r0, int c0, int r1, int c1, const peps_c128 G[16]) {
+  if (!c || !G) return fail(PEPS_EINVAL, "peps_apply_2q: NULL argument");
+  if (c->broken) return fail(PEPS_ESTATE, "context unusable after an earlier device failure");
+  if (r0 < 0 || r0 >= c->R || c0 < 0 || c0 >= c->C || r1 < 0 || r1 >= c->R || c1 < 0 ||
+      c1 >= c->C)
+    return fail(PEPS_EINVAL, "peps_apply_2q: qubit outside the %dx%d lattice", c->R, c->C);
+  if (std::abs(r0 - r1) + std::abs(c0 - c1) != 1)
+    return fail(PEPS_ENOTADJ, "peps_apply_2q: (%d,%d) and (%d,%d) are not nearest neighbours",
+                r0, c0, r1, c1);
+  std::complex<double> g[4][4];
+  for (int i = 0; i < 16; ++i) {
+    if (!std::isfinite(G[i].re) || !std::isfinite(G[i].im))
+      return fail(PEPS_EINVAL, "peps_apply_2q: non-finite matrix entry");
+    g[i / 4][i % 4] = std::complex<double>(G[i].re, G[i].im);
+  }
+  int qa = r0 * c->C + c0, qb = r1 * c->C + c1;
+  if (qa > qb) {  // the lower site first: G'[(t1 t0), (s1 s0)] = G[(t0 t1), (s0 s1)]
+    std::swap(qa, qb);
+    std::complex<double> t[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) t[((i & 1) << 1) | (i >> 1)][((j & 1) << 1) | (j >> 1)] = g[i][j];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) g[i][j] = t[i][j];
+  }
+  GateRec rec{};
+  rec.kind = 2;
+  rec.q0 = qa;
+  rec.q1 = qb;
+  const int ra = qa / c->C, ca = qa % c->C;
+  rec.horiz = (r0 == r1) ? 1 : 0;
+  rec.chi = split_2q(g, rec.W0, rec.W1);
+  if (rec.chi == 0) return fail(PEPS_EINVAL, "peps_apply_2q: zero matrix");
+  const int e = rec.horiz ? edge_h(c, ra, ca) : edge_v(c, ra, ca);
+  int64_t &gm = rec.horiz ? c->gmul_h[e] : c->gmul_v[e];
+  const int ncz = rec.horiz ? c->ncz_h[e] : c->ncz_v[e];
+  if (((int64_t)1 << ncz) * gm * rec.chi > ((int64_t)1 << 20))
+    return fail(PEPS_EUNSUPPORTED, "peps_apply_2q: bond dimension above 2^20 on one edge");
+  gm *= rec.chi;
+  (rec.horiz ? c->ngen_h[e] : c->ngen_v[e])++;
+  c->gates.push_back(rec);
   c->generation++;
   return PEPS_OK;
 }
@@ -257,8 +386,10 @@ extern "C" int peps_bond_dim(const peps_ctx *c, int r0, int c0, int r1, int c1, 
   int qa = r0 * c->C + c0, qb = r1 * c->C + c1;
   if (qa > qb) std::swap(qa, qb);
   const int ra = qa / c->C, ca = qa % c->C;
-  const int cnt = (r0 == r1) ? c->ncz_h[edge_h(c, ra, ca)] : c->ncz_v[edge_v(c, ra, ca)];
-  *dim = (int64_t)1 << cnt;
+  const bool h = r0 == r1;
+  const int e = h ? edge_h(c, ra, ca) : edge_v(c, ra, ca);
+  const int cnt = h ? c->ncz_h[e] : c->ncz_v[e];
+  *dim = ((int64_t)1 << cnt) * (h ? c->gmul_h[e] : c->gmul_v[e]);
   return PEPS_OK;
 }
 
@@ -386,8 +517,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   LegInfo L;
   L.dim_h.resize(c->ncz_h.size());
   L.dim_v.resize(c->ncz_v.size());
-  for (size_t e = 0; e < c->ncz_h.size(); ++e) L.dim_h[e] = 1 << c->ncz_h[e];
-  for (size_t e = 0; e < c->ncz_v.size(); ++e) L.dim_v[e] = 1 << c->ncz_v[e];
+  for (size_t e = 0; e < c->ncz_h.size(); ++e) L.dim_h[e] = (int)((1LL << c->ncz_h[e]) * c->gmul_h[e]);
+  for (size_t e = 0; e < c->ncz_v.size(); ++e) L.dim_v[e] = (int)((1LL << c->ncz_v[e]) * c->gmul_v[e]);
   L.fix_h.assign(c->ncz_h.size(), 0u);
   L.fix_v.assign(c->ncz_v.size(), 0u);
   P.sliced.assign(o.sliced_cz ? o.sliced_cz : nullptr, o.sliced_cz ? o.sliced_cz + o.n_sliced : nullptr);
@@ -395,6 +526,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     const uint32_t k = o.sliced_cz[j];
     if (k >= czpos.size()) return fail(PEPS_EINVAL, "sliced CZ ordinal %u out of range", k);
     const CzPos &p = czpos[k];
+    if (p.horiz ? c->ngen_h[p.edge] : c->ngen_v[p.edge])
+      return fail(PEPS_EINVAL, "CZ ordinal %u shares its edge with a general two-qubit gate "
+                  "(its bond bit is not addressable); it cannot be sliced", k);
     uint32_t &m = p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge];
     if (m & (1u << p.bit)) return fail(PEPS_EINVAL, "CZ ordinal %u sliced twice", k);
     m |= 1u << p.bit;
@@ -408,6 +542,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     if (k >= czpos.size()) return fail(PEPS_EINVAL, "fixed CZ ordinal %u out of range", k);
     if (o.fixed_s[j] > 1) return fail(PEPS_EINVAL, "fixed_s[%d] must be 0 or 1", j);
     const CzPos &p = czpos[k];
+    if (p.horiz ? c->ngen_h[p.edge] : c->ngen_v[p.edge])
+      return fail(PEPS_EINVAL, "CZ ordinal %u shares its edge with a general two-qubit gate; "
+                  "it cannot be held", k);
     uint32_t &m = p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge];
     if (m & (1u << p.bit)) return fail(PEPS_EINVAL, "CZ ordinal %u fixed or sliced twice", k);
     m |= 1u << p.bit;
@@ -865,6 +1002,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   // evolution schedule (needs only offsets)
   std::vector<Gate1Entry> g1;
   std::vector<CzEntry> cz;
+  std::vector<Gate2Entry> g2e;
   P.evo.clear();
   {
     std::vector<int> cur(NQ, 0);
@@ -877,7 +1015,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     auto start_batch = [&](int kind) {
       Plan::EvoBatch eb{};
       eb.kind = kind;
-      eb.off = kind == 0 ? (int64_t)g1.size() : (int64_t)cz.size();
+      eb.off = kind == 0 ? (int64_t)g1.size() : kind == 1 ? (int64_t)cz.size() : (int64_t)g2e.size();
       eb.n = 0;
       eb.max_work = 0;
       P.evo.push_back(eb);
@@ -889,7 +1027,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       bool clash = batch_kind != kind;
       if (!clash) {
         if (in_batch[g.q0] == batch_id) clash = true;
-        if (kind == 1 && in_batch[g.q1] == batch_id) clash = true;
+        if (kind != 0 && in_batch[g.q1] == batch_id) clash = true;
       }
       if (clash || batch_id < 0) start_batch(kind);
       Plan::EvoBatch &eb = P.evo[batch_id];
@@ -909,6 +1047,37 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         eb.n++;
         eb.max_work = std::max(eb.max_work, e.half);
         in_batch[q] = batch_id;
+      } else if (kind == 2) {
+        // general two-qubit gate: W0 on the lower site, W1 on the other; the
+        // shared leg grows by the rank (s fastest)
+        const bool horiz = g.horiz != 0;
+        const int qs[2] = {g.q0, g.q1};
+        const int axes[2] = {horiz ? 1 : 3, horiz ? 0 : 2};
+        for (int side = 0; side < 2; ++side) {
+          const int q = qs[side];
+          Gate2Entry e{};
+          e.in = site_ptr(q, cur[q]);
+          e.out = site_ptr(q, cur[q] ^ 1);
+          e.lo_off = P.site_elems[q];
+          for (int a = 0; a < 4; ++a) e.dims[a] = dims[4 * q + a];
+          e.axis = axes[side];
+          e.chi = g.chi;
+          for (int k = 0; k < g.chi; ++k)
+            for (int i = 0; i < 4; ++i) {
+              const std::complex<double> w = side ? g.W1[k][i] : g.W0[k][i];
+              const float hr = (float)w.real(), hi_ = (float)w.imag();
+              e.W_hi[k][i] = make_float2(hr, hi_);
+              e.W_lo[k][i] = make_float2((float)(w.real() - (double)hr), (float)(w.imag() - (double)hi_));
+            }
+          dims[4 * q + e.axis] *= g.chi;
+          const int64_t out_n =
+              2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
+          cur[q] ^= 1;
+          g2e.push_back(e);
+          eb.n++;
+          eb.max_work = std::max(eb.max_work, out_n);
+          in_batch[q] = batch_id;
+        }
       } else {
         const bool horiz = g.horiz != 0;
         const int qs[2] = {g.q0, g.q1};
@@ -943,6 +1112,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   }
   P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
   P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
+  P.off_g2 = off; off = align_up(off + std::max<size_t>(g2e.size(), 1) * sizeof(Gate2Entry));
 
   // operands (restricted dims): 2^nq variants per step
   const int n_ops = n_ops_total;
@@ -1317,7 +1487,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           fv = horiz ? val_h[eidx] : val_v[eidx];
         }
         pd[a] = sd[4 * q + a];
-        pfm[a] = (uint32_t)(pd[a] - 1) & ~fm;
+        // nothing fixed on this leg: the restricted index is the index
+        pfm[a] = fm ? (uint32_t)(pd[a] - 1) & ~fm : 0xFFFFFFFFu;
         pfv[a] = fv;
         prd[a] = pd[a] >> popcount32(fm);
       };
@@ -1379,6 +1550,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   put(P.off_site_lo, P.site_elems.data(), NQ * sizeof(int64_t));
   put(P.off_g1, g1.data(), g1.size() * sizeof(Gate1Entry));
   put(P.off_cz, cz.data(), cz.size() * sizeof(CzEntry));
+  put(P.off_g2, g2e.data(), g2e.size() * sizeof(Gate2Entry));
   put(P.off_opdesc, ops.data(), ops.size() * sizeof(OpDesc));
   put(P.off_opbuild, obe.data(), obe.size() * sizeof(OpBuildEntry));
   put(P.off_opbuild2, obe2.data(), obe2.size() * sizeof(OpBuild2Entry));
@@ -1492,8 +1664,10 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
     for (auto &eb : P.evo) {
       if (eb.kind == 0)
         CUDA_TRY(launch_gate1((const Gate1Entry *)(base + P.off_g1) + eb.off, eb.n, eb.max_work, s));
-      else
+      else if (eb.kind == 1)
         CUDA_TRY(launch_cz((const CzEntry *)(base + P.off_cz) + eb.off, eb.n, eb.max_work, s));
+      else
+        CUDA_TRY(launch_gate2((const Gate2Entry *)(base + P.off_g2) + eb.off, eb.n, eb.max_work, s));
       S.launches_evolve++;
     }
   } else {

@@ -157,6 +157,22 @@ struct CzEntry {     // one half of a CZ on one site tensor (out of place)
   int32_t pad_;
 };
 
+// One half of a general two-qubit gate split as sum_s W0_s (x) W1_s (main
+// text, "factorize"; rank chi <= 4): on this site
+//   A'^tau[..., i*chi + s, ...] = sum_sigma W_s[tau][sigma] A^sigma[..., i, ...]
+// (the leg `axis` grows from d to d*chi, s fastest), out of place.  W as
+// float-float: W = W_hi + W_lo, index [s][2*tau + sigma].
+struct Gate2Entry {
+  const float2 *in;
+  float2 *out;
+  int64_t lo_off;
+  int32_t dims[4];   // input l, r, u, d
+  int32_t axis;      // 0..3 = l, r, u, d
+  int32_t chi;       // Schmidt rank, 1..4
+  float2 W_hi[4][4];
+  float2 W_lo[4][4];
+};
+
 // Operand build entry (one site, one tau, one slice variant).  The four legs
 // are given by their role in the sweep that absorbs the site: l and u are
 // contracted (K = l u), r and d are new (N = r d).  For the column sweep the
@@ -167,7 +183,8 @@ struct OpBuildEntry {
   int64_t lo_off;       // entries from the hi plane to the lo plane
   int32_t dims[4];      // full dims by role l, r, u, d
   int32_t rdims[4];     // restricted dims by role
-  uint32_t free_mask[4];// bits of the full index that vary (by role)
+  uint32_t free_mask[4];// bits of the full index that vary (by role); all ones
+                        // = nothing fixed (the index is the full index)
   uint32_t fixed_val[4];// value of the fixed bits (by role)
   int64_t stride[4];    // element stride of each role's physical leg
   int64_t tau_stride;   // elements per sigma slice
@@ -242,6 +259,7 @@ cudaError_t launch_init_sites(float2 *const *bufs, const int64_t *lo_off, int n_
 cudaError_t launch_gate1(const Gate1Entry *d_entries, int n, int64_t max_half,
                          cudaStream_t s);
 cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStream_t s);
+cudaError_t launch_gate2(const Gate2Entry *d_entries, int n, int64_t max_out, cudaStream_t s);
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
                                   OpDesc *d_ops, cudaStream_t s);
 cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s);

@@ -1,5 +1,6 @@
 // Circuit evolution on the PEPS: initial product state, single-qubit gate
-// absorption (K1) and CZ absorption with bond doubling (K2).
+// absorption (K1), CZ absorption with bond doubling (K2) and general
+// two-qubit gates by their operator-Schmidt split (bond times the rank).
 //
 // Site tensor layout: complex [sigma][l][r][u][d], sigma slowest, d fastest,
 // held as float-float (a hi and a lo plane of float2, value = hi + lo).  The
@@ -148,6 +149,44 @@ __global__ void k_cz(const CzEntry *__restrict__ entries) {
   }
 }
 
+// General two-qubit gate, one half (see Gate2Entry): each thread writes one
+// output entry, mixing the two sigma slices of its input position with
+// W_s[tau][.] in float-float complex arithmetic.
+__global__ void k_gate2(const Gate2Entry *__restrict__ entries) {
+  const Gate2Entry &g = entries[blockIdx.y];
+  int od[4] = {g.dims[0], g.dims[1], g.dims[2], g.dims[3]};
+  od[g.axis] *= g.chi;
+  const int64_t half_in = (int64_t)g.dims[0] * g.dims[1] * g.dims[2] * g.dims[3];
+  const int64_t half_out = (int64_t)od[0] * od[1] * od[2] * od[3];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * half_out;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = e;
+    int idx[4];
+    idx[3] = (int)(rem % od[3]); rem /= od[3];
+    idx[2] = (int)(rem % od[2]); rem /= od[2];
+    idx[1] = (int)(rem % od[1]); rem /= od[1];
+    idx[0] = (int)(rem % od[0]); rem /= od[0];
+    const int tau = (int)rem;
+    const int s = idx[g.axis] % g.chi;
+    idx[g.axis] /= g.chi;
+    const int64_t in_e =
+        ((((int64_t)idx[0]) * g.dims[1] + idx[1]) * g.dims[2] + idx[2]) * g.dims[3] + idx[3];
+    ff re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const int64_t p = (int64_t)sg * half_in + in_e;
+      const float2 h = g.in[p], l = g.in[g.lo_off + p];
+      const float2 wh = g.W_hi[s][2 * tau + sg], wl = g.W_lo[s][2 * tau + sg];
+      ff r, i;
+      cmul_ff({wh.x, wl.x}, {wh.y, wl.y}, {h.x, l.x}, {h.y, l.y}, r, i);
+      re = ff_add(re, r);
+      im = ff_add(im, i);
+    }
+    g.out[e] = make_float2(re.hi, im.hi);
+    g.out[g.lo_off + e] = make_float2(re.lo, im.lo);
+  }
+}
+
 static int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b > 4096) b = 4096;
@@ -175,6 +214,13 @@ cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStre
   if (n <= 0) return cudaSuccess;
   dim3 grid(grid_for(max_out, 256), n);
   k_cz<<<grid, 256, 0, s>>>(d_entries);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate2(const Gate2Entry *d_entries, int n, int64_t max_out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(grid_for(max_out, 256), n);
+  k_gate2<<<grid, 256, 0, s>>>(d_entries);
   return cudaGetLastError();
 }
 

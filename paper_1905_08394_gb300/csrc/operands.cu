@@ -15,7 +15,12 @@
 
 namespace peps {
 
+// Spread the bits of v over the set bits of mask (low to high).  An all-ones
+// mask means a leg with nothing fixed: the index itself (legs whose
+// dimension is not a power of two, from general two-qubit gates, always
+// take this path since they cannot be sliced).
 __device__ __forceinline__ int deposit_bits(uint32_t v, uint32_t mask) {
+  if (mask == 0xFFFFFFFFu) return (int)v;
   uint32_t out = 0;
   for (int b = 0; b < 32 && v; ++b) {
     if (mask & (1u << b)) {

@@ -47,6 +47,9 @@ class Simulator:
             if g.kind == "1q":
                 q = g.qubits[0]
                 self.apply_1q(q // C, q % C, g.U)
+            elif g.kind == "2q":
+                a, b = g.qubits
+                B.peps_apply_2q(self.h, a // C, a % C, b // C, b % C, g.U)
             else:
                 a, b = g.qubits
                 self.apply_cz(a // C, a % C, b // C, b % C)

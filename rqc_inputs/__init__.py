@@ -237,3 +237,46 @@ def workload(name: str):
     else:
         bits = uniform_bitstrings(w["R"] * w["C"], w["bitstrings"], w["seed"])
     return circ, bits
+
+
+def two_qubit_test_gates(seed: int):
+    """Four 4x4 gate matrices (rows 2*t0 + t1, columns 2*s0 + s1): iSWAP
+    (operator-Schmidt rank 4), CNOT (rank 2), the non-unitary II + XX/2 + YY/4
+    (rank 3) and a seeded random unitary (rank 4)."""
+    rng = np.random.default_rng(seed)
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    iswap = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=np.complex128)
+    rank3 = np.eye(4, dtype=np.complex128) + 0.5 * np.kron(X, X) + 0.25 * np.kron(Y, Y)
+    z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    q, r = np.linalg.qr(z)
+    return [iswap, cnot, rank3, q * (np.diag(r) / np.abs(np.diag(r)))]
+
+
+def make_circuit_general(R: int, C: int, layers: int, seed: int) -> Circuit:
+    """H on all qubits, then `layers` rounds of two-qubit gates from
+    two_qubit_test_gates on every third edge (rotating), each in a random
+    qubit order, each round followed by a random single-qubit unitary on every
+    qubit; H on all at the end.  Seeded (numpy default_rng(seed))."""
+    rng = np.random.default_rng(seed)
+    gs = two_qubit_test_gates(seed)
+    n = R * C
+    circ = Circuit(R, C, layers, seed)
+    circ.gates = [Gate("1q", (q,), "H", GATES["H"]) for q in range(n)]
+    edges = [(r * C + c, r * C + c + 1) for r in range(R) for c in range(C - 1)] + \
+            [(r * C + c, (r + 1) * C + c) for r in range(R - 1) for c in range(C)]
+    for layer in range(layers):
+        for k, (a, b) in enumerate(edges):
+            if (k + layer) % 3 == 0:
+                G = gs[(k + layer) % len(gs)]
+                qs = (a, b) if rng.random() < 0.5 else (b, a)
+                if qs[0] > qs[1]:   # the matrix is given with qubit qs[0] first
+                    G = G.reshape(2, 2, 2, 2).transpose(1, 0, 3, 2).reshape(4, 4)
+                circ.gates.append(Gate("2q", qs, "G", G))
+        for q in range(n):
+            z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+            u, rr = np.linalg.qr(z)
+            circ.gates.append(Gate("1q", (q,), "U", u * (np.diag(rr) / np.abs(np.diag(rr)))))
+    circ.gates += [Gate("1q", (q,), "H", GATES["H"]) for q in range(n)]
+    return circ

@@ -225,6 +225,31 @@ def test_quadrant_plan_rejects_bad_requests():
     B.peps_destroy(h)
 
 
+def test_general_two_qubit_gates_grow_the_bond_by_their_rank():
+    from rqc_inputs import two_qubit_test_gates
+    iswap, cnot, rank3, rnd = two_qubit_test_gates(1)
+    h = B.peps_create(2, 3)
+    B.peps_apply_2q(h, 0, 0, 0, 1, iswap)
+    assert B.peps_bond_dim(h, 0, 0, 0, 1) == 4
+    B.peps_apply_2q(h, 0, 1, 0, 0, cnot)          # either qubit order
+    assert B.peps_bond_dim(h, 0, 0, 0, 1) == 8
+    B.peps_apply_2q(h, 0, 1, 1, 1, rank3)
+    assert B.peps_bond_dim(h, 0, 1, 1, 1) == 3
+    B.peps_apply_cz(h, 0, 1, 1, 1)
+    assert B.peps_bond_dim(h, 0, 1, 1, 1) == 6
+    B.peps_apply_2q(h, 1, 1, 1, 2, np.diag([1, 1, 1, -1.0]))   # CZ as a general gate
+    assert B.peps_bond_dim(h, 1, 1, 1, 2) == 2
+    with pytest.raises(B.PepsError):
+        B.peps_apply_2q(h, 0, 0, 1, 1, rnd)       # not neighbours
+    with pytest.raises(B.PepsError):
+        B.peps_apply_2q(h, 0, 0, 0, 1, np.zeros((4, 4)))
+    # a CZ on an edge with a general gate cannot be sliced
+    o, k = B.make_opts(precision="fp32", sliced_cz=[0])
+    with pytest.raises(B.PepsError):
+        B.peps_plan_info_get(h, 1, o)
+    B.peps_destroy(h)
+
+
 def test_slicing_plan():
     c, h = make(5, 5, 16, 2)
     ncz = B.peps_cz_count(h)
