@@ -26,12 +26,14 @@ Follows the paper step by step, in plain NumPy (complex128):
   the paper allows when the lattice is wider than tall).  Each absorption is
   one np.tensordot over the legs the running tensor shares with the site.
 
-* Square partition (supplementary, Fig. S2(b) and the "spacesquareeven" /
-  "timesquareeven" equations), for even side lengths: the lattice is split
-  into four quarters; each quarter's projected sites are contracted into one
-  tensor (F_ul, F_ur, F_bl, F_br) whose open legs are the edges it shares with
-  its neighbouring quarters; then F_ul is contracted with F_ur and F_bl with
-  F_br, and the two results with each other.
+* Square partition (supplementary, Fig. S2(b) and (c) and the "spacesquare*"
+  / "timesquare*" equations): the lattice is split into four parts (four
+  quarters for even sides; for an odd side 2m+1 an (m+1) x m, an
+  (m+1) x (m+1) part holding the centre site, an m x (m+1) and an m x m
+  part); each part's projected sites are contracted into one tensor (F_ul,
+  F_ur, F_bl, F_br) whose open legs are the edges it shares with the other
+  parts; then F_ul is contracted with F_ur and F_bl with F_br, and the two
+  results with each other.
 
 * Marginals (the main text's remark on measuring a subset of qubits):
   P(x_S) = <psi| Pi_S |psi> is the same network with every site replaced by
@@ -307,21 +309,29 @@ def marginals(peps: PEPS, bitstrings, mask: int) -> np.ndarray:
 
 
 def quadrant_sites(R: int, C: int):
-    """The four quarters of an even R x C lattice (supplementary Fig. S2(b)):
-    {"ul", "ur", "bl", "br"} -> their sites in contraction order.  Every
-    quarter is contracted row by row starting from its corner of the lattice
-    (the upper-left quarter's order, mirrored), so the open legs toward the
-    other quarters appear last and every quarter costs the same."""
-    if R % 2 or C % 2:
-        raise ValueError("the square partition needs even side lengths")
-    h, w = R // 2, C // 2
-    out = {}
-    for name, rows, cols in (("ul", range(0, h), range(0, w)),
-                             ("ur", range(0, h), range(C - 1, w - 1, -1)),
-                             ("bl", range(R - 1, h - 1, -1), range(0, w)),
-                             ("br", range(R - 1, h - 1, -1), range(C - 1, w - 1, -1))):
-        out[name] = [r * C + c for r in rows for c in cols]
-    return out
+    """The four parts of the square partition: {"ul", "ur", "bl", "br"} ->
+    their sites in contraction order.  Even R and C (supplementary Fig.
+    S2(b)): four R/2 x C/2 quarters.  Odd square side 2m+1 (Fig. S2(c)):
+    ul = rows 0..m x cols 0..m-1 ((m+1) x m), ur = rows 0..m x cols m..2m
+    ((m+1) x (m+1), holding the centre site), bl = rows m+1..2m x cols 0..m
+    (m x (m+1)) and br = rows m+1..2m x cols m+1..2m (m x m).  Every part is
+    contracted row by row starting from its corner of the lattice, so the
+    open legs toward the other parts appear last."""
+    if R % 2 == 0 and C % 2 == 0:
+        h, w = R // 2, C // 2
+        parts = (("ul", range(0, h), range(0, w)),
+                 ("ur", range(0, h), range(C - 1, w - 1, -1)),
+                 ("bl", range(R - 1, h - 1, -1), range(0, w)),
+                 ("br", range(R - 1, h - 1, -1), range(C - 1, w - 1, -1)))
+    elif R == C and R % 2 == 1 and R >= 3:
+        m = R // 2
+        parts = (("ul", range(0, m + 1), range(0, m)),
+                 ("ur", range(0, m + 1), range(C - 1, m - 1, -1)),
+                 ("bl", range(R - 1, m, -1), range(0, m + 1)),
+                 ("br", range(R - 1, m, -1), range(C - 1, m, -1)))
+    else:
+        raise ValueError("the square partition needs even sides or an odd square")
+    return {name: [r * C + c for r in rows for c in cols] for name, rows, cols in parts}
 
 
 def merge(a, b):

@@ -123,7 +123,9 @@ struct Plan {
   struct Quarter {
     int first = 0, count = 0;  // its sweep's steps
     int64_t batch = 1, rest = 1;  // stored as [batch][rest]
+    int64_t rest_last = 1;     // dim of the fastest rest leg
   } quarter[4];                 // ul, bl, ur, br
+  bool odd = false;             // odd-side partition (Fig. S2(c))
   int s_m1 = -1, s_m2 = -1;     // merge steps F_l = F_ul F_bl, Y = F_br F_l^T
   int op_m1 = -1, op_m2 = -1;
   int n_site_ops = 0;           // ops rebuilt from the site tensors per slice
@@ -492,10 +494,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   const bool dl = (o.flags & PEPS_FLAG_MARGINALS) != 0;
   if (dl && (o.n_sliced > 0 || o.n_fixed > 0))
     return fail(PEPS_EINVAL, "marginals do not combine with slicing or held CZ bits");
-  if (quad && (R % 2 || C % 2))
-    return fail(PEPS_EINVAL, "the square partition needs even R and C (got %d x %d)", R, C);
-  if (quad && o.prefix_cols != 0 && o.prefix_cols != C / 2)
+  // even R and C: Fig. S2(b); an odd square side 2m+1: Fig. S2(c)
+  const bool odd = quad && (R % 2 || C % 2);
+  if (odd && (R != C || R < 3))
+    return fail(PEPS_EINVAL, "the square partition needs even R and C, or R = C odd (got %d x %d)",
+                R, C);
+  if (quad && !odd && o.prefix_cols != 0 && o.prefix_cols != C / 2)
     return fail(PEPS_EINVAL, "with the square partition prefix_cols must be 0 or C/2");
+  if (odd && o.prefix_cols != 0)
+    return fail(PEPS_EINVAL, "the odd-side partition takes no prefix groups");
   if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster))
     return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128 and tc_cluster 0, 1 or 2");
   if (o.n_fixed > 0 && (!o.fixed_cz || !o.fixed_s)) return fail(PEPS_EINVAL, "fixed_cz / fixed_s is NULL");
@@ -869,6 +876,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           return fail(PEPS_EINVAL, "internal: quarter %d final leg order", qi);
         Q.rest *= legs[i].dim;
       }
+      Q.rest_last = legs[Hs - 1].dim;
       Q.batch = B;
       Q.count = (int)P.steps.size() - Q.first;
       return PEPS_OK;
@@ -904,19 +912,49 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       return (int)PEPS_OK;
     };
     int rc;
-    if ((rc = plan_quarter(0, {1, 0, 0}, w, h))) return rc;   // ul
-    if ((rc = plan_quarter(1, {1, 1, 0}, w, h))) return rc;   // bl
-    const Plan::Quarter &ul = P.quarter[0], &bl = P.quarter[1];
-    if (ul.rest != bl.rest) return fail(PEPS_EINVAL, "internal: ul / bl cut dims differ");
-    P.s_m1 = (int)P.steps.size();
-    if ((rc = add_merge(merge_shape(ul.batch, ul.rest, bl.batch)))) return rc;
-    if ((rc = plan_quarter(2, {0, 0, 1}, h, w))) return rc;   // ur
-    if ((rc = plan_quarter(3, {0, 1, 1}, h, w))) return rc;   // br
-    const Plan::Quarter &ur = P.quarter[2], &br = P.quarter[3];
-    if (br.rest != bl.batch || br.batch != ur.batch || ul.batch != ur.rest)
-      return fail(PEPS_EINVAL, "internal: quarter cut dims differ");
-    P.s_m2 = (int)P.steps.size();
-    if ((rc = add_merge(merge_shape(br.batch, br.rest, ul.batch)))) return rc;
+    P.odd = odd;
+    if (!odd) {
+      if ((rc = plan_quarter(0, {1, 0, 0}, w, h))) return rc;   // ul
+      if ((rc = plan_quarter(1, {1, 1, 0}, w, h))) return rc;   // bl
+      const Plan::Quarter &ul = P.quarter[0], &bl = P.quarter[1];
+      if (ul.rest != bl.rest) return fail(PEPS_EINVAL, "internal: ul / bl cut dims differ");
+      P.s_m1 = (int)P.steps.size();
+      if ((rc = add_merge(merge_shape(ul.batch, ul.rest, bl.batch)))) return rc;
+      if ((rc = plan_quarter(2, {0, 0, 1}, h, w))) return rc;   // ur
+      if ((rc = plan_quarter(3, {0, 1, 1}, h, w))) return rc;   // br
+      const Plan::Quarter &ur = P.quarter[2], &br = P.quarter[3];
+      if (br.rest != bl.batch || br.batch != ur.batch || ul.batch != ur.rest)
+        return fail(PEPS_EINVAL, "internal: quarter cut dims differ");
+      P.s_m2 = (int)P.steps.size();
+      if ((rc = add_merge(merge_shape(br.batch, br.rest, ul.batch)))) return rc;
+    } else {
+      // odd side L = 2m+1 (Fig. S2(c)): ul = rows 0..m x cols 0..m-1, ur =
+      // rows 0..m x cols m..2m (holds the centre site), bl = rows m+1..2m x
+      // cols 0..m, br = rows m+1..2m x cols m+1..2m, swept from their corners:
+      //   F_ul = [horizontal cut, cols 0..m-1][upper vertical cut, rows 0..m]
+      //   F_ur = [upper vertical cut, rows 0..m][horizontal cut, cols 2m..m]
+      //   F_bl = [horizontal cut, cols 0..m][lower vertical cut, rows 2m..m+1]
+      //   F_br = [lower vertical cut, rows 2m..m+1][horizontal cut, cols 2m..m+1]
+      // F_u = F_ul F_ur (ur's operand with col m moved to the front of N) and
+      // F_b = F_bl F_br are then both [cols 0..m][cols 2m..m+1], and the
+      // amplitude is their dot product: the paper's order (upper-left with
+      // upper-right, bottom-left with bottom-right, then the halves).
+      const int m = R / 2;
+      if ((rc = plan_quarter(0, {0, 0, 0}, m + 1, m))) return rc;       // ul
+      if ((rc = plan_quarter(2, {1, 0, 1}, m + 1, m + 1))) return rc;   // ur
+      const Plan::Quarter &ul = P.quarter[0], &ur = P.quarter[2];
+      if (ul.rest != ur.batch) return fail(PEPS_EINVAL, "internal: ul / ur cut dims differ");
+      P.s_m1 = (int)P.steps.size();
+      if ((rc = add_merge(merge_shape(ul.batch, ul.rest, ur.rest)))) return rc;
+      if ((rc = plan_quarter(1, {0, 1, 0}, m, m + 1))) return rc;       // bl
+      if ((rc = plan_quarter(3, {1, 1, 1}, m, m))) return rc;           // br
+      const Plan::Quarter &bl = P.quarter[1], &br = P.quarter[3];
+      if (bl.rest != br.batch) return fail(PEPS_EINVAL, "internal: bl / br cut dims differ");
+      if (ul.batch * ur.rest != bl.batch * br.rest)
+        return fail(PEPS_EINVAL, "internal: the halves' cut dims differ");
+      P.s_m2 = (int)P.steps.size();
+      if ((rc = add_merge(merge_shape(bl.batch, bl.rest, br.rest)))) return rc;
+    }
     P.n_site_ops = n_ops_total;
     P.op_m1 = n_ops_total++;
     P.op_m2 = n_ops_total++;
@@ -1234,6 +1272,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       t.G = (const void *)(REL + g_rel);
       t.ks = 1;
       t.ns = ns;
+      t.ns_hi = 0;
+      t.Nlo = N;
       t.K = (int)K;
       t.N = (int)N;
       t.rec = rec;
@@ -1251,7 +1291,65 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       tops.push_back(t);
       P.launches.push_back(ln);
     };
-    for (int g = 0; g < P.n_groups; ++g) {
+    if (P.odd) {
+      // per bitstring: ul, ur -> F_u (group buffers); bl, br -> F_b (lane 0's
+      // buffers); amplitude = F_u . F_b
+      for (int64_t i = 0; i < n; ++i) {
+        const int64_t chain = i;
+        auto ch = [&](int) { return chain; };
+        auto bit = [&](int) { return i; };
+        const int bul = sweep(ul, 1, ch, bit, [&](int, int b) { return pre_buf(b); });
+        const int bur = sweep(ur, 1, ch, bit, [&](int, int b) { return pre_buf(2 + b); });
+        const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
+        const int rec_ur = (int)(chain * NS + ur.first + ur.count - 1);
+        const int rec_u = (int)(chain * NS + P.s_m1);
+        // Ec[k][n'] from F_ur[k][rest]: n' = (col m, cols 2m..m+1) while the
+        // rest is (cols 2m..m+1, col m), col m the fastest rest leg
+        tensor_op(pre_buf(2 + bur), ur.batch, ur.rest, ur.rest_last, rec_ur, P.op_m1, P.s_m1);
+        tops.back().ks = ur.rest;
+        tops.back().ns_hi = 1;
+        tops.back().Nlo = ur.rest / ur.rest_last;
+        {
+          StepItem it{};
+          it.op_base = P.op_m1;
+          it.in_rec = rec_ul;
+          it.out_rec = rec_u;
+          RelItem ri{pre_buf(bul), pre_buf(bul ^ 1), false, i};
+          add_step_launch(P.s_m1, {it}, {ri}, 1);
+        }
+        const int bbl = sweep(bl, 1, ch, bit, [&](int, int b) { return lane_buf(0, b); });
+        const int bbr = sweep(br, 1, ch, bit, [&](int, int b) { return lane_buf(0, 2 + b); });
+        const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
+        const int rec_br = (int)(chain * NS + br.first + br.count - 1);
+        const int rec_b = (int)(chain * NS + P.s_m2);
+        // F_br = [K][N] row-major: Ec[k][n] = F_br[k N + n]
+        tensor_op(lane_buf(0, 2 + bbr), br.batch, br.rest, 1, rec_br, P.op_m2, P.s_m2);
+        tops.back().ks = br.rest;
+        {
+          StepItem it{};
+          it.op_base = P.op_m2;
+          it.in_rec = rec_bl;
+          it.out_rec = rec_b;
+          RelItem ri{lane_buf(0, bbl), lane_buf(0, bbl ^ 1), false, i};
+          add_step_launch(P.s_m2, {it}, {ri}, 1);
+        }
+        Launch dl{};
+        dl.kind = 3;
+        dl.aux_off = (int64_t)dots.size();
+        dl.n_aux = 1;
+        dl.flops = dl.bytes = 0;
+        DotEntry d{};
+        d.Y = (const void *)(REL + pre_buf(bul ^ 1));
+        d.F = (const void *)(REL + lane_buf(0, bbl ^ 1));
+        d.n = ul.batch * ur.rest;
+        d.rec_y = rec_u;
+        d.rec_f = rec_b;
+        d.out_index = (int)i;
+        dots.push_back(d);
+        P.launches.push_back(dl);
+      }
+    }
+    for (int g = 0; g < (P.odd ? 0 : P.n_groups); ++g) {
       const int64_t chain = g, first = (int64_t)g * gs;
       auto gch = [&](int) { return chain; };
       auto gbit = [&](int) { return first; };
@@ -1738,7 +1836,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
         CUDA_TRY(launch_operand_bounds(1, ops + l.op, s));
         S.launches_operand += 2;
         if (l.tc) {
-          CUDA_TRY(launch_build_tc_operands(1, (int)l.kn, ops + l.op, P.fmt, s));
+          CUDA_TRY(launch_build_tc_operands(1, l.kn, ops + l.op, P.fmt, s));
           S.launches_operand++;
         }
       } else if (l.kind == 3) {

@@ -211,12 +211,16 @@ struct OpBuild2Entry {
 };
 
 // Operand of a merge built from a finished quarter (or half) tensor G held in
-// the running-tensor format:  Ec[k][n] = G[k ks + n ns] 2^-target (so that
-// |Ec| <= 1), and e_c of the op = exp(G's record) - target, which carries
-// G's scale into the merge's output exponent.
+// the running-tensor format:  Ec[k][n] = G[k ks + n_hi ns_hi + n_lo ns] 2^-target
+// with n = n_hi * Nlo + n_lo (so that |Ec| <= 1), and e_c of the op =
+// exp(G's record) - target, which carries G's scale into the merge's output
+// exponent.  The two-level N index reorders the operand's columns (a leg
+// moved to the front); Nlo = N gives the plain strided gather.
 struct TensorOpEntry {
   const void *G;
-  int64_t ks, ns;       // element strides of the operand's K and N indices
+  int64_t ks, ns;       // element strides of the operand's K and (low) N indices
+  int64_t ns_hi;        // element stride of the high N index
+  int64_t Nlo;          // size of the low N index
   int32_t K, N;
   int32_t rec;          // G's record
   int32_t op;           // OpDesc to fill
@@ -272,7 +276,7 @@ cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s);
 // Tensor-core planes (and their bound) of ops [0, n_ops) from their Ec.
-cudaError_t launch_build_tc_operands(int n_ops, int max_kn, OpDesc *d_ops, int fmt,
+cudaError_t launch_build_tc_operands(int n_ops, int64_t max_kn, OpDesc *d_ops, int fmt,
                                      cudaStream_t s);
 cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, int n_items,
                                  const OpDesc *d_ops, Rec *d_recs, const DeviceStatus *st,

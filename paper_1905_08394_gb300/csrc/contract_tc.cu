@@ -892,10 +892,11 @@ __global__ void k_build_bt(OpDesc *ops) {
   OpDesc &op = ops[blockIdx.y];
   if (op.Bt[0] == nullptr) return;
   const int K = op.K, N = op.N;
-  const int Kr = 2 * K, Nr = 2 * N;
+  const int64_t Kr = 2 * (int64_t)K, Nr = 2 * (int64_t)N;
   const float sc = ldexpf(1.f, op.b_t);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Kr * Nr; i += gridDim.x * blockDim.x) {
-    const int nr = i / Kr, kr = i - nr * Kr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Kr * Nr;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nr = i / Kr, kr = i - nr * Kr;
     const int k = kr >> 1, a = kr & 1, n = nr >> 1, b = nr & 1;
     const float2 e = op.Ec[(int64_t)k * N + n];
     float v;
@@ -926,10 +927,10 @@ __global__ void k_build_bt(OpDesc *ops) {
   }
 }
 
-cudaError_t launch_build_tc_operands(int n, int max_kn, OpDesc *d_ops, int fmt,
+cudaError_t launch_build_tc_operands(int n, int64_t max_kn, OpDesc *d_ops, int fmt,
                                      cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int blocks = (4 * max_kn + 255) / 256;
+  int64_t blocks = (4 * max_kn + 255) / 256;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
   dim3 grid(blocks, n);

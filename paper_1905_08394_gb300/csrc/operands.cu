@@ -216,7 +216,8 @@ __global__ void k_tensor_op(const TensorOpEntry *__restrict__ e, int64_t plane, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i / g.N, n = i - k * g.N;
-    const float2 v = load_g<FMT>(g.G, k * g.ks + n * g.ns, plane);
+    const int64_t nh = n / g.Nlo, nl = n - nh * g.Nlo;
+    const float2 v = load_g<FMT>(g.G, k * g.ks + nh * g.ns_hi + nl * g.ns, plane);
     Ec[i] = make_float2(v.x * sc, v.y * sc);
   }
 }

@@ -253,9 +253,53 @@ def test_quadrant_equals_column_sweep_6x6():
     assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
 
 
-def test_quadrant_needs_even_sides():
+def test_quadrant_needs_even_sides_or_an_odd_square():
     with pytest.raises(ValueError):
         op.quadrant_sites(5, 6)
+    with pytest.raises(ValueError):
+        op.quadrant_sites(5, 7)
+    parts = op.quadrant_sites(7, 7)
+    assert sorted(q for v in parts.values() for q in v) == list(range(49))
+    assert [len(parts[k]) for k in ("ul", "ur", "bl", "br")] == [12, 16, 12, 9]
+
+
+@pytest.mark.parametrize("L,d,seed", [(3, 8, 1), (3, 16, 2), (3, 24, 3)])
+def test_odd_partition_equals_statevector(L, d, seed):
+    c = make_circuit(L, L, d, seed)
+    n = L * L
+    x = np.arange(1 << n, dtype=np.uint64) if n <= 9 else uniform_bitstrings(n, 16, seed)
+    ref = sv.amplitudes(n, c.gates, x)
+    assert np.abs(op.amplitudes_quadrant(op.build(L, L, c.gates), x) - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("L,d,seed", [(5, 16, 3), (7, 16, 4)])
+def test_odd_partition_equals_column_sweep(L, d, seed):
+    c = make_circuit(L, L, d, seed)
+    x = uniform_bitstrings(L * L, 3, seed)
+    p = op.build(L, L, c.gates)
+    a, b = op.amplitudes_quadrant(p, x), op.amplitudes(p, x)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("L,d", [(7, 40), (9, 40), (7, 24)])
+def test_odd_partition_cost_matches_the_paper(L, d):
+    # Eq. (timesquareodd): (2^k + 1) 2^(k (3L - 1) / 2) for the merges;
+    # Eq. (spacesquareodd): 2^(k (L + 1)) + 2^(k L): the largest part and one more
+    from paper_1905_08394_gb300 import complexity as cx
+    k = -(-d // 8)
+    chi = 2 ** k
+    dims = {}
+    for r in range(L):
+        for cc in range(L):
+            q = r * L + cc
+            if cc + 1 < L:
+                dims[(q, q + 1)] = chi
+            if r + 1 < L:
+                dims[(q, q + L)] = chi
+    cost = op.quadrant_contraction_cmacs(L, L, dims)
+    # the two pair merges give the formula; the last merge adds chi^L
+    assert cost["merges"] == cx.time_square_odd(L, d) + chi ** L
+    assert cost["largest"] + chi ** L == cx.space_square_odd(L, d)
 
 
 @pytest.mark.parametrize("L,d", [(6, 32), (8, 40), (6, 24)])
