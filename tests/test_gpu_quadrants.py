@@ -151,3 +151,42 @@ def test_autotune_chooses_an_order_and_caches_it(sim_factory, tmp_path):
     ref = op.amplitudes(op.build(6, 6, circ.gates), bits)
     out = sim.amplitudes(bits, **kw, **best)
     assert relerr(out, ref) < SPLIT_TOL
+
+
+# ---------------------------------------------------------------------------
+# Odd side (Fig. S2(c)): ul (m+1) x m, ur (m+1) x (m+1) with the centre site,
+# bl m x (m+1), br m x m; F_u = F_ul F_ur, F_b = F_bl F_br, amplitude F_u . F_b
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_odd_3x3_against_the_state_vector(sim_factory, prec):
+    circ = make_circuit(3, 3, 16, 31)
+    x = np.arange(512, dtype=np.uint64)
+    ref = sv.amplitudes(9, circ.gates, x)
+    sim = sim_factory(circ)
+    assert relerr(sim.amplitudes(x, precision=prec, **QUAD), ref) < SPLIT_TOL
+
+
+def test_odd_5x5_against_the_column_oracle(sim_factory):
+    circ = make_circuit(5, 5, 16, 32)
+    x = uniform_bitstrings(25, 16, 32)
+    ref = op.amplitudes(op.build(5, 5, circ.gates), x)
+    sim = sim_factory(circ)
+    for prec in ("fp32", "fp16x3", "bf16x3"):
+        assert relerr(sim.amplitudes(x, precision=prec, **QUAD), ref) < tol_for(prec, 22), prec
+
+
+def test_odd_7x7_d24_against_the_golden_values(sim_factory):
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_7x7_d24.json")) as f:
+        g = json.load(f)
+    circ = make_circuit(7, 7, 24, 5)
+    x = np.array(g["bitstrings"], dtype=np.uint64)
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])
+    sim = sim_factory(circ)
+    for prec in ("fp32", "fp16x3"):
+        assert relerr(sim.amplitudes(x, precision=prec, **QUAD), ref) < SPLIT_TOL, prec
+    # and the two schemes agree
+    assert relerr(sim.amplitudes(x, precision="fp16x3", **QUAD), sim.amplitudes(x, precision="fp16x3")) < 2 * SPLIT_TOL
