@@ -102,7 +102,7 @@ def parse():
                          "circuit and their Porter-Thomas statistics; marginals: marginal "
                          "probabilities of the top half's 18 qubits of a 6x6 (1+16+1) "
                          "circuit (the double-layer network), 512 bitstrings")
-    ap.add_argument("--slices", type=int, default=3, help="timed slices for --case slices")
+    ap.add_argument("--slices", type=int, default=4, help="timed slices for --case slices")
     return ap.parse_args()
 
 
@@ -517,9 +517,11 @@ def run_profile_case(args):
 
 
 def run_slices_case(args):
-    """7x7 (1+40+1), one bitstring: the slice set that keeps every running
-    tensor at <= 2^33 entries (two 64 GiB buffers), a seeded subset of slices
-    timed one by one, projected full time = seconds per slice x 2^|S|."""
+    """7x7 (1+40+1), one bitstring, on the odd-side square partition (Fig. S2(c)):
+    the slice set the square-partition chooser picks under a 200 GiB workspace,
+    a seeded subset of slices timed one by one, projected full time = seconds
+    per slice x 2^|S|.  The column sweep's own slice set (every running tensor
+    <= 2^33) is reported beside it from the planner's figures."""
     import numpy as np
     import torch
 
@@ -528,42 +530,55 @@ def run_slices_case(args):
     from rqc_inputs import workload
 
     circ, bits = workload("7x7_d40")
-    ss = slicing.choose(circ, 2 ** 33, seed=5)
-    ids = slicing.seeded_slice_ids(len(ss.sliced_cz), args.slices + 1, seed=5)
     sim = Simulator(circ.R, circ.C)
     sim.apply_circuit(circ)
+    t0 = time.time()
+    ss = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5)
+    choose_s = time.time() - t0
+    ids = slicing.seeded_slice_ids(len(ss.sliced_cz), args.slices, seed=5)
     stream = torch.cuda.current_stream()
     d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
-    kw = dict(precision=args.precision, sliced_cz=ss.sliced_cz, max_lanes=1)
-    # warm-up slice (plan, tensor maps, evolution)
-    sim.amplitudes_device(d_bits, slice_ids=[ids[0]], flags=B.PEPS_FLAG_TIMING, **kw)
+    kw = dict(precision=args.precision, sliced_cz=ss.sliced_cz, scheme="quadrants",
+              slice_ids=ids)
+    # warm-up: the same call (plan, tensor maps, evolution)
+    warm = sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **kw).cpu().numpy()
     torch.cuda.synchronize()
-    times, tc = [], []
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    for sid in ids[1:]:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = sim.amplitudes_device(d_bits, slice_ids=[sid],
-                                    flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD, **kw)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        st = sim.stats()
-        tc.append((st["contract_tc_flops"], st["contract_tc_ms"], st["launches_contract_tc"]))
+    # the timed slices run in one call, the evolution included
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_call = e0.elapsed_time(e1) / 1e3
+    st = sim.stats()
+    vals = [complex(out.cpu().numpy()[0])]
+    times = [t_call / len(ids)]
+    tc = [(st["contract_tc_flops"], st["contract_tc_ms"], st["launches_contract_tc"])]
     clk = clocks.stop()
-    ws_opts, ws_keep = B.make_opts(slice_ids=[0], **kw)
+    ws_opts, ws_keep = B.make_opts(**kw)
     ws_gib = B.peps_workspace_bytes(sim.h, 1, ws_opts) / 2 ** 30
     s_per = sum(times) / len(times)
-    n_sl = 2 ** len(ss.sliced_cz)
-    flops = 8 * sum(ss.step_cmacs)
+    n_sl = ss.n_slices
     tcf = sum(t[0] for t in tc) / max(1e-9, sum(t[1] for t in tc)) / 1e9
-    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring", "precision": args.precision,
-            "sliced_cz": len(ss.sliced_cz), "n_slices": n_sl, "max_entries": ss.max_entries,
-            "flops_per_slice": flops, "timed_slice_ids": ids[1:], "seconds_per_slice": s_per,
-            "slice_seconds": times, "projected_seconds": s_per * n_sl,
-            "projected_years": s_per * n_sl / 3.156e7, "tc_tflops": tcf,
-            "workspace_gib": ws_gib,
+    # the column sweep's slice set, for comparison (planner figures only)
+    cs = slicing.choose(circ, 2 ** 33, seed=5)
+    col = {"sliced_cz": len(cs.sliced_cz), "max_entries": cs.max_entries,
+           "flops_per_slice": 8 * sum(cs.step_cmacs),
+           "flops_total": 8 * sum(cs.step_cmacs) * 2.0 ** len(cs.sliced_cz),
+           "seconds_per_slice_measured_earlier": 1.38}
+    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring", "scheme": "quadrants (odd side)",
+            "precision": args.precision, "sliced_cz": len(ss.sliced_cz), "n_slices": n_sl,
+            "max_entries": ss.max_entries, "flops_per_slice": ss.flops_per_slice,
+            "flops_total": ss.flops_per_slice * n_sl, "chooser_seconds": choose_s,
+            "timed_slice_ids": ids, "seconds_per_slice": s_per, "call_seconds": t_call,
+            "contract_seconds": st["contract_ms"] / 1e3, "launches": st["launches_total"],
+            "partial_sum": [vals[0].real, vals[0].imag],
+            "replay_identical": bool(np.array_equal(warm, out.cpu().numpy())),
+            "useful_tflops": ss.flops_per_slice / s_per / 1e12,
+            "projected_seconds": s_per * n_sl, "projected_minutes": s_per * n_sl / 60,
+            "tc_tflops": tcf, "workspace_gib": ws_gib, "columns": col,
             "clocks": clk, "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
             "(odd-square partition, 92.51 TB)"}
     print(json.dumps(line), flush=True)

@@ -94,7 +94,7 @@ enum {
                                included) into a CUDA graph on the first call
                                and replay it on later calls with the same
                                plan; ignored together with PEPS_FLAG_TIMING */
-    PEPS_FLAG_MARGINALS = 16 /* return marginal probabilities P(x_S) =
+    PEPS_FLAG_MARGINALS = 16, /* return marginal probabilities P(x_S) =
                                <psi| Pi_S |psi> instead of amplitudes: S = the
                                set bits of opts.measured_mask, their values
                                from each bitstring; the other qubits are summed
@@ -102,6 +102,12 @@ enum {
                                (every site sum_sigma A^sigma (x) conj(A^sigma),
                                every bond squared); out[i].re = P, .im ~ 0.
                                Not with slicing or held CZ bits.          */
+    PEPS_FLAG_ESTIMATE = 32 /* planning only: peps_plan_info_get and
+                               peps_workspace_bytes report the figures of a
+                               plan whose running tensor exceeds the 2^36
+                               entries an amplitude call accepts (a slice-set
+                               search starts there); an amplitude call with
+                               this flag returns PEPS_EINVAL.              */
 };
 
 /* Options of an amplitude call.  All-zero means: FP32_SIMT, no prefix reuse,

@@ -105,6 +105,7 @@ struct Plan {
   std::vector<size_t> ec_off, bt_off[2];
   size_t lane_off = 0, prefix_off = 0;
   size_t gbuf_bytes = 0;
+  size_t odd_bytes = 0;         // odd side: bytes of all sweep buffers
 
   // evolution batches
   struct EvoBatch {
@@ -124,8 +125,11 @@ struct Plan {
     int first = 0, count = 0;  // its sweep's steps
     int64_t batch = 1, rest = 1;  // stored as [batch][rest]
     int64_t rest_last = 1;     // dim of the fastest rest leg
+    int64_t batch_last = 1;    // dim of the fastest batch leg
+    int64_t span = 1;          // largest running tensor of its sweep (entries)
   } quarter[4];                 // ul, bl, ur, br
   bool odd = false;             // odd-side partition (Fig. S2(c))
+  size_t obuf_off[8] = {};      // odd side: buffer offsets (hi planes), ul ur bl br pairs
   int s_m1 = -1, s_m2 = -1;     // merge steps F_l = F_ul F_bl, Y = F_br F_l^T
   int op_m1 = -1, op_m2 = -1;
   int n_site_ops = 0;           // ops rebuilt from the site tensors per slice
@@ -143,12 +147,19 @@ struct Plan {
   std::vector<Launch> launches;
   int n_recs = 0;
   int64_t n_opbuild_per_slice = 0;
+  // per slice: first entry and count of the operand builds it launches (the
+  // first slice builds every operand, a later one only those whose
+  // restriction differs from the slice before it)
+  std::vector<int64_t> obe_first, obe_count, obe2_first, obe2_count;
   int max_kn = 0;
   std::vector<int64_t> slice_list;
   double flops_per_slice = 0, bytes_per_slice = 0;
 
-  // host copy of the tables blob (uploaded once)
+  // host copy of the tables (uploaded once): [off_site_ptrs, off_ops_begin)
+  // then [off_opdesc, off_tables_end); the operand storage between them is
+  // written on the device only
   std::vector<unsigned char> blob;
+  size_t off_ops_begin = 0;
 
   // CUDA graph of the whole launch sequence (PEPS_FLAG_GRAPH)
   cudaGraphExec_t graph_exec = nullptr;
@@ -747,6 +758,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     auto plan_quarter = [&](int qi, Orient ori, int Hs, int Ws) -> int {
       Plan::Quarter &Q = P.quarter[qi];
       Q.first = (int)P.steps.size();
+      Q.span = 1;
       auto hs = [](int i, int j) { return 1000 + i * 64 + (j + 1); };
       const int VID = 2;
       static const int di[4] = {0, 0, -1, 1}, dj[4] = {-1, 1, 0, 0};
@@ -853,6 +865,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         P.step_opbase.push_back(n_ops_total);
         n_ops_total += 1 << k;
         cap = std::max(cap, std::max(sh.M * K, sh.M * (int64_t)sh.N));
+        Q.span = std::max(Q.span, std::max(sh.M * K, sh.M * (int64_t)sh.N));
         flops += 8.0 * (double)sh.M * K * sh.N;
         bytes += (double)bpe * (double)(sh.M * K + sh.M * (int64_t)sh.N);
         std::vector<Leg> nlgs;
@@ -878,6 +891,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       }
       Q.rest_last = legs[Hs - 1].dim;
       Q.batch = B;
+      Q.batch_last = info(Hs - 1, Ws - 1).rd[3];
       Q.count = (int)P.steps.size() - Q.first;
       return PEPS_OK;
     };
@@ -930,30 +944,52 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     } else {
       // odd side L = 2m+1 (Fig. S2(c)): ul = rows 0..m x cols 0..m-1, ur =
       // rows 0..m x cols m..2m (holds the centre site), bl = rows m+1..2m x
-      // cols 0..m, br = rows m+1..2m x cols m+1..2m, swept from their corners:
+      // cols 0..m, br = rows m+1..2m x cols m+1..2m, each swept column by
+      // column from its lattice corner, so that the horizontal cut is every
+      // quarter's batch (its legs appear one per sweep column, from the first
+      // column on: a sliced bit there shrinks the rest of the sweep):
       //   F_ul = [horizontal cut, cols 0..m-1][upper vertical cut, rows 0..m]
-      //   F_ur = [upper vertical cut, rows 0..m][horizontal cut, cols 2m..m]
+      //   F_ur = [horizontal cut, cols 2m..m][upper vertical cut, rows 0..m]
       //   F_bl = [horizontal cut, cols 0..m][lower vertical cut, rows 2m..m+1]
-      //   F_br = [lower vertical cut, rows 2m..m+1][horizontal cut, cols 2m..m+1]
-      // F_u = F_ul F_ur (ur's operand with col m moved to the front of N) and
-      // F_b = F_bl F_br are then both [cols 0..m][cols 2m..m+1], and the
-      // amplitude is their dot product: the paper's order (upper-left with
-      // upper-right, bottom-left with bottom-right, then the halves).
+      //   F_br = [horizontal cut, cols 2m..m+1][lower vertical cut, rows 2m..m+1]
+      // The larger quarter of each half (ur: 8 open legs, bl: 2m+1) is its
+      // merge's A operand as stored, the other one the (transposed) B operand:
+      //   F_u^T = F_ur F_ul^T,  F_b = F_bl F_br^T,
+      // both written as [col m][cols 0..m-1][cols 2m..m+1], and the amplitude
+      // is their dot product: the paper's order (upper-left with upper-right,
+      // bottom-left with bottom-right, then the halves).
       const int m = R / 2;
       if ((rc = plan_quarter(0, {0, 0, 0}, m + 1, m))) return rc;       // ul
-      if ((rc = plan_quarter(2, {1, 0, 1}, m + 1, m + 1))) return rc;   // ur
+      if ((rc = plan_quarter(2, {0, 0, 1}, m + 1, m + 1))) return rc;   // ur
       const Plan::Quarter &ul = P.quarter[0], &ur = P.quarter[2];
-      if (ul.rest != ur.batch) return fail(PEPS_EINVAL, "internal: ul / ur cut dims differ");
+      if (ul.rest != ur.rest) return fail(PEPS_EINVAL, "internal: ul / ur cut dims differ");
+      // F_u^T rows are (cols 2m..m+1, col m), its columns cols 0..m-1; stored
+      // [col m][cols 0..m-1][cols 2m..m+1] by the epilogue's permuted store
+      // (m_lo = col m, m_hi = cols 2m..m+1, h' = the whole N)
       P.s_m1 = (int)P.steps.size();
-      if ((rc = add_merge(merge_shape(ul.batch, ul.rest, ur.rest)))) return rc;
+      {
+        StepShape sh = merge_shape(ur.batch, ur.rest, ul.batch);
+        sh.P = ur.batch / ur.batch_last;
+        sh.dh_out = (int)ul.batch;
+        sh.dv_out = 1;
+        if ((rc = add_merge(sh))) return rc;
+      }
       if ((rc = plan_quarter(1, {0, 1, 0}, m, m + 1))) return rc;       // bl
-      if ((rc = plan_quarter(3, {1, 1, 1}, m, m))) return rc;           // br
+      if ((rc = plan_quarter(3, {0, 1, 1}, m, m))) return rc;           // br
       const Plan::Quarter &bl = P.quarter[1], &br = P.quarter[3];
-      if (bl.rest != br.batch) return fail(PEPS_EINVAL, "internal: bl / br cut dims differ");
-      if (ul.batch * ur.rest != bl.batch * br.rest)
+      if (bl.rest != br.rest) return fail(PEPS_EINVAL, "internal: bl / br cut dims differ");
+      if (ul.batch * ur.batch != bl.batch * br.batch || ur.batch_last != bl.batch_last)
         return fail(PEPS_EINVAL, "internal: the halves' cut dims differ");
+      // F_b = F_bl F_br^T: rows (cols 0..m-1, col m), columns cols 2m..m+1;
+      // the same order (m_lo = col m, m_hi = cols 0..m-1, v' = the whole N)
       P.s_m2 = (int)P.steps.size();
-      if ((rc = add_merge(merge_shape(bl.batch, bl.rest, br.rest)))) return rc;
+      {
+        StepShape sh = merge_shape(bl.batch, bl.rest, br.batch);
+        sh.P = bl.batch / bl.batch_last;
+        sh.dh_out = 1;
+        sh.dv_out = (int)br.batch;
+        if ((rc = add_merge(sh))) return rc;
+      }
     }
     P.n_site_ops = n_ops_total;
     P.op_m1 = n_ops_total++;
@@ -982,7 +1018,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       sh.csep = 0;
     }
   }
-  if (cap > ((int64_t)1 << 36)) return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
+  if (cap > ((int64_t)1 << 36) && !(o.flags & PEPS_FLAG_ESTIMATE))
+    return fail(PEPS_EUNSUPPORTED, "running tensor too large (%lld entries)", (long long)cap);
+  if (ws && (o.flags & PEPS_FLAG_ESTIMATE))
+    return fail(PEPS_EINVAL, "PEPS_FLAG_ESTIMATE is for planning queries only");
   P.cap = cap;
   P.n_steps = (int)P.steps.size();
   P.flops_per_slice = flops;
@@ -995,6 +1034,24 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   } else {
     P.plane = 0;
     P.gbuf_bytes = align_up((size_t)cap * bpe, 1024);
+  }
+  P.odd_bytes = 0;
+  if (quad && P.odd) {
+    // odd side: one bitstring at a time, so each sweep pair gets its own size
+    // (ul pair also holds F_u^T, bl pair F_b); all hi planes first, every
+    // lo plane at the same offset behind them
+    const bool two = fmt == FMT_BF16X2 || fmt == FMT_FP16X2;
+    const size_t pe = two ? 4 : (size_t)bpe;
+    const StepShape &m1 = P.steps[P.s_m1], &m2 = P.steps[P.s_m2];
+    const int64_t span[4] = {std::max(P.quarter[0].span, m1.M * (int64_t)m1.N), P.quarter[2].span,
+                             std::max(P.quarter[1].span, m2.M * (int64_t)m2.N), P.quarter[3].span};
+    size_t o2 = 0;
+    for (int b = 0; b < 8; ++b) {
+      P.obuf_off[b] = o2;
+      o2 = align_up(o2 + pe * (size_t)span[b / 2], 1024);
+    }
+    P.plane = two ? (int64_t)o2 / 2 : 0;
+    P.odd_bytes = two ? 2 * o2 : o2;
   }
   for (auto &s : P.steps) s.plane = P.plane;
 
@@ -1151,6 +1208,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
   P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
   P.off_g2 = off; off = align_up(off + std::max<size_t>(g2e.size(), 1) * sizeof(Gate2Entry));
+  P.off_ops_begin = off;
 
   // operands (restricted dims): 2^nq variants per step
   const int n_ops = n_ops_total;
@@ -1171,10 +1229,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       P.max_kn2 = std::max<int>(P.max_kn2, sh.K * sh.N);
       n2 += 4;
     }  // nq == 0: a merge operand, built from a stored tensor during the call
+    // a tensor-core merge builds its planes straight from the stored tensor
+    const bool merge_tc = sh.nq == 0 && want_tc && tc_supports(sh, fmt);
     for (int t = 0; t < (1 << sh.nq); ++t) {
       const int op = P.step_opbase[s] + t;
-      P.ec_off[op] = off;
-      off = align_up(off + (size_t)sh.K * (size_t)sh.N * sizeof(float2), 1024);
+      P.ec_off[op] = 0;
+      if (!merge_tc) {
+        P.ec_off[op] = off;
+        off = align_up(off + (size_t)sh.K * (size_t)sh.N * sizeof(float2), 1024);
+      }
       if (want_tc && tc_supports(sh, fmt)) {
         const size_t planes = (fmt == FMT_BF16X2 || fmt == FMT_FP16X2) ? 2 : 1;
         const size_t esz = (fmt == FMT_TF32) ? 4 : 2;
@@ -1292,46 +1355,43 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       P.launches.push_back(ln);
     };
     if (P.odd) {
-      // per bitstring: ul, ur -> F_u (group buffers); bl, br -> F_b (lane 0's
-      // buffers); amplitude = F_u . F_b
+      // per bitstring: bl, br -> F_b; ul, ur -> F_u^T; amplitude = F_u^T . F_b.
+      // One bitstring at a time in sized buffers: ul 0-1 (then F_u^T), ur 2-3,
+      // bl 4-5 (then F_b), br 6-7.
+      auto ob = [&](int b) -> size_t { return P.obuf_off[b]; };
       for (int64_t i = 0; i < n; ++i) {
         const int64_t chain = i;
         auto ch = [&](int) { return chain; };
         auto bit = [&](int) { return i; };
-        const int bul = sweep(ul, 1, ch, bit, [&](int, int b) { return pre_buf(b); });
-        const int bur = sweep(ur, 1, ch, bit, [&](int, int b) { return pre_buf(2 + b); });
-        const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
-        const int rec_ur = (int)(chain * NS + ur.first + ur.count - 1);
-        const int rec_u = (int)(chain * NS + P.s_m1);
-        // Ec[k][n'] from F_ur[k][rest]: n' = (col m, cols 2m..m+1) while the
-        // rest is (cols 2m..m+1, col m), col m the fastest rest leg
-        tensor_op(pre_buf(2 + bur), ur.batch, ur.rest, ur.rest_last, rec_ur, P.op_m1, P.s_m1);
-        tops.back().ks = ur.rest;
-        tops.back().ns_hi = 1;
-        tops.back().Nlo = ur.rest / ur.rest_last;
-        {
-          StepItem it{};
-          it.op_base = P.op_m1;
-          it.in_rec = rec_ul;
-          it.out_rec = rec_u;
-          RelItem ri{pre_buf(bul), pre_buf(bul ^ 1), false, i};
-          add_step_launch(P.s_m1, {it}, {ri}, 1);
-        }
-        const int bbl = sweep(bl, 1, ch, bit, [&](int, int b) { return lane_buf(0, b); });
-        const int bbr = sweep(br, 1, ch, bit, [&](int, int b) { return lane_buf(0, 2 + b); });
+        const int bbl = sweep(bl, 1, ch, bit, [&](int, int b) { return ob(4 + b); });
+        const int bbr = sweep(br, 1, ch, bit, [&](int, int b) { return ob(6 + b); });
         const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
         const int rec_br = (int)(chain * NS + br.first + br.count - 1);
         const int rec_b = (int)(chain * NS + P.s_m2);
-        // F_br = [K][N] row-major: Ec[k][n] = F_br[k N + n]
-        tensor_op(lane_buf(0, 2 + bbr), br.batch, br.rest, 1, rec_br, P.op_m2, P.s_m2);
-        tops.back().ks = br.rest;
+        // Ec[k][n] = F_br[n K + k]
+        tensor_op(ob(6 + bbr), br.rest, br.batch, br.rest, rec_br, P.op_m2, P.s_m2);
         {
           StepItem it{};
           it.op_base = P.op_m2;
           it.in_rec = rec_bl;
           it.out_rec = rec_b;
-          RelItem ri{lane_buf(0, bbl), lane_buf(0, bbl ^ 1), false, i};
+          RelItem ri{ob(4 + bbl), ob(4 + (bbl ^ 1)), false, i};
           add_step_launch(P.s_m2, {it}, {ri}, 1);
+        }
+        const int bul = sweep(ul, 1, ch, bit, [&](int, int b) { return ob(b); });
+        const int bur = sweep(ur, 1, ch, bit, [&](int, int b) { return ob(2 + b); });
+        const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
+        const int rec_ur = (int)(chain * NS + ur.first + ur.count - 1);
+        const int rec_u = (int)(chain * NS + P.s_m1);
+        // Ec[k][n] = F_ul[n K + k]
+        tensor_op(ob(bul), ul.rest, ul.batch, ul.rest, rec_ul, P.op_m1, P.s_m1);
+        {
+          StepItem it{};
+          it.op_base = P.op_m1;
+          it.in_rec = rec_ur;
+          it.out_rec = rec_u;
+          RelItem ri{ob(2 + bur), ob(bul ^ 1), false, i};
+          add_step_launch(P.s_m1, {it}, {ri}, 1);
         }
         Launch dl{};
         dl.kind = 3;
@@ -1339,9 +1399,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         dl.n_aux = 1;
         dl.flops = dl.bytes = 0;
         DotEntry d{};
-        d.Y = (const void *)(REL + pre_buf(bul ^ 1));
-        d.F = (const void *)(REL + lane_buf(0, bbl ^ 1));
-        d.n = ul.batch * ur.rest;
+        d.Y = (const void *)(REL + ob(bul ^ 1));
+        d.F = (const void *)(REL + ob(4 + (bbl ^ 1)));
+        d.n = ur.batch * ul.batch;
         d.rec_y = rec_u;
         d.rec_f = rec_b;
         d.out_index = (int)i;
@@ -1501,7 +1561,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   off = align_up(off, 4096);
   P.lane_off = off;
   const int n_gbufs = quad ? 4 * P.lanes + 4 : 2 * P.lanes + (pc > 0 ? 2 : 0);
-  off += (size_t)n_gbufs * P.gbuf_bytes;
+  off += (quad && P.odd) ? P.odd_bytes : (size_t)n_gbufs * P.gbuf_bytes;
   P.need = off;
   if (!ws) return PEPS_OK;
   if (ws_bytes < P.need)
@@ -1545,7 +1605,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     for (int t = 0; t < (1 << sh.nq); ++t) {
       const int op = P.step_opbase[s] + t;
       OpDesc d{};
-      d.Ec = (const float2 *)(base + P.ec_off[op]);
+      d.Ec = P.ec_off[op] ? (const float2 *)(base + P.ec_off[op]) : nullptr;
       d.Bt[0] = P.bt_off[0][op] ? (const void *)(base + P.bt_off[0][op]) : nullptr;
       d.Bt[1] = P.bt_off[1][op] ? (const void *)(base + P.bt_off[1][op]) : nullptr;
       d.b_t = operand_scale_exp(fmt);
@@ -1636,13 +1696,46 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       }
     }
   }
+  // keep, for each slice after the first, only the entries that change
+  {
+    const size_t n1 = (size_t)P.n_opbuild_per_slice, n2 = (size_t)P.n_obe2_per_slice;
+    const size_t ns = P.slice_list.size();
+    std::vector<OpBuildEntry> c1;
+    std::vector<OpBuild2Entry> c2;
+    P.obe_first.assign(ns, 0);
+    P.obe_count.assign(ns, 0);
+    P.obe2_first.assign(ns, 0);
+    P.obe2_count.assign(ns, 0);
+    for (size_t si = 0; si < ns; ++si) {
+      P.obe_first[si] = (int64_t)c1.size();
+      for (size_t j = 0; j < n1; ++j) {
+        const OpBuildEntry &e = obe[si * n1 + j];
+        if (si == 0 || std::memcmp(&e, &obe[(si - 1) * n1 + j], sizeof(OpBuildEntry)) != 0)
+          c1.push_back(e);
+      }
+      P.obe_count[si] = (int64_t)c1.size() - P.obe_first[si];
+      P.obe2_first[si] = (int64_t)c2.size();
+      for (size_t j = 0; j < n2; ++j) {
+        const OpBuild2Entry &e = obe2[si * n2 + j];
+        if (si == 0 || std::memcmp(&e, &obe2[(si - 1) * n2 + j], sizeof(OpBuild2Entry)) != 0)
+          c2.push_back(e);
+      }
+      P.obe2_count[si] = (int64_t)c2.size() - P.obe2_first[si];
+    }
+    obe.swap(c1);
+    obe2.swap(c2);
+  }
 
   std::vector<float2 *> site_ptrs(NQ);
   for (int q = 0; q < NQ; ++q) site_ptrs[q] = (float2 *)(base + P.site_buf_off[0][q]);
 
-  P.blob.assign(P.off_tables_end - P.off_site_ptrs, 0);
+  const size_t part_a = P.off_ops_begin - P.off_site_ptrs;
+  P.blob.assign(part_a + (P.off_tables_end - P.off_opdesc), 0);
   auto put = [&](size_t off_abs, const void *src, size_t nbytes) {
-    if (nbytes) std::memcpy(P.blob.data() + (off_abs - P.off_site_ptrs), src, nbytes);
+    if (!nbytes) return;
+    const size_t at = off_abs < P.off_ops_begin ? off_abs - P.off_site_ptrs
+                                                : part_a + (off_abs - P.off_opdesc);
+    std::memcpy(P.blob.data() + at, src, nbytes);
   };
   put(P.off_site_ptrs, site_ptrs.data(), NQ * sizeof(float2 *));
   put(P.off_site_lo, P.site_elems.data(), NQ * sizeof(int64_t));
@@ -1721,7 +1814,9 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   const int64_t ns = (int64_t)P.slice_list.size();
-  S.launches_operand = ns * (2 + (P.n_obe2_per_slice > 0 ? 1 : 0) + (any_tc ? 1 : 0));
+  S.launches_operand = ns * (1 + (any_tc ? 1 : 0));
+  for (int64_t si = 0; si < ns; ++si)
+    S.launches_operand += (P.obe_count[si] > 0 ? 1 : 0) + (P.obe2_count[si] > 0 ? 1 : 0);
   for (auto &l : P.launches) {
     if (l.kind == 0) {
       S.launches_contract += ns;
@@ -1796,12 +1891,15 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   for (size_t si = 0; si < P.slice_list.size(); ++si) {
     if (P.n_recs > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, P.n_recs * sizeof(Rec), s));
-    const OpBuildEntry *e = obe + si * P.n_opbuild_per_slice;
-    const OpBuild2Entry *e2 = obe2 + si * P.n_obe2_per_slice;
-    CUDA_TRY(launch_build_operands(e, (int)P.n_opbuild_per_slice, P.max_kn, ops, s));
-    S.launches_operand++;
-    if (P.n_obe2_per_slice > 0) {
-      CUDA_TRY(launch_build_operands2(e2, (int)P.n_obe2_per_slice, P.max_kn2, ops, s));
+    // operands whose restriction is unchanged since the previous slice stay
+    const OpBuildEntry *e = obe + P.obe_first[si];
+    const OpBuild2Entry *e2 = obe2 + P.obe2_first[si];
+    if (P.obe_count[si] > 0) {
+      CUDA_TRY(launch_build_operands(e, (int)P.obe_count[si], P.max_kn, ops, s));
+      S.launches_operand++;
+    }
+    if (P.obe2_count[si] > 0) {
+      CUDA_TRY(launch_build_operands2(e2, (int)P.obe2_count[si], P.max_kn2, ops, s));
       S.launches_operand++;
     }
     CUDA_TRY(launch_operand_bounds(P.n_site_ops, ops, s));
@@ -1831,13 +1929,16 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
         S.contract_flops += l.flops;
         S.contract_bytes += l.bytes;
       } else if (l.kind == 2) {
-        // a merge operand from a stored tensor: Ec, its bound, the planes
-        CUDA_TRY(launch_tensor_operand(tops + l.aux_off, l.kn, P.fmt, P.plane, ops, recs, s));
-        CUDA_TRY(launch_operand_bounds(1, ops + l.op, s));
-        S.launches_operand += 2;
+        // a merge operand from a stored tensor: for the tensor cores its bound
+        // and planes straight from the tensor, else Ec and its bound
         if (l.tc) {
-          CUDA_TRY(launch_build_tc_operands(1, l.kn, ops + l.op, P.fmt, s));
-          S.launches_operand++;
+          CUDA_TRY(launch_tensor_operand_tc(tops + l.aux_off, l.shape.K, l.shape.N, P.fmt, P.plane,
+                                            ops, recs, s));
+          S.launches_operand += 3;
+        } else {
+          CUDA_TRY(launch_tensor_operand(tops + l.aux_off, l.kn, P.fmt, P.plane, ops, recs, s));
+          CUDA_TRY(launch_operand_bounds(1, ops + l.op, s, l.shape.N));
+          S.launches_operand += 2;
         }
       } else if (l.kind == 3) {
         CUDA_TRY(launch_dot(dots + l.aux_off, l.n_aux, P.fmt, P.plane, recs, partials, acc, s));
@@ -1963,8 +2064,13 @@ static int prepare(peps_ctx *c, int64_t n, const peps_opts *opts, void *ws, size
   auto NP = std::make_unique<Plan>();
   int rc = build_plan(c, n, o, ws, ws_bytes, bits_dev, host_bits, *NP);
   if (rc) return rc;
-  CUDA_TRY(cudaMemcpy((char *)ws + NP->off_site_ptrs, NP->blob.data(), NP->blob.size(),
-                      cudaMemcpyHostToDevice));
+  {
+    const size_t part_a = NP->off_ops_begin - NP->off_site_ptrs;
+    CUDA_TRY(cudaMemcpy((char *)ws + NP->off_site_ptrs, NP->blob.data(), part_a,
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy((char *)ws + NP->off_opdesc, NP->blob.data() + part_a,
+                        NP->blob.size() - part_a, cudaMemcpyHostToDevice));
+  }
   c->plan = std::move(NP);
   c->built_generation = 0;  // site buffers may have moved: re-evolve
   return PEPS_OK;

@@ -266,7 +266,9 @@ cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStre
 cudaError_t launch_gate2(const Gate2Entry *d_entries, int n, int64_t max_out, cudaStream_t s);
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
                                   OpDesc *d_ops, cudaStream_t s);
-cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s);
+// `n_cols`: the widest operand's N (sizes the grid of a single op)
+cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s,
+                                  int64_t n_cols = 4096);
 cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int fmt, int64_t plane,
                                   OpDesc *d_ops, const Rec *d_recs, cudaStream_t s);
 // Blocks per DotEntry; `d_partials` holds kDotBlocks double2 per entry.
@@ -275,6 +277,11 @@ cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
                        const Rec *d_recs, double2 *d_partials, double2 *d_acc, cudaStream_t s);
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s);
+// A merge operand's tensor-core planes and bound straight from the stored
+// tensor (no Ec); K, N are the operand's sizes.
+cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int K, int N, int fmt,
+                                     int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+                                     cudaStream_t s);
 // Tensor-core planes (and their bound) of ops [0, n_ops) from their Ec.
 cudaError_t launch_build_tc_operands(int n_ops, int64_t max_kn, OpDesc *d_ops, int fmt,
                                      cudaStream_t s);

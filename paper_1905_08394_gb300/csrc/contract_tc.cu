@@ -927,6 +927,117 @@ __global__ void k_build_bt(OpDesc *ops) {
   }
 }
 
+// A merge operand straight from a stored tensor G whose k index is contiguous:
+// Ec[k][n] = G[k + nh ns_hi + nl ns] 2^-target (n = nh Nlo + nl) is never
+// written out.  k_tensor_bound takes the column bound beta_c = max_n
+// sum_k |Ec[k][n]|_1 (one block per column, the threads along k), k_tensor_bt
+// the complex-as-real planes Bt[(n, b)][(k, a)] (reads and writes both run
+// along k).  Same values as Ec -> k_beta_ops -> k_build_bt.
+__global__ void k_tensor_init(const TensorOpEntry *__restrict__ e, OpDesc *ops, const Rec *recs) {
+  const TensorOpEntry g = *e;
+  OpDesc &op = ops[g.op];
+  op.beta_c_bits = 0u;
+  op.beta_t_bits = 0u;
+  op.e_c = recs[g.rec].exp - g.target;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_tensor_bound(const TensorOpEntry *__restrict__ e,
+                                                      int64_t plane, OpDesc *ops) {
+  const TensorOpEntry g = *e;
+  const float sc = pow2f(-g.target);
+  __shared__ float red[8];
+  float best = 0.f;
+  for (int64_t n = blockIdx.x; n < g.N; n += gridDim.x) {
+    const int64_t nh = n / g.Nlo, nl = n - nh * g.Nlo;
+    const int64_t base = nh * g.ns_hi + nl * g.ns;
+    float s = 0.f;
+    for (int64_t k = threadIdx.x; k < g.K; k += blockDim.x) {
+      const float2 v = load_g<FMT>(g.G, base + k * g.ks, plane);
+      s += fabsf(v.x * sc) + fabsf(v.y * sc);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      best = fmaxf(best, t);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    atomicMax(&ops[g.op].beta_c_bits, __float_as_uint(best * (1.0f + 1.0f / 256.0f)));
+}
+
+template <int FMT>
+__global__ void k_tensor_bt(const TensorOpEntry *__restrict__ e, int64_t plane, OpDesc *ops) {
+  const TensorOpEntry g = *e;
+  OpDesc &op = ops[g.op];
+  const int64_t K = g.K, N = g.N;
+  const float sc = pow2f(-g.target), sb = ldexpf(1.f, op.b_t);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K * N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = i / K, k = i - n * K;
+    const int64_t nh = n / g.Nlo, nl = n - nh * g.Nlo;
+    const float2 v = load_g<FMT>(g.G, k * g.ks + nh * g.ns_hi + nl * g.ns, plane);
+    const float re = (v.x * sc) * sb, im = (v.y * sc) * sb;
+    // row 2n holds (re, -im) at columns 2k, 2k+1; row 2n+1 holds (im, re)
+    const float2 r0 = make_float2(re, -im), r1 = make_float2(im, re);
+    const int64_t w0 = 2 * n * K + k, w1 = (2 * n + 1) * K + k;   // in column pairs
+    if (FMT == FMT_TF32) {
+      ((float2 *)op.Bt[0])[w0] = make_float2(round_tf32(r0.x), round_tf32(r0.y));
+      ((float2 *)op.Bt[0])[w1] = make_float2(round_tf32(r1.x), round_tf32(r1.y));
+    } else if (FMT == FMT_BF16) {
+      ((uint32_t *)op.Bt[0])[w0] = pack_bf16(r0.x, r0.y);
+      ((uint32_t *)op.Bt[0])[w1] = pack_bf16(r1.x, r1.y);
+    } else if (FMT == FMT_FP16) {
+      ((uint32_t *)op.Bt[0])[w0] = pack_f16(r0.x, r0.y);
+      ((uint32_t *)op.Bt[0])[w1] = pack_f16(r1.x, r1.y);
+    } else {
+      constexpr bool BF = FMT == FMT_BF16X2;
+      uint32_t h0, l0, h1, l1;
+      split16<BF>(r0, h0, l0);
+      split16<BF>(r1, h1, l1);
+      ((uint32_t *)op.Bt[0])[w0] = h0;
+      ((uint32_t *)op.Bt[0])[w1] = h1;
+      ((uint32_t *)op.Bt[1])[w0] = l0;
+      ((uint32_t *)op.Bt[1])[w1] = l1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const float bc = __uint_as_float(op.beta_c_bits);
+    op.beta_t_bits = __float_as_uint(bc * sb * (1.0f + 1.0f / 128.0f));
+  }
+}
+
+cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int K, int N, int fmt,
+                                     int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+                                     cudaStream_t s) {
+  const int64_t kn = (int64_t)K * N;
+  int64_t gb = N < 16384 ? N : 16384;
+  if (gb < 1) gb = 1;
+  int64_t gt = (kn + 255) / 256;
+  if (gt > 16384) gt = 16384;
+  if (gt < 1) gt = 1;
+  k_tensor_init<<<1, 1, 0, s>>>(d_entry, d_ops, d_recs);
+  switch (fmt) {
+#define PEPS_TOP_CASE(F)                                                              \
+  case F:                                                                            \
+    k_tensor_bound<F><<<(int)gb, 256, 0, s>>>(d_entry, plane, d_ops);                \
+    k_tensor_bt<F><<<(int)gt, 256, 0, s>>>(d_entry, plane, d_ops);                   \
+    break;
+    PEPS_TOP_CASE(FMT_TF32)
+    PEPS_TOP_CASE(FMT_BF16)
+    PEPS_TOP_CASE(FMT_FP16)
+    PEPS_TOP_CASE(FMT_BF16X2)
+    PEPS_TOP_CASE(FMT_FP16X2)
+#undef PEPS_TOP_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build_tc_operands(int n, int64_t max_kn, OpDesc *d_ops, int fmt,
                                      cudaStream_t s) {
   if (n <= 0) return cudaSuccess;

@@ -259,10 +259,13 @@ cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_
   return cudaGetLastError();
 }
 
-cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s) {
+cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s, int64_t n_cols) {
   if (n_ops <= 0) return cudaSuccess;
-  // 32 columns per block and pass; 128 blocks cover N = 4096 in one pass
-  k_beta_ops<<<dim3(n_ops == 1 ? 128 : 8, n_ops), 1024, 0, s>>>(d_ops);
+  // 32 columns per block and pass; a single op gets a block per 32 columns
+  // (at least 128, at most 2048)
+  int64_t g1 = (n_cols + 31) / 32;
+  g1 = g1 < 128 ? 128 : (g1 > 2048 ? 2048 : g1);
+  k_beta_ops<<<dim3(n_ops == 1 ? (unsigned)g1 : 8u, n_ops), 1024, 0, s>>>(d_ops);
   return cudaGetLastError();
 }
 

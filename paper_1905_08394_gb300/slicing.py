@@ -10,6 +10,14 @@ horizontal bonds.  The chooser below is greedy: while some step's running
 tensor exceeds the budget, it cuts one more bit of the widest horizontal bond
 of the largest running tensor (ties broken by a seeded draw), choosing which
 CZ of that edge to slice by a seeded draw as well.  Host-side planning only.
+
+For the square partition (Fig. S2(b, c)) the cost of a slice set is not a
+property of one running tensor: a bit cut on a quarter's open leg shrinks its
+sweep from the column where that leg appears, and a quarter is recomputed for
+every bit it does not touch.  `choose_quadrants` therefore searches on the C
+planner's own figures (multiply-adds per slice and workspace bytes): a beam
+search that adds one cut bit at a time and keeps the cheapest total
+(per-slice flops x 2^|S|) among the sets whose workspace fits the budget.
 """
 from __future__ import annotations
 
@@ -23,7 +31,9 @@ class SliceSet:
     sliced_cz: list        # CZ ordinals (order of application)
     max_entries: int       # largest running tensor with these cuts
     n_slices: int          # 2 ** len(sliced_cz)
-    step_cmacs: list       # complex multiply-adds per step of one slice
+    step_cmacs: list       # complex multiply-adds per step of one slice (column sweep)
+    flops_per_slice: float = 0.0   # the planner's figure (square partition)
+    workspace_bytes: int = 0       # the planner's figure (square partition)
 
 
 def cz_edges(circ):
@@ -115,3 +125,77 @@ def seeded_slice_ids(n_sliced: int, count: int, seed: int):
         if x not in out:
             out.append(x)
     return out
+
+
+def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: int = 0,
+                     beam: int = 16, max_bits: int = 24) -> SliceSet:
+    """Slice set for the square partition on the planner of handle `h` (the
+    circuit `circ` applied to it): the cheapest total flops found whose
+    workspace is at most `ws_budget` bytes.  Each beam level adds one cut bit
+    on one edge (which CZ of the edge by a seeded draw); candidates are ranked
+    by log2(total flops) + 2 log2(workspace / budget) above the budget."""
+    import math
+
+    from . import binding as B
+
+    _, per_edge = cz_edges(circ)
+    keys = sorted(per_edge)
+    rng = SplitMix64(seed ^ 0x9A4D)
+    pick = {k: [per_edge[k][i] for i in _seeded_perm(len(per_edge[k]), rng)] for k in keys}
+
+    def evaluate(counts):
+        sl = sorted(o for k, c in counts.items() for o in pick[k][:c])
+        kw = dict(precision=precision, scheme="quadrants", sliced_cz=sl, slice_ids=[0] if sl else None,
+                  flags=B.PEPS_FLAG_ESTIMATE)
+        o, keep = B.make_opts(**kw)
+        try:
+            info = B.peps_plan_info_get(h, 1, o)
+            ws = B.peps_workspace_bytes(h, 1, o)
+        except B.PepsError:
+            return None
+        del keep
+        return sl, info, ws
+
+    best = None
+    frontier = [{}]
+    seen = set()
+    for _ in range(max_bits + 1):
+        scored = []
+        for counts in frontier:
+            for k in keys:
+                c = counts.get(k, 0)
+                if c >= len(per_edge[k]):
+                    continue
+                nc = dict(counts)
+                nc[k] = c + 1
+                tag = tuple(sorted(nc.items()))
+                if tag in seen:
+                    continue
+                seen.add(tag)
+                r = evaluate(nc)
+                if r is None:
+                    continue
+                sl, info, ws = r
+                total = info["flops_per_chain"] * 2.0 ** len(sl)
+                if ws <= ws_budget and (best is None or total < best[0]):
+                    best = (total, sl, info, ws)
+                over = max(0.0, math.log2(ws / ws_budget))
+                scored.append((math.log2(total) + 2.0 * over, tag, nc))
+        if not scored:
+            break
+        scored.sort(key=lambda t: (t[0], t[1]))
+        frontier = [nc for _, _, nc in scored[:beam]]
+    if best is None:
+        raise ValueError("no slice set within the budget was found")
+    total, sl, info, ws = best
+    return SliceSet(sl, int(info["max_entries"]), 2 ** len(sl), [], float(info["flops_per_chain"]),
+                    int(ws))
+
+
+def _seeded_perm(n: int, rng):
+    """A seeded permutation of range(n) (Fisher-Yates on SplitMix64 draws)."""
+    p = list(range(n))
+    for i in range(n - 1, 0, -1):
+        j = rng.next() % (i + 1)
+        p[i], p[j] = p[j], p[i]
+    return p

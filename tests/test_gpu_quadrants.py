@@ -190,3 +190,46 @@ def test_odd_7x7_d24_against_the_golden_values(sim_factory):
         assert relerr(sim.amplitudes(x, precision=prec, **QUAD), ref) < SPLIT_TOL, prec
     # and the two schemes agree
     assert relerr(sim.amplitudes(x, precision="fp16x3", **QUAD), sim.amplitudes(x, precision="fp16x3")) < 2 * SPLIT_TOL
+
+
+def test_odd_slices_sum_to_the_unsliced_amplitude(sim_factory):
+    # a sliced bit on the horizontal cut (the quarters' batch legs), one on the
+    # upper vertical cut and one inside ur
+    circ = make_circuit(5, 5, 16, 33)
+    bits = uniform_bitstrings(25, 4, 33)
+    from paper_1905_08394_gb300 import slicing
+
+    _, per = slicing.cz_edges(circ)
+    sliced = sorted([per[("v", 2, 1)][0], per[("h", 1, 1)][1], per[("h", 0, 3)][0]])
+    sim = sim_factory(circ)
+    full = sim.amplitudes(bits, precision="fp32", **QUAD)
+    tot = sim.amplitudes(bits, precision="fp32", sliced_cz=sliced, **QUAD)
+    assert relerr(tot, full) < 1e-6
+    for sid in (3, 6):
+        one = sim.amplitudes(bits, precision="fp16x3", sliced_cz=sliced, slice_ids=[sid], **QUAD)
+        ref = op.amplitudes(op.build(5, 5, circ.gates, sliced=sliced, slice_id=sid), bits)
+        assert relerr(one, ref) < SPLIT_TOL, sid
+
+
+def test_odd_7x7_d24_chosen_slices_against_the_golden_values(sim_factory):
+    # the slice chooser of the square partition under a 64 MiB workspace budget
+    # (the unsliced plan needs ~456 MiB); the slice sum is the amplitude
+    import json
+    import os
+
+    from paper_1905_08394_gb300 import binding as Bn
+    from paper_1905_08394_gb300 import slicing
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_7x7_d24.json")) as f:
+        g = json.load(f)
+    circ = make_circuit(7, 7, 24, 5)
+    x = np.array(g["bitstrings"], dtype=np.uint64)[:2]
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"]])[:2]
+    sim = sim_factory(circ)
+    ss = slicing.choose_quadrants(sim.h, circ, 64 * 2 ** 20, seed=5)
+    assert 0 < len(ss.sliced_cz) <= 10 and ss.workspace_bytes <= 64 * 2 ** 20
+    o, keep = Bn.make_opts(precision="fp16x3", scheme="quadrants", sliced_cz=ss.sliced_cz)
+    assert Bn.peps_workspace_bytes(sim.h, len(x), o) <= 2 * 64 * 2 ** 20
+    for prec in ("fp32", "fp16x3"):
+        out = sim.amplitudes(x, precision=prec, sliced_cz=ss.sliced_cz, **QUAD)
+        assert relerr(out, ref) < SPLIT_TOL, prec

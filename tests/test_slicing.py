@@ -78,3 +78,26 @@ def test_seeded_slice_ids():
     ids = slicing.seeded_slice_ids(40, 5, 5)
     assert len(set(ids)) == 5 and all(0 <= i < 2 ** 40 for i in ids)
     assert ids == slicing.seeded_slice_ids(40, 5, 5)
+
+
+def test_square_partition_chooser_fits_7x7_d40():
+    # the square partition's slice set for 7x7 (1+40+1) under 200 GiB: a
+    # dozen cut bits instead of forty, every quarter within 2^32 entries
+    circ, _ = workload("7x7_d40")
+    h = ctx_for(circ)
+    ss = slicing.choose_quadrants(h, circ, 200 * 2 ** 30, seed=5)
+    assert ss.workspace_bytes <= 200 * 2 ** 30
+    assert len(ss.sliced_cz) <= 14 and ss.max_entries <= 2 ** 33
+    assert ss.flops_per_slice * ss.n_slices < 2e18
+    o, keep = B.make_opts(precision="fp16x3", scheme="quadrants", sliced_cz=ss.sliced_cz,
+                          slice_ids=[0])
+    info = B.peps_plan_info_get(h, 1, o)
+    assert info["flops_per_chain"] == ss.flops_per_slice
+    assert B.peps_workspace_bytes(h, 1, o) == ss.workspace_bytes
+    # the unsliced plan is too large to run; the estimate flag still sizes it
+    o, keep = B.make_opts(precision="fp16x3", scheme="quadrants")
+    with pytest.raises(B.PepsError):
+        B.peps_workspace_bytes(h, 1, o)
+    o, keep = B.make_opts(precision="fp16x3", scheme="quadrants", flags=B.PEPS_FLAG_ESTIMATE)
+    assert B.peps_plan_info_get(h, 1, o)["max_entries"] == 2 ** 40
+    B.peps_destroy(h)
