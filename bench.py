@@ -90,8 +90,9 @@ def parse():
                              "quadrants", "pt8x8", "marginals"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
-                         "slices: 7x7 (1+40+1) sliced contraction, seconds per slice and "
-                         "projected full time from a seeded subset of slices; precision: "
+                         "slices: 7x7 (1+40+1), the whole amplitude of one bitstring on "
+                         "the sliced square partition, timed, with a second decomposition "
+                         "as its check; precision: "
                          "6x6 (1+24+1), every form's amplitudes/s on 4096 bitstrings and its "
                          "error against the oracle on 64; small: 4x4 (1+8+1) and 5x5 (1+16+1), "
                          "eager launches vs CUDA-graph replay; peaks: this GPU's FP32 FMA "
@@ -102,7 +103,9 @@ def parse():
                          "circuit and their Porter-Thomas statistics; marginals: marginal "
                          "probabilities of the top half's 18 qubits of a 6x6 (1+16+1) "
                          "circuit (the double-layer network), 512 bitstrings")
-    ap.add_argument("--slices", type=int, default=4, help="timed slices for --case slices")
+    ap.add_argument("--slices", type=int, default=4, help="(unused; kept for older command lines)")
+    ap.add_argument("--check-full", action="store_true",
+                    help="--case slices: also the amplitude from the slice set chosen without x")
     return ap.parse_args()
 
 
@@ -517,11 +520,15 @@ def run_profile_case(args):
 
 
 def run_slices_case(args):
-    """7x7 (1+40+1), one bitstring, on the odd-side square partition (Fig. S2(c)):
-    the slice set the square-partition chooser picks under a 200 GiB workspace,
-    a seeded subset of slices timed one by one, projected full time = seconds
-    per slice x 2^|S|.  The column sweep's own slice set (every running tensor
-    <= 2^33) is reported beside it from the planner's figures."""
+    """7x7 (1+40+1), one bitstring x, on the odd-side square partition (Fig.
+    S2(c)): the whole amplitude.  The slice set is the square-partition
+    chooser's under a 200 GiB workspace, given x: the CZs whose bit x fixes
+    are cut first (they add no slices), and only the slices that can be
+    nonzero run (slicing.consistent_slice_ids), lower-half reuse included.
+    Timed in one call, the evolution included.  The same amplitude from a
+    second slice set (another budget and seed) is the cross-check; with
+    --check-full also from the slice set chosen without x (every slice of it
+    that can be nonzero, ~10 min)."""
     import numpy as np
     import torch
 
@@ -530,57 +537,72 @@ def run_slices_case(args):
     from rqc_inputs import workload
 
     circ, bits = workload("7x7_d40")
+    x = int(bits[0])
     sim = Simulator(circ.R, circ.C)
     sim.apply_circuit(circ)
     t0 = time.time()
-    ss = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5)
+    ss = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5, x=x)
     choose_s = time.time() - t0
-    ids = slicing.seeded_slice_ids(len(ss.sliced_cz), args.slices, seed=5)
+    ids = slicing.consistent_slice_ids(circ, ss.sliced_cz, x)
+    lmask = slicing.lower_half_mask(circ, ss.sliced_cz)
     stream = torch.cuda.current_stream()
     d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
-    kw = dict(precision=args.precision, sliced_cz=ss.sliced_cz, scheme="quadrants",
-              slice_ids=ids)
-    # warm-up: the same call (plan, tensor maps, evolution)
-    warm = sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **kw).cpu().numpy()
+    base = dict(precision=args.precision, scheme="quadrants")
+    kw = dict(base, sliced_cz=ss.sliced_cz, slice_ids=ids)
+    # warm-up: one run of slices that share the lower half (evolution, kernels)
+    group = [i for i in ids if (i & lmask) == (ids[0] & lmask)]
+    sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **dict(kw, slice_ids=group))
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    # the timed slices run in one call, the evolution included
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     out = sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD, **kw)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     t_call = e0.elapsed_time(e1) / 1e3
     st = sim.stats()
-    vals = [complex(out.cpu().numpy()[0])]
-    times = [t_call / len(ids)]
-    tc = [(st["contract_tc_flops"], st["contract_tc_ms"], st["launches_contract_tc"])]
-    clk = clocks.stop()
+    amp = complex(out.cpu().numpy()[0])
     ws_opts, ws_keep = B.make_opts(**kw)
     ws_gib = B.peps_workspace_bytes(sim.h, 1, ws_opts) / 2 ** 30
-    s_per = sum(times) / len(times)
-    n_sl = ss.n_slices
-    tcf = sum(t[0] for t in tc) / max(1e-9, sum(t[1] for t in tc)) / 1e9
+    # a second decomposition of the same amplitude
+    s2 = slicing.choose_quadrants(sim.h, circ, 120 * 2 ** 30, precision=args.precision, seed=7, x=x)
+    ids2 = slicing.consistent_slice_ids(circ, s2.sliced_cz, x)
+    t1 = time.time()
+    amp2 = complex(sim.amplitudes(bits, sliced_cz=s2.sliced_cz, slice_ids=ids2, **base)[0])
+    t2 = time.time() - t1
+    check = {"sliced_cz": len(s2.sliced_cz), "slices": len(ids2), "flops": s2.flops_total,
+             "amplitude": [amp2.real, amp2.imag], "wall_seconds": t2,
+             "rel_diff": abs(amp2 - amp) / abs(amp) if amp != 0 else None}
+    if args.check_full:
+        s3 = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5)
+        ids3 = slicing.consistent_slice_ids(circ, s3.sliced_cz, x)
+        t1 = time.time()
+        amp3 = complex(sim.amplitudes(bits, sliced_cz=s3.sliced_cz, slice_ids=ids3, **base)[0])
+        check["without_x"] = {"sliced_cz": len(s3.sliced_cz), "slices": len(ids3),
+                              "amplitude": [amp3.real, amp3.imag],
+                              "wall_seconds": time.time() - t1,
+                              "rel_diff": abs(amp3 - amp) / abs(amp) if amp != 0 else None}
     # the column sweep's slice set, for comparison (planner figures only)
     cs = slicing.choose(circ, 2 ** 33, seed=5)
     col = {"sliced_cz": len(cs.sliced_cz), "max_entries": cs.max_entries,
            "flops_per_slice": 8 * sum(cs.step_cmacs),
-           "flops_total": 8 * sum(cs.step_cmacs) * 2.0 ** len(cs.sliced_cz),
-           "seconds_per_slice_measured_earlier": 1.38}
-    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring", "scheme": "quadrants (odd side)",
-            "precision": args.precision, "sliced_cz": len(ss.sliced_cz), "n_slices": n_sl,
-            "max_entries": ss.max_entries, "flops_per_slice": ss.flops_per_slice,
-            "flops_total": ss.flops_per_slice * n_sl, "chooser_seconds": choose_s,
-            "timed_slice_ids": ids, "seconds_per_slice": s_per, "call_seconds": t_call,
-            "contract_seconds": st["contract_ms"] / 1e3, "launches": st["launches_total"],
-            "partial_sum": [vals[0].real, vals[0].imag],
-            "replay_identical": bool(np.array_equal(warm, out.cpu().numpy())),
-            "useful_tflops": ss.flops_per_slice / s_per / 1e12,
-            "projected_seconds": s_per * n_sl, "projected_minutes": s_per * n_sl / 60,
-            "tc_tflops": tcf, "workspace_gib": ws_gib, "columns": col,
-            "clocks": clk, "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
-            "(odd-square partition, 92.51 TB)"}
+           "flops_total": 8 * sum(cs.step_cmacs) * 2.0 ** len(cs.sliced_cz)}
+    n = circ.R * circ.C
+    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring, the whole amplitude",
+            "scheme": "quadrants (odd side)", "precision": args.precision,
+            "sliced_cz": len(ss.sliced_cz), "slices_run": len(ids),
+            "lower_groups": len({i & lmask for i in ids}),
+            "max_entries": ss.max_entries, "flops_total": ss.flops_total,
+            "planned_flops_call": st["contract_flops"], "chooser_seconds": choose_s,
+            "seconds": t_call, "contract_seconds": st["contract_ms"] / 1e3,
+            "launches": st["launches_total"],
+            "useful_tflops": st["contract_flops"] / t_call / 1e12,
+            "amplitude": [amp.real, amp.imag], "n_abs2": (2 ** n) * abs(amp) ** 2,
+            "check": check, "workspace_gib": ws_gib, "columns": col, "clocks": clk,
+            "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
+                     "(odd-square partition, 92.51 TB)"}
     print(json.dumps(line), flush=True)
     sim.close()
 

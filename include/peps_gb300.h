@@ -243,6 +243,14 @@ typedef struct {
     int64_t n_tc_launches;    /* of which tcgen05                            */
     int64_t n_slices;         /* slices summed                               */
     int64_t lanes;            /* bitstrings contracted concurrently          */
+    double flops_lower;       /* odd-side square partition, one bitstring:
+                                 the part of flops_per_chain in the lower half
+                                 (bl, br -> F_b), which a slice skips when its
+                                 lower bits equal the previous slice's; the
+                                 call's slices run with equal lower bits
+                                 adjacent (flops_call counts the skips)      */
+    int64_t n_lower_bits;     /* sliced bits the lower half depends on (all
+                                 of them where nothing is skipped)           */
 } peps_plan_info;
 
 /* Plan of an amplitude call on n_bitstrings with opts (host only). */

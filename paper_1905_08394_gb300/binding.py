@@ -89,7 +89,8 @@ class peps_plan_info(ct.Structure):
                 ("flops_per_chain", ct.c_double), ("bytes_per_chain", ct.c_double),
                 ("flops_call", ct.c_double), ("bytes_call", ct.c_double),
                 ("n_launches", ct.c_int64), ("n_tc_launches", ct.c_int64),
-                ("n_slices", ct.c_int64), ("lanes", ct.c_int64)]
+                ("n_slices", ct.c_int64), ("lanes", ct.c_int64),
+                ("flops_lower", ct.c_double), ("n_lower_bits", ct.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -73,6 +73,7 @@ struct Launch {
   int op = -1;          // kind 2: the OpDesc built
   int64_t kn = 0;       // kind 2: K * N of that operand
   double flops, bytes;
+  bool lower = false;   // odd side: a launch of the lower half (bl, br -> F_b)
 };
 
 struct Plan {
@@ -130,6 +131,13 @@ struct Plan {
   } quarter[4];                 // ul, bl, ur, br
   bool odd = false;             // odd-side partition (Fig. S2(c))
   size_t obuf_off[8] = {};      // odd side: buffer offsets (hi planes), ul ur bl br pairs
+  size_t obuf_fb = 0;           // odd side: F_b's own buffer
+  // odd side, one bitstring: the slice-id bits the lower half depends on (its
+  // sites' sliced CZs); a slice whose lower bits equal the previous slice's
+  // keeps F_b and skips the lower half
+  uint64_t lower_mask = 0;
+  bool lower_skip = false;
+  double flops_lower = 0;       // per slice
   int s_m1 = -1, s_m2 = -1;     // merge steps F_l = F_ul F_bl, Y = F_br F_l^T
   int op_m1 = -1, op_m2 = -1;
   int n_site_ops = 0;           // ops rebuilt from the site tensors per slice
@@ -437,6 +445,7 @@ struct LegInfo {
 };
 
 int popcount32(uint32_t x) { return __builtin_popcount(x); }
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 
 // Which edge and bond bit a CZ ordinal owns.
 struct CzPos {
@@ -584,6 +593,23 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     }
   } else {
     P.slice_list.push_back(0);
+  }
+  P.lower_mask = 0;
+  P.lower_skip = odd && n == 1 && o.n_sliced > 0;
+  if (P.lower_skip) {
+    // the lower half holds rows R/2+1 .. R-1; a CZ touches it if either site does
+    const int m = R / 2;
+    for (int j = 0; j < o.n_sliced; ++j) {
+      const CzPos &p = czpos[o.sliced_cz[j]];
+      const int r0 = p.horiz ? p.edge / (C - 1) : p.edge / C;
+      const int r1 = p.horiz ? r0 : r0 + 1;
+      if (r0 > m || r1 > m) P.lower_mask |= 1ull << j;
+    }
+    // slices with equal lower bits next to one another (the sum's order only)
+    const uint64_t lm = P.lower_mask;
+    std::stable_sort(P.slice_list.begin(), P.slice_list.end(), [lm](int64_t a, int64_t b) {
+      return ((uint64_t)a & lm) < ((uint64_t)b & lm);
+    });
   }
 
   auto rdim_h = [&](int r, int col) -> int64_t {
@@ -1037,19 +1063,25 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   }
   P.odd_bytes = 0;
   if (quad && P.odd) {
-    // odd side: one bitstring at a time, so each sweep pair gets its own size
-    // (ul pair also holds F_u^T, bl pair F_b); all hi planes first, every
-    // lo plane at the same offset behind them
+    // odd side: one bitstring at a time, so each sweep pair gets its own
+    // size.  The lower half (bl, br -> F_b) runs first; only F_b, in a buffer
+    // of its own, outlives it, so the upper half's pairs (ul, which also
+    // holds F_u^T, and ur) reuse the lower half's memory.  All hi planes
+    // first, every lo plane at the same offset behind them.
     const bool two = fmt == FMT_BF16X2 || fmt == FMT_FP16X2;
     const size_t pe = two ? 4 : (size_t)bpe;
     const StepShape &m1 = P.steps[P.s_m1], &m2 = P.steps[P.s_m2];
     const int64_t span[4] = {std::max(P.quarter[0].span, m1.M * (int64_t)m1.N), P.quarter[2].span,
-                             std::max(P.quarter[1].span, m2.M * (int64_t)m2.N), P.quarter[3].span};
-    size_t o2 = 0;
-    for (int b = 0; b < 8; ++b) {
-      P.obuf_off[b] = o2;
-      o2 = align_up(o2 + pe * (size_t)span[b / 2], 1024);
+                             P.quarter[1].span, P.quarter[3].span};
+    size_t top = 0, bot = 0;
+    for (int b = 0; b < 4; ++b) {
+      P.obuf_off[b] = top;
+      top = align_up(top + pe * (size_t)span[b / 2], 1024);
+      P.obuf_off[4 + b] = bot;
+      bot = align_up(bot + pe * (size_t)span[2 + b / 2], 1024);
     }
+    P.obuf_fb = std::max(top, bot);
+    const size_t o2 = align_up(P.obuf_fb + pe * (size_t)(m2.M * (int64_t)m2.N), 1024);
     P.plane = two ? (int64_t)o2 / 2 : 0;
     P.odd_bytes = two ? 2 * o2 : o2;
   }
@@ -1357,12 +1389,13 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     if (P.odd) {
       // per bitstring: bl, br -> F_b; ul, ur -> F_u^T; amplitude = F_u^T . F_b.
       // One bitstring at a time in sized buffers: ul 0-1 (then F_u^T), ur 2-3,
-      // bl 4-5 (then F_b), br 6-7.
+      // bl 4-5, br 6-7 (the lower half's, under the upper half's), F_b.
       auto ob = [&](int b) -> size_t { return P.obuf_off[b]; };
       for (int64_t i = 0; i < n; ++i) {
         const int64_t chain = i;
         auto ch = [&](int) { return chain; };
         auto bit = [&](int) { return i; };
+        const size_t lower_first = P.launches.size();
         const int bbl = sweep(bl, 1, ch, bit, [&](int, int b) { return ob(4 + b); });
         const int bbr = sweep(br, 1, ch, bit, [&](int, int b) { return ob(6 + b); });
         const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
@@ -1375,8 +1408,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           it.op_base = P.op_m2;
           it.in_rec = rec_bl;
           it.out_rec = rec_b;
-          RelItem ri{ob(4 + bbl), ob(4 + (bbl ^ 1)), false, i};
+          RelItem ri{ob(4 + bbl), P.obuf_fb, false, i};
           add_step_launch(P.s_m2, {it}, {ri}, 1);
+        }
+        for (size_t li = lower_first; li < P.launches.size(); ++li) {
+          P.launches[li].lower = true;
+          if (P.launches[li].kind == 0) P.flops_lower += P.launches[li].flops;
         }
         const int bul = sweep(ul, 1, ch, bit, [&](int, int b) { return ob(b); });
         const int bur = sweep(ur, 1, ch, bit, [&](int, int b) { return ob(2 + b); });
@@ -1400,7 +1437,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         dl.flops = dl.bytes = 0;
         DotEntry d{};
         d.Y = (const void *)(REL + ob(bul ^ 1));
-        d.F = (const void *)(REL + ob(4 + (bbl ^ 1)));
+        d.F = (const void *)(REL + P.obuf_fb);
         d.n = ur.batch * ul.batch;
         d.rec_y = rec_u;
         d.rec_f = rec_b;
@@ -1752,6 +1789,17 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   return PEPS_OK;
 }
 
+// Slices of the call that run the lower half (odd side): the first, and every
+// one whose lower bits differ from the slice before it.
+static int64_t lower_runs(const Plan &P) {
+  const int64_t ns = (int64_t)P.slice_list.size();
+  if (!P.lower_skip) return ns;
+  int64_t k = ns > 0 ? 1 : 0;
+  for (int64_t si = 1; si < ns; ++si)
+    if ((((uint64_t)P.slice_list[si] ^ (uint64_t)P.slice_list[si - 1]) & P.lower_mask) != 0) ++k;
+  return k;
+}
+
 extern "C" int peps_workspace_bytes(const peps_ctx *c, int64_t n, const peps_opts *opts,
                                     size_t *bytes) {
   if (!c || !bytes) return fail(PEPS_EINVAL, "peps_workspace_bytes: NULL argument");
@@ -1777,19 +1825,19 @@ extern "C" int peps_plan_info_get(const peps_ctx *c, int64_t n, const peps_opts 
   I.max_entries = P.cap;
   I.flops_per_chain = P.flops_per_slice;
   I.bytes_per_chain = P.bytes_per_slice;
+  I.n_slices = (int64_t)P.slice_list.size();
+  const int64_t nl = lower_runs(P);
   for (auto &l : P.launches) {
     if (l.kind != 0) continue;
-    I.flops_call += l.flops;
-    I.bytes_call += l.bytes;
-    I.n_launches++;
-    I.n_tc_launches += l.tc;
+    const int64_t k = l.lower ? nl : I.n_slices;
+    I.flops_call += (double)k * l.flops;
+    I.bytes_call += (double)k * l.bytes;
+    I.n_launches += k;
+    I.n_tc_launches += l.tc ? k : 0;
   }
-  I.n_slices = (int64_t)P.slice_list.size();
-  I.flops_call *= (double)I.n_slices;
-  I.bytes_call *= (double)I.n_slices;
-  I.n_launches *= I.n_slices;
-  I.n_tc_launches *= I.n_slices;
   I.lanes = P.lanes;
+  I.flops_lower = P.flops_lower;
+  I.n_lower_bits = P.lower_skip ? popcount64(P.lower_mask) : o.n_sliced;
   *info = I;
   return PEPS_OK;
 }
@@ -1817,22 +1865,24 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
   S.launches_operand = ns * (1 + (any_tc ? 1 : 0));
   for (int64_t si = 0; si < ns; ++si)
     S.launches_operand += (P.obe_count[si] > 0 ? 1 : 0) + (P.obe2_count[si] > 0 ? 1 : 0);
+  const int64_t nl = lower_runs(P);
   for (auto &l : P.launches) {
+    const int64_t k = l.lower ? nl : ns;
     if (l.kind == 0) {
-      S.launches_contract += ns;
-      S.contract_flops += ns * l.flops;
-      S.contract_bytes += ns * l.bytes;
+      S.launches_contract += k;
+      S.contract_flops += k * l.flops;
+      S.contract_bytes += k * l.bytes;
       if (l.tc) {
-        S.launches_contract_tc += ns;
-        S.contract_tc_flops += ns * l.flops;
-        S.contract_tc_bytes += ns * l.bytes;
+        S.launches_contract_tc += k;
+        S.contract_tc_flops += k * l.flops;
+        S.contract_tc_bytes += k * l.bytes;
       }
     } else if (l.kind == 2) {
-      S.launches_operand += ns * (l.tc ? 3 : 2);
+      S.launches_operand += k * (l.tc ? 3 : 2);
     } else if (l.kind == 3) {
-      S.launches_finalize += 2 * ns;
+      S.launches_finalize += 2 * k;
     } else {
-      S.launches_finalize += ns;
+      S.launches_finalize += k;
     }
   }
   S.launches_total = S.launches_evolve + S.launches_operand + S.launches_contract + S.launches_finalize;
@@ -1890,7 +1940,13 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
   for (size_t si = 0; si < P.slice_list.size(); ++si) {
-    if (P.n_recs > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, P.n_recs * sizeof(Rec), s));
+    // odd side: the lower half (and F_b's records, the steps after s_m1) stays
+    // when this slice's lower bits equal the previous slice's
+    const bool skip_lower = P.lower_skip && si > 0 &&
+                            (((uint64_t)P.slice_list[si] ^ (uint64_t)P.slice_list[si - 1]) &
+                             P.lower_mask) == 0;
+    const int64_t n_clear = skip_lower ? (int64_t)P.s_m1 + 1 : P.n_recs;
+    if (n_clear > 0) CUDA_TRY(cudaMemsetAsync(recs, 0, n_clear * sizeof(Rec), s));
     // operands whose restriction is unchanged since the previous slice stay
     const OpBuildEntry *e = obe + P.obe_first[si];
     const OpBuild2Entry *e2 = obe2 + P.obe2_first[si];
@@ -1909,6 +1965,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
       S.launches_operand++;
     }
     for (auto &l : P.launches) {
+      if (skip_lower && l.lower) continue;
       if (l.kind == 0) {
         if (timing) CUDA_TRY(cudaEventRecord(c->ev[2 * *n_timed], s));
         if (l.tc) {

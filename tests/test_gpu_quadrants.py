@@ -233,3 +233,30 @@ def test_odd_7x7_d24_chosen_slices_against_the_golden_values(sim_factory):
     for prec in ("fp32", "fp16x3"):
         out = sim.amplitudes(x, precision=prec, sliced_cz=ss.sliced_cz, **QUAD)
         assert relerr(out, ref) < SPLIT_TOL, prec
+
+
+def test_odd_one_bitstring_reuses_the_lower_half(sim_factory):
+    # one bitstring: slices that share their lower-half bits keep F_b; the sum
+    # over every slice is the amplitude, a sub-list of slices the oracle's
+    # sum over the same slices, and a call with one slice per group agrees
+    from paper_1905_08394_gb300 import slicing
+
+    circ = make_circuit(5, 5, 16, 41)
+    _, per = slicing.cz_edges(circ)
+    sl = sorted([per[("h", 0, 1)][0], per[("h", 1, 1)][1], per[("v", 2, 3)][0], per[("h", 3, 2)][0]])
+    x = uniform_bitstrings(25, 1, 41)
+    sim = sim_factory(circ)
+    full = sim.amplitudes(x, precision="fp16x3", **QUAD)
+    tot = sim.amplitudes(x, precision="fp16x3", sliced_cz=sl, **QUAD)
+    assert relerr(tot, full) < SPLIT_TOL
+    st = sim.stats()
+    assert st["launches_contract"] < 16 * sim.plan_info(1, precision="fp16x3", sliced_cz=sl,
+                                                          slice_ids=[0], **QUAD)["n_launches"]
+    ids = [9, 3, 12, 1, 11]
+    part = sim.amplitudes(x, precision="fp16x3", sliced_cz=sl, slice_ids=ids, **QUAD)
+    ref = sum(op.amplitudes(op.build(5, 5, circ.gates, sliced=sl, slice_id=i), x) for i in ids)
+    assert relerr(part, ref) < SPLIT_TOL
+    for i in ids:
+        one = sim.amplitudes(x, precision="fp16x3", sliced_cz=sl, slice_ids=[i], **QUAD)
+        r1 = op.amplitudes(op.build(5, 5, circ.gates, sliced=sl, slice_id=i), x)
+        assert np.abs(one - r1).max() < SPLIT_TOL * np.abs(full).max(), i

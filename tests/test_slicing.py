@@ -101,3 +101,74 @@ def test_square_partition_chooser_fits_7x7_d40():
     o, keep = B.make_opts(precision="fp16x3", scheme="quadrants", flags=B.PEPS_FLAG_ESTIMATE)
     assert B.peps_plan_info_get(h, 1, o)["max_entries"] == 2 ** 40
     B.peps_destroy(h)
+
+
+def test_lower_half_reuse_accounting():
+    # odd side, one bitstring: the planner counts the lower half once per value
+    # of its own bits; the chooser's closed form agrees with the planner's
+    # figure for the call over every slice
+    circ = make_circuit(5, 5, 16, 41)
+    _, per = slicing.cz_edges(circ)
+    sl = sorted([per[("h", 0, 1)][0], per[("h", 1, 1)][1], per[("v", 2, 3)][0], per[("h", 3, 2)][0]])
+    h = ctx_for(circ)
+    o, keep = B.make_opts(precision="fp16x3", scheme="quadrants", sliced_cz=sl, slice_ids=[0])
+    one = B.peps_plan_info_get(h, 1, o)
+    o, keep = B.make_opts(precision="fp16x3", scheme="quadrants", sliced_cz=sl)
+    full = B.peps_plan_info_get(h, 1, o)
+    mask = slicing.lower_half_mask(circ, sl)
+    assert one["n_lower_bits"] == bin(mask).count("1") == 2
+    assert 0 < one["flops_lower"] < one["flops_per_chain"]
+    assert full["flops_call"] == pytest.approx(slicing.call_flops(one, len(sl)), rel=1e-12)
+    assert full["flops_call"] < one["flops_per_chain"] * 2 ** len(sl)
+    # several bitstrings: nothing is reused
+    multi = B.peps_plan_info_get(h, 3, o)
+    assert multi["flops_call"] == pytest.approx(3 * one["flops_per_chain"] * 2 ** len(sl), rel=1e-12)
+    B.peps_destroy(h)
+
+
+def test_slice_group_shares_the_lower_bits():
+    mask = 0b1010011
+    g = slicing.slice_group(7, mask, seed=5)
+    assert len(g) == 2 ** 3 and len(set(g)) == len(g)
+    assert len({x & mask for x in g}) == 1
+    assert g == slicing.slice_group(7, mask, seed=5)
+
+
+@pytest.mark.parametrize("R,C,depth,seed", [(4, 4, 12, 3), (3, 4, 16, 8), (4, 3, 10, 11)])
+def test_vanishing_slices_against_the_oracle(R, C, depth, seed):
+    # slice the last CZs of the circuit (where a run such as sqrt(Y) and the
+    # final H ties a projector to the output bit): every slice the tie rule
+    # rejects is zero in the oracle's sliced network, and the slices it keeps
+    # sum to the amplitude
+    from oracle import peps as op
+    from rqc_inputs import make_circuit, uniform_bitstrings
+
+    circ = make_circuit(R, C, depth, seed)
+    ncz = sum(1 for g in circ.gates if g.kind == "cz")
+    sl = list(range(ncz - 7, ncz))
+    for x in uniform_bitstrings(R * C, 3, seed):
+        x = int(x)
+        keep = set(slicing.consistent_slice_ids(circ, sl, x))
+        assert len(keep) < 2 ** len(sl)          # some tie holds for these circuits
+        vals = {i: op.amplitudes(op.build(R, C, circ.gates, sliced=sl, slice_id=i), [x])[0]
+                for i in range(2 ** len(sl))}
+        full = op.amplitudes(op.build(R, C, circ.gates), [x])[0]
+        scale = max(abs(v) for v in vals.values())
+        for i, v in vals.items():
+            if i not in keep:
+                assert abs(v) <= 1e-12 * scale, (i, v)
+        assert abs(sum(vals[i] for i in keep) - full) <= 1e-12 * abs(full)
+        n_cons, n_low = slicing.slice_counts(circ, sl, x, 0)
+        assert n_cons == len(keep) and n_low == 1
+
+
+def test_ties_without_output_bits():
+    # with no output bit only ties between projectors on one qubit (or to the
+    # initial |0>) remain, and they never fix a bit to a constant after H
+    from rqc_inputs import make_circuit
+
+    circ = make_circuit(4, 4, 12, 3)
+    ncz = sum(1 for g in circ.gates if g.kind == "cz")
+    sl = list(range(ncz - 7, ncz))
+    assert all(i >= 0 for _, i, _ in slicing.slice_constraints(circ, sl))
+    assert len(slicing.consistent_slice_ids(circ, sl)) <= 2 ** len(sl)
