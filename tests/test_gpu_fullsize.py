@@ -128,25 +128,29 @@ def test_7x7_d24_slices_sum_to_the_amplitude(sim7_d24):
 
 
 def test_7x7_d40_subslices(cuda_device):
-    """The 7x7 (1+40+1) circuit with 84 CZ bits held (sub-slices of the slices
-    the benchmark times): the oracle's values vanish (see the generating
-    script), and so must the GPU's, to within the error the forms allow at
-    the amplitude scale 2^-24.5."""
+    """The 7x7 (1+40+1) circuit with 84 CZ bits held (sub-slices; every
+    running tensor of the column sweep at most 2^26 entries), at values that
+    do not vanish (see the generating script): four sub-slices of magnitude
+    ~1e-20 against the oracle, normwise.  Column sweep only: these held bits
+    lie on horizontal edges, which leave the square partition's quarters
+    near full size (836 GiB)."""
     from paper_1905_08394_gb300 import Simulator
 
     g = _golden("oracle_7x7_d40.json")
     circ, bits = workload("7x7_d40")
     assert int(bits[0]) == g["bitstring"]
+    ref = np.array([complex(*sub["amplitude"]) for sub in g["subslices"]])
+    assert len(ref) == 4 and np.abs(ref).min() > 1e-22
     s = Simulator(7, 7)
     s.apply_circuit(circ)
-    scale = 2.0 ** -24.5
-    for sub in g["subslices"]:
-        ref = complex(*sub["amplitude"])
+    for scheme in ("columns",):
         for prec in ("fp32", "fp16x3"):
-            a = s.amplitudes(bits[:1], precision=prec, fixed_cz=g["fixed_cz"],
-                             fixed_s=sub["fixed_s"])[0]
-            print(f"7x7 d40 sub-slice {prec}: gpu {a:.3e} oracle {ref:.3e}")
-            assert abs(a - ref) < TOL * scale
+            out = np.array([s.amplitudes(bits[:1], precision=prec, scheme=scheme,
+                                         fixed_cz=g["fixed_cz"], fixed_s=sub["fixed_s"])[0]
+                            for sub in g["subslices"]])
+            err = float(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+            print(f"7x7 d40 sub-slices {scheme} {prec}: normwise rel.err {err:.3e}")
+            assert err < TOL, (scheme, prec)
     s.close()
 
 

@@ -260,3 +260,27 @@ def test_odd_one_bitstring_reuses_the_lower_half(sim_factory):
         one = sim.amplitudes(x, precision="fp16x3", sliced_cz=sl, slice_ids=[i], **QUAD)
         r1 = op.amplitudes(op.build(5, 5, circ.gates, sliced=sl, slice_id=i), x)
         assert np.abs(one - r1).max() < SPLIT_TOL * np.abs(full).max(), i
+
+
+def test_7x7_d32_sliced_square_partition_against_the_column_sweep(sim_factory):
+    # the 7x7 geometry at bond dimension 16, whole: the slices the square
+    # partition's chooser picks for one bitstring under 4 GiB, only those the
+    # tie rule keeps, sum to the unsliced square partition, which agrees with
+    # the column sweep; slices the rule rejects vanish on the GPU
+    from paper_1905_08394_gb300 import slicing
+
+    circ = make_circuit(7, 7, 32, 5)
+    x = uniform_bitstrings(49, 1, 5)
+    sim = sim_factory(circ)
+    col = sim.amplitudes(x, precision="fp16x3")
+    quad = sim.amplitudes(x, precision="fp16x3", **QUAD)
+    assert relerr(quad, col) < 2 * SPLIT_TOL
+    ss = slicing.choose_quadrants(sim.h, circ, 4 << 30, seed=5, x=int(x[0]))
+    keep = slicing.consistent_slice_ids(circ, ss.sliced_cz, int(x[0]))
+    assert 0 < len(keep) < 2 ** len(ss.sliced_cz)
+    tot = sim.amplitudes(x, precision="fp16x3", sliced_cz=ss.sliced_cz, slice_ids=keep, **QUAD)
+    assert relerr(tot, quad) < SPLIT_TOL
+    drop = [i for i in range(min(2 ** len(ss.sliced_cz), 4096)) if i not in set(keep)][:4]
+    for i in drop:
+        z = sim.amplitudes(x, precision="fp16x3", sliced_cz=ss.sliced_cz, slice_ids=[i], **QUAD)
+        assert abs(z[0]) <= 1e-12 * abs(quad[0]), i
