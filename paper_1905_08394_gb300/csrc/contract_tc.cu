@@ -56,7 +56,7 @@ template <> struct FormTraits<FMT_FP16X2> { static constexpr int NP = 2, ESZ = 2
 template <> struct FormTraits<FMT_TF32>   { static constexpr int NP = 1, ESZ = 4, KIND = 1, AB = 2; };
 
 struct __align__(64) TcParams {
-  CUtensorMap mapA;        // {k, m, plane, lane}
+  CUtensorMap mapA;        // {k, m, plane, lane}; m_hi-major steps: {k, m_hi, m_lo, b, plane/lane}
   CUtensorMap mapB[4][2];  // [block variant][plane] {k, n}
   StepShape sh;
   const StepItem *items;
@@ -75,6 +75,14 @@ struct __align__(64) TcParams {
   int nacc;     // accumulators per buffer: ksplit + csep
   int nbuf;     // accumulator buffers (2: the epilogue of a tile overlaps the
                 // next tile's MMAs)
+  int mhi;      // 1: a tile's rows are ph consecutive m_hi x lh consecutive m_lo
+                // (ph lh = BM) at one b, so that the open-leg store (contiguous
+                // in m_hi only) coalesces
+  int lp_mul;   // m_hi-major: the A map's last coordinate is lane * lp_mul + plane
+  int ph, lh;   // m_hi-major: tile extent in m_hi (min(P, BM)) and in m_lo
+  int gm;       // tile order: gm row groups at a time, n fastest within them
+                // (1: n fastest over a whole row group)
+  int64_t mlo;  // m_hi-major: Mr / P
   int64_t watchdog_ns;
 };
 
@@ -189,6 +197,23 @@ __device__ __forceinline__ void tma_load_4d_cg2(void *dst, const CUtensorMap *ma
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar_cluster_addr)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d_cg2(void *dst, const CUtensorMap *map,
+                                                uint32_t bar_cluster_addr, int c0, int c1, int c2,
+                                                int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar_cluster_addr)
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_2d_cg2(void *dst, const CUtensorMap *map,
                                                 uint32_t bar_cluster_addr, int c0, int c1) {
   asm volatile(
@@ -204,6 +229,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Tile `rem` of an item -> (row group mg, column tile nt).  Blocks of gm row
+// groups are walked column by column, so that the tiles in flight at once
+// (one per CTA pair) share the k-slabs of gm A row panels and of a few B
+// column panels in L2; gm = 1 is the plain n-fastest order.
+__device__ __forceinline__ void tile_of(int rem, int mgroups, int tiles_n, int gm, int &mg,
+                                        int &nt) {
+  if (gm <= 1) {
+    mg = rem / tiles_n;
+    nt = rem - mg * tiles_n;
+    return;
+  }
+  const int blk = rem / (gm * tiles_n), within = rem - blk * gm * tiles_n;
+  const int g0 = blk * gm, gsz = mgroups - g0 < gm ? mgroups - g0 : gm;
+  nt = within / gsz;
+  mg = g0 + (within - nt * gsz);
 }
 
 // Shared-memory matrix descriptor of a K-major swizzled tile (rows of
@@ -372,10 +414,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       for (int t = cid; t < total; t += ncl) {
         const int item = t / tiles_per_item;
         const int rem = t - item * tiles_per_item;
-        const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
+        int mg, nt;
+        tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
         const int mt = mg * CG + (int)rank;
         const StepItem &si = p.items[item];
         const int tau = block_variant(*si.bits, p.sh);
+        // m_hi-major: tile mt is rows m_hi = hb0 .. hb0+ph-1, m_lo = mlo_t ..
+        // mlo_t+lh-1 at b_t
+        int64_t b_t = 0, mlo_t = 0;
+        int hb0 = 0;
+        if (p.mhi) {
+          const int64_t hper = p.sh.P / p.ph, lper = p.mlo / p.lh;
+          const int64_t rest = mt / hper;
+          hb0 = (int)(mt - rest * hper) * p.ph;
+          b_t = rest / lper;
+          mlo_t = (rest - b_t * lper) * p.lh;
+        }
         bool ok = true;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
           const int s = it % S;
@@ -386,7 +440,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           if (CG == 1) {
             mbar_expect_tx(&full[s], stage_bytes);
             for (int pl = 0; pl < NP; ++pl) {
-              tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
+              if (p.mhi)
+                tma_load_5d(st + pl * a_bytes, &p.mapA, &full[s], k0, hb0, (int)mlo_t, (int)b_t,
+                            si.a_lane * p.lp_mul + pl);
+              else
+                tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
               tma_load_2d(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl], &full[s], k0,
                           nt * BN);
             }
@@ -394,8 +452,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
             // the even CTA's full barrier counts both CTAs' bytes
             if (leader) mbar_expect_tx(&full[s], 2 * stage_bytes);
             for (int pl = 0; pl < NP; ++pl) {
-              tma_load_4d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0, mt * BM,
-                              pl, si.a_lane);
+              if (p.mhi)
+                tma_load_5d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0, hb0,
+                                (int)mlo_t, (int)b_t, si.a_lane * p.lp_mul + pl);
+              else
+                tma_load_4d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0,
+                                mt * BM, pl, si.a_lane);
               tma_load_2d_cg2(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl],
                               full0 + (uint32_t)s * 8u, k0, nt * BN + (int)rank * BNL);
             }
@@ -494,7 +556,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     for (int t = cid; t < total; t += ncl, ++local) {
       const int item = t / tiles_per_item;
       const int rem = t - item * tiles_per_item;
-      const int mg = rem / p.tiles_n, nt = rem - mg * p.tiles_n;
+      int mg, nt;
+      tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
       const int mt = mg * CG + (int)rank;
       if (item != cached_item) {
         cached_item = item;
@@ -513,11 +576,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc_fence_after();
-      const int64_t m = (int64_t)mt * BM + row;
-      const bool live = m < M;
-      // row m = b * Mr + m_r (b: the batch of open legs, when there is one)
-      const int64_t b = live ? m / Mr : 0, mr = live ? m - b * Mr : 0;
-      const int64_t m_hi = mr / Mlo, m_lo = mr % Mlo;
+      int64_t b, m_hi, m_lo;
+      bool live;
+      if (p.mhi) {
+        // row = l ph + h: m_hi = hb0 + h, m_lo = mlo_t + l (the tile of the producer)
+        const int64_t hper = P / p.ph, lper = Mlo / p.lh, rest = mt / hper;
+        m_hi = (mt - rest * hper) * p.ph + row % p.ph;
+        b = rest / lper;
+        m_lo = (rest - b * lper) * p.lh + row / p.ph;
+        live = true;
+      } else {
+        const int64_t m = (int64_t)mt * BM + row;
+        live = m < M;
+        // row m = b * Mr + m_r (b: the batch of open legs, when there is one)
+        b = live ? m / Mr : 0;
+        const int64_t mr = live ? m - b * Mr : 0;
+        m_hi = mr / Mlo;
+        m_lo = mr % Mlo;
+      }
       float vmax = 0.f;
       const int KSP = p.nacc;   // K segments, then the correction accumulator
       const uint32_t tbase =
@@ -687,11 +763,61 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
       esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
   const CUtensorMapSwizzle sw =
       rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  {
+  // unused dimensions (one plane, one lane) get the packed stride
+  const int64_t packed = (int64_t)Kr * esz * sh.M;
+  // A step that stores its open bottom leg into the batch (vb) writes
+  // (b dv' + v') Mr dh' + ((m_lo dh' + h') P + m_hi): contiguous in m_hi
+  // only.  Its tiles then take ph = min(P, BM) consecutive m_hi by lh = BM / ph
+  // consecutive m_lo at one b, through a 5-d map {k, m_hi, m_lo, b,
+  // plane/lane} (the plane and the lane share a coordinate: lane * lp_mul +
+  // plane), so that a warp's stores cover 32 consecutive entries.  The box
+  // lands in shared memory as the usual 128 rows (row = l ph + h).
+  bool mhi = false;
+  int64_t lp_mul = 1, lp_stride = 0, lp_ext = 1;
+  const int64_t ph = sh.P < BM ? sh.P : BM, lh = BM / (ph > 0 ? ph : 1);
+  if (sh.vb && sh.nvs == 0 && sh.P >= 32 && (sh.P % BM == 0 || BM % sh.P == 0) && sh.Mr > 0 &&
+      sh.Mr % sh.P == 0 && sh.M % sh.Mr == 0 && (sh.Mr / sh.P) % lh == 0) {
+    if (np > 1) {
+      if (a_lanes == 1) {
+        mhi = true;
+        lp_stride = plane_stride_bytes;
+        lp_ext = np;
+      } else if (plane_stride_bytes > 0 && a_lane_stride % plane_stride_bytes == 0) {
+        mhi = true;
+        lp_mul = a_lane_stride / plane_stride_bytes;
+        lp_stride = plane_stride_bytes;
+        lp_ext = (int64_t)(a_lanes - 1) * lp_mul + np;
+      }
+    } else {
+      mhi = true;
+      lp_stride = a_lanes > 1 ? a_lane_stride : packed;
+      lp_ext = a_lanes;
+    }
+    if (lp_stride % 16 != 0) mhi = false;
+  }
+  if (mhi) {
+    const int64_t Mlo = sh.Mr / sh.P, B = sh.M / sh.Mr;
+    cuuint64_t dims[5] = {(cuuint64_t)Kr, (cuuint64_t)sh.P, (cuuint64_t)Mlo, (cuuint64_t)B,
+                          (cuuint64_t)lp_ext};
+    cuuint64_t strides[4] = {(cuuint64_t)(Mlo * Kr * esz), (cuuint64_t)Kr * esz,
+                             (cuuint64_t)(sh.Mr * Kr * esz), (cuuint64_t)lp_stride};
+    cuuint32_t box[5] = {(cuuint32_t)(rowb / esz), (cuuint32_t)ph, (cuuint32_t)lh, 1, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(&d->prm.mapA, dt, 5, const_cast<void *>(a_base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      delete d;
+      return -3;
+    }
+    d->prm.mhi = 1;
+    d->prm.lp_mul = (int)lp_mul;
+    d->prm.ph = (int)ph;
+    d->prm.lh = (int)lh;
+    d->prm.mlo = Mlo;
+  } else {
     cuuint64_t dims[4] = {(cuuint64_t)Kr, (cuuint64_t)sh.M, (cuuint64_t)np,
                           (cuuint64_t)a_lanes};
-    // unused dimensions (one plane, one lane) get the packed stride
-    const int64_t packed = (int64_t)Kr * esz * sh.M;
     const int64_t plane_st = np > 1 ? plane_stride_bytes : packed;
     const int64_t lane_st = a_lanes > 1 ? a_lane_stride : plane_st * np;
     cuuint64_t strides[3] = {(cuuint64_t)Kr * esz, (cuuint64_t)((plane_st + 15) / 16 * 16),
@@ -747,6 +873,13 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   d->prm.BN = BN;
   d->prm.tiles_m = (int)((sh.M + BM - 1) / BM);
   d->prm.tiles_n = Nr / BN;
+  // wide launches (the merges): 8 row groups at a time, so that concurrent
+  // tiles reuse both operands' k-slabs from L2 instead of streaming one B
+  // column panel per tile
+  {
+    const int mgroups = d->prm.tiles_m / d->cg;
+    d->prm.gm = (d->prm.tiles_n >= 32 && mgroups >= 16) ? 8 : 1;
+  }
   d->prm.ksplit = KS;
   d->prm.csep = CS;
   d->prm.nacc = NA;
