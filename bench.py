@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--slices", type=int, default=4, help="(unused; kept for older command lines)")
     ap.add_argument("--check-full", action="store_true",
                     help="--case slices: also the amplitude from the slice set chosen without x")
+    ap.add_argument("--group-only", action="store_true",
+                    help="--case slices: only one run of slices that share the lower half "
+                         "(the profiling case), timed in one call")
     return ap.parse_args()
 
 
@@ -551,8 +554,19 @@ def run_slices_case(args):
     kw = dict(base, sliced_cz=ss.sliced_cz, slice_ids=ids)
     # warm-up: one run of slices that share the lower half (evolution, kernels)
     group = [i for i in ids if (i & lmask) == (ids[0] & lmask)]
+    t0 = time.time()
     sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **dict(kw, slice_ids=group))
     torch.cuda.synchronize()
+    if args.group_only:
+        st = sim.stats()
+        print(json.dumps({"case": "slices", "workload": "7x7 (1+40+1), one run of slices that "
+                          "share the lower half", "slices": len(group),
+                          "wall_seconds": time.time() - t0,
+                          "contract_seconds": st["contract_ms"] / 1e3,
+                          "flops": st["contract_flops"], "launches": st["launches_total"]}),
+              flush=True)
+        sim.close()
+        return
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
