@@ -51,8 +51,8 @@ FLOPS_PER_CMAC = 8
 # --steps 1 --warmup 1 --other-steps 1`: mean DRAM bytes per k_contract_tc
 # launch, per contraction scheme (2200 column-sweep launches in 5 calls, 2640
 # square-partition launches in 6 calls).
-TRAFFIC = {"sources_sha256_16": "985e4f68b332ea27",
-           "bytes_per_launch": {"columns": 37.88e9, "quadrants": 3.580e9}}
+TRAFFIC = {"sources_sha256_16": "d2d8f442fc786027",
+           "bytes_per_launch": {"columns": 36.36e9, "quadrants": 2.562e9}}
 TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
 
 
