@@ -27,7 +27,7 @@ roofline  the tensor-core contraction kernel: algorithmic flops per launch
         while the kernel's sources hash to the captured version.
 cpu_baseline  the CPU FP64 oracle on a bounded sample (see "sample").
 
---impl reference times the oracle (the reference arm of this build).
+--impl reference times the CPU FP64 oracle on the same workload (the reference arm).
 """
 from __future__ import annotations
 
@@ -204,7 +204,9 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"peps_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

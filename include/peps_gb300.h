@@ -61,7 +61,7 @@ typedef enum {
     PEPS_ECUDA = -4,        /* a CUDA runtime/driver call failed             */
     PEPS_ETIMEOUT = -5,     /* a device wait exceeded the watchdog budget    */
     PEPS_ESTATE = -6,       /* context unusable after an earlier failure     */
-    PEPS_EUNSUPPORTED = -7  /* valid request this build cannot run           */
+    PEPS_EUNSUPPORTED = -7  /* valid request this library cannot run         */
 } peps_status;
 
 /* Arithmetic of the column-absorption contraction (the other kernels are
