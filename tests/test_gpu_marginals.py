@@ -49,15 +49,27 @@ def test_4x4_against_the_state_vector(sim_factory, scheme, prec):
         assert np.abs(got.imag).max() < 1e-6 * np.abs(ref).max()
 
 
-def test_5x5_against_the_state_vector(sim_factory):
+@pytest.mark.parametrize("scheme", ["columns", "quadrants"])
+def test_5x5_against_the_state_vector(sim_factory, scheme):
+    # quadrants: the odd-side square partition (Fig. S2(c)) on the double layer
     circ = make_circuit(5, 5, 16, 22)
     x = uniform_bitstrings(25, 8, 22)
     sim = sim_factory(circ)
     mask = (1 << 12) - 1
     ref = sv.marginals(25, circ.gates, x, mask)
     for prec in ("fp32", "fp16x3"):
-        got = sim.amplitudes(x, precision=prec, measured_mask=mask)
-        assert relerr(got.real, ref) < TOL
+        got = sim.amplitudes(x, precision=prec, scheme=scheme, measured_mask=mask)
+        assert relerr(got.real, ref) < TOL, prec
+
+
+def test_3x3_odd_partition_every_mask(sim_factory):
+    circ = make_circuit(3, 3, 16, 23)
+    x = uniform_bitstrings(9, 16, 23)
+    sim = sim_factory(circ)
+    for mask in (0x001, 0x010, 0x0F0, 0x1FF):
+        ref = sv.marginals(9, circ.gates, x, mask)
+        got = sim.amplitudes(x, precision="fp16x3", scheme="quadrants", measured_mask=mask)
+        assert relerr(got.real, ref) < TOL, mask
 
 
 def test_special_cases(sim_factory):
