@@ -16,8 +16,12 @@ property of one running tensor: a bit cut on a quarter's open leg shrinks its
 sweep from the column where that leg appears, and a quarter is recomputed for
 every bit it does not touch.  `choose_quadrants` therefore searches on the C
 planner's own figures (multiply-adds per slice and workspace bytes): a beam
-search that adds one cut bit at a time and keeps the cheapest total
-(per-slice flops x 2^|S|) among the sets whose workspace fits the budget.
+search that adds one cut bit at a time and keeps the cheapest total among the
+sets whose workspace fits the budget.  The total counts the odd side's lower
+half once per value of its own bits (one bitstring: consecutive slices that
+share them keep F_b) and, for a given output bitstring, only the slices that
+can be nonzero: ties between slice bits (`slice_constraints`, below) make the
+others vanish exactly.
 """
 from __future__ import annotations
 
@@ -419,31 +423,15 @@ def consistent_slice_ids(circ, sliced_cz, x=None):
     """The slice ids that satisfy every tie of slice_constraints (the others
     are exactly zero), ascending; [] when the ties contradict one another."""
     S = len(sliced_cz)
-    parent = list(range(S + 1))        # node S: the constant 0
-    par = [0] * (S + 1)                # parity to the parent
-
-    def find(u):
-        p = 0
-        while parent[u] != u:
-            p ^= par[u]
-            u = parent[u]
-        return u, p
-
-    for j, i, c in slice_constraints(circ, sliced_cz, x):
-        a, b = (j, S if i < 0 else i)
-        ra, pa = find(a)
-        rb, pb = find(b)
-        if ra == rb:
-            if pa ^ pb != c:
-                return []
-            continue
-        parent[ra] = rb
-        par[ra] = pa ^ pb ^ c
-    roots = sorted({find(u)[0] for u in range(S)} - {find(S)[0]})
+    find = _tie_components(circ, sliced_cz, x)
+    if find is None:
+        return []
+    const = find(S)[0]
+    roots = sorted({find(u)[0] for u in range(S)} - {const})
     out = []
     for t in range(1 << len(roots)):
         val = {r: (t >> i) & 1 for i, r in enumerate(roots)}
-        val[find(S)[0]] = 0
+        val[const] = 0
         sid = 0
         for u in range(S):
             r, p = find(u)
