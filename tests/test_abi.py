@@ -175,6 +175,28 @@ def test_quadrant_plan_matches_the_oracle_count(R, C, d, seed):
     B.peps_destroy(h)
 
 
+@pytest.mark.parametrize("L,d,seed", [(3, 8, 1), (5, 16, 2), (5, 12, 7), (7, 24, 5)])
+def test_odd_quadrant_plan_matches_the_oracle_count(L, d, seed):
+    # odd side (Fig. S2(c)): the planner merges in the paper's order (ul with
+    # ur, bl with br), so with single-site steps its multiply-adds equal the
+    # oracle's direct count less the last contraction (the dot over the
+    # horizontal cut), and the largest tensors agree
+    from oracle import peps as op
+    c, h = make(L, L, d, seed)
+    o, k = B.make_opts(precision="fp16x3", scheme="quadrants", fuse_rows=1)
+    info = B.peps_plan_info_get(h, 1, o)
+    dims = _bond_dims(h, L, L)
+    cost = op.quadrant_contraction_cmacs(L, L, dims)
+    m = L // 2
+    cut = 1
+    for (a, b), v in dims.items():
+        if (a // L <= m) != (b // L <= m):
+            cut *= v
+    assert info["flops_per_chain"] == 8 * (cost["quarters"] + cost["merges"] - cut)
+    assert info["max_entries"] == cost["largest"]
+    B.peps_destroy(h)
+
+
 def test_quadrant_sweeps_fuse_their_top_row_pairs():
     # in each sweep column of a 3 x 3 quarter the top two rows go in one step
     # (no incoming vertical leg): 6 steps per quarter instead of 9, the same
