@@ -35,6 +35,19 @@ def rank_prefix_batch(R: int, C: int, prefix_cols: int, groups_per_rank: int, pe
     return allbits[g0 * per_group:g1 * per_group]
 
 
+def rank_slice_ids(ids, lower_mask: int, world: int, rank: int) -> list:
+    """This rank's share of one amplitude's slices: whole runs of slices that
+    share the odd-side lower half's bits (so that each rank keeps the lower
+    half's reuse), the runs split contiguously over the ranks.  Each rank sums
+    its slices; allreduce_sum_c128 adds the ranks' partial amplitudes."""
+    runs = {}
+    for i in sorted(int(v) for v in ids):
+        runs.setdefault(i & lower_mask, []).append(i)
+    keys = sorted(runs)
+    g0, g1 = shard(len(keys), world, rank)
+    return [i for k in keys[g0:g1] for i in runs[k]]
+
+
 def max_over_ranks(value: float, dist, device=None) -> float:
     """Max of a float over all ranks (the timing rule of the benchmark)."""
     import torch
