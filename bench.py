@@ -527,7 +527,7 @@ def run_profile_case(args):
 def run_slices_case(args):
     """7x7 (1+40+1), one bitstring x, on the odd-side square partition (Fig.
     S2(c)): the whole amplitude.  The slice set is the square-partition
-    chooser's under a 200 GiB workspace, given x: the CZs whose bit x fixes
+    chooser's under a 180 GB workspace, given x: the CZs whose bit x fixes
     are cut first (they add no slices), and only the slices that can be
     nonzero run (slicing.consistent_slice_ids), lower-half reuse included.
     Timed in one call, the evolution included.  The same amplitude from a
@@ -546,7 +546,7 @@ def run_slices_case(args):
     sim = Simulator(circ.R, circ.C)
     sim.apply_circuit(circ)
     t0 = time.time()
-    ss = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5, x=x)
+    ss = slicing.choose_quadrants(sim.h, circ, 180 * 10 ** 9, precision=args.precision, seed=5, x=x)
     choose_s = time.time() - t0
     ids = slicing.consistent_slice_ids(circ, ss.sliced_cz, x)
     lmask = slicing.lower_half_mask(circ, ss.sliced_cz)
@@ -592,7 +592,7 @@ def run_slices_case(args):
              "amplitude": [amp2.real, amp2.imag], "wall_seconds": t2,
              "rel_diff": abs(amp2 - amp) / abs(amp) if amp != 0 else None}
     if args.check_full:
-        s3 = slicing.choose_quadrants(sim.h, circ, 200 * 2 ** 30, precision=args.precision, seed=5)
+        s3 = slicing.choose_quadrants(sim.h, circ, 180 * 10 ** 9, precision=args.precision, seed=5)
         ids3 = slicing.consistent_slice_ids(circ, s3.sliced_cz, x)
         t1 = time.time()
         amp3 = complex(sim.amplitudes(bits, sliced_cz=s3.sliced_cz, slice_ids=ids3, **base)[0])
