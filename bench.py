@@ -45,6 +45,37 @@ METRIC = "amplitudes/s at 6x6 (1+32+1), mixed vs FP32 path, rel.err <= 1e-5"
 UNIT = "amplitudes/s"
 WORKLOAD = "6x6_d32"
 FLOPS_PER_CMAC = 8
+REL_ERR_GATE = 1e-5
+# the workload, identical in both arms' lines
+CONFIG = {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing columns 0-2",
+          "seed": 4, "bitstrings": 512,
+          "l2": "inputs larger than L2 (128 MiB quarter tensors x 4 per lane for the square "
+                "partition, 2 GiB running tensor per lane for the column sweep)"}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_6x6_d32.json")
+
+
+def golden_check(out, bits, first=0):
+    """Normwise relative error of `out` (amplitudes of bits[first:first+len(out)])
+    against the FP64 oracle values of this batch stored in tests/golden (written
+    by the oracle alone).  Returns None when the batch holds none of them."""
+    import numpy as np
+
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    idx, ref, got = [], [], []
+    for i, b, a in zip(g["indices"], g["bitstrings"], g["amplitudes"]):
+        j = i - first
+        if 0 <= j < len(out) and int(bits[i]) == int(b):
+            idx.append(i)
+            ref.append(complex(a[0], a[1]))
+            got.append(complex(out[j]))
+    if not idx:
+        return None
+    ref, got = np.array(ref), np.array(got)
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"rel_err": err, "rel_err_ok": bool(err <= REL_ERR_GATE), "gate": REL_ERR_GATE,
+            "checked": len(idx), "indices": idx,
+            "against": "FP64 oracle values of these bitstrings (tests/golden/oracle_6x6_d32.json)"}
 
 # ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
 # dram__bytes_write.sum; one pass) of `bench.py --no-cpu --fp32-steps 0
@@ -103,7 +134,6 @@ def parse():
                          "circuit and their Porter-Thomas statistics; marginals: marginal "
                          "probabilities of the top half's 18 qubits of a 6x6 (1+16+1) "
                          "circuit (the double-layer network), 512 bitstrings")
-    ap.add_argument("--slices", type=int, default=4, help="(unused; kept for older command lines)")
     ap.add_argument("--check-full", action="store_true",
                     help="--case slices: also the amplitude from the slice set chosen without x")
     ap.add_argument("--group-only", action="store_true",
@@ -125,18 +155,18 @@ def load_peaks():
 # CPU oracle sample
 # ---------------------------------------------------------------------------
 
-def oracle_sample(seconds: float, scheme: str = "columns"):
-    """Time the FP64 oracle on the batch's first bitstring for about `seconds`
-    and scale by flops to the batched job's flops per amplitude, for the given
-    contraction scheme:
-      columns    the oracle's column sweep, cut off after `seconds`; the job
-                 reuses columns 0-2 across each group of 64;
+def oracle_sample(seconds: float, scheme: str = "quadrants", start: int = 0):
+    """Time the FP64 oracle, as it stands, on this workload for about `seconds`.
       quadrants  the oracle's square partition (four quarters, the two pair
-                 merges and the last contraction) of one bitstring, repeated
-                 while time is left; the job builds the left half once per
-                 group of 64 and does one quarter pair, one merge and the dot
-                 product per bitstring.
-    Returns (amplitudes/s, description, cores)."""
+                 merges, the last contraction) of whole amplitudes of the
+                 batch's bitstrings start, start+1, ... until the time is up
+                 (at least one): measured amplitudes/s, nothing projected;
+      columns    the oracle's column sweep of the batch's first bitstring,
+                 cut off after `seconds` (one amplitude takes far longer) and
+                 scaled by flops to the batched job's flops per amplitude
+                 (prefix reuse over each group of 64): a projection.
+    Returns (amplitudes/s, description, cores, projected, seconds spent,
+    amplitudes done)."""
     import numpy as np
 
     from oracle import peps as op
@@ -147,53 +177,40 @@ def oracle_sample(seconds: float, scheme: str = "columns"):
     p = op.build(circ.R, circ.C, circ.gates)
     R, C = circ.R, circ.C
     if scheme == "quadrants":
-        dims = {}
-        for r in range(R):
-            for c in range(C):
-                q = r * C + c
-                if c + 1 < C:
-                    dims[(q, q + 1)] = p.bond_dim(q, q + 1)
-                if r + 1 < R:
-                    dims[(q, q + C)] = p.bond_dim(q, q + C)
-        cost = op.quadrant_contraction_cmacs(R, C, dims)
-        chi_l = 16 ** C            # the last contraction (the GPU's dot product)
-        one = cost["quarters"] + cost["merges"]
-        # per bitstring of the job: half the quarters and half the pair merges
-        # per bitstring plus the same again per group of 64, and the dot
-        per_amp = (cost["quarters"] / 2 + (cost["merges"] - chi_l) / 2) * (1 + 1 / 64) + chi_l
         t0 = time.perf_counter()
         done = 0
         while True:
-            op.amplitude_quadrant(p, int(bits[0]))
+            op.amplitude_quadrant(p, int(bits[(start + done) % len(bits)]))
             done += 1
             if time.perf_counter() - t0 > seconds:
                 break
         dt = time.perf_counter() - t0
-        cmacs = done * one
-        what = (f"oracle O3 (numpy complex128 tensordot) square partition of bitstring 0, "
-                f"{done} full amplitude(s)")
-    else:
-        E = p.project(int(bits[0]))
-        steps = cx.column_sweep_step_cmacs(R, C, 16)
-        order = op.sweep_order(R, C, "column")
-        G, labels = np.ones((), dtype=np.complex128), []
-        t0 = time.perf_counter()
-        done = 0
-        cmacs = 0
-        for i, q in enumerate(order):
-            G, labels = op.absorb(G, labels, E[q], q, R, C)
-            cmacs += steps[i]
-            done += 1
-            if time.perf_counter() - t0 > seconds:
-                break
-        dt = time.perf_counter() - t0
-        per_amp = (8 * sum(steps[:18]) + 512 * sum(steps[18:])) / 512  # prefix reuse, as the GPU job
-        what = (f"oracle O3 (numpy complex128 tensordot) column sweep of bitstring 0, first {done} "
-                f"of 36 site absorptions")
+        rate = done / dt
+        desc = (f"oracle O3 (numpy complex128 tensordot), square partition, {done} whole "
+                f"amplitude(s) of the batch's bitstrings {start}..{start + done - 1} in {dt:.1f} s "
+                f"(measured, not projected)")
+        return rate, desc, os.cpu_count(), False, dt, done
+    E = p.project(int(bits[0]))
+    steps = cx.column_sweep_step_cmacs(R, C, 16)
+    order = op.sweep_order(R, C, "column")
+    G, labels = np.ones((), dtype=np.complex128), []
+    t0 = time.perf_counter()
+    done = 0
+    cmacs = 0
+    for i, q in enumerate(order):
+        G, labels = op.absorb(G, labels, E[q], q, R, C)
+        cmacs += steps[i]
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    per_amp = (8 * sum(steps[:18]) + 512 * sum(steps[18:])) / 512  # prefix reuse, as the GPU job
     rate = (cmacs / dt) / per_amp
-    desc = (f"{what} ({cmacs * FLOPS_PER_CMAC:.3e} flops in {dt:.1f} s), scaled by "
-            f"{per_amp * FLOPS_PER_CMAC:.3e} flops per amplitude of the batched job ({scheme})")
-    return rate, desc, os.cpu_count()
+    desc = (f"oracle O3 (numpy complex128 tensordot) column sweep of bitstring 0, first {done} "
+            f"of 36 site absorptions ({cmacs * FLOPS_PER_CMAC:.3e} flops in {dt:.1f} s), scaled "
+            f"by {per_amp * FLOPS_PER_CMAC:.3e} flops per amplitude of the batched job "
+            f"(projected)")
+    return rate, desc, os.cpu_count(), True, dt, 0
 
 
 class Clocks:
@@ -260,6 +277,9 @@ def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world:
+        raise SystemExit(f"bench.py --gpus {args.gpus} needs one process per GPU: launch it with "
+                         f"torchrun --nproc-per-node {args.gpus} (WORLD_SIZE is {world})")
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -269,28 +289,41 @@ def dist_setup(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU FP64 oracle as it stands, on this machine's host
+    cores, on the workload of the GPU arm.  Each step is a bounded sample
+    (whole amplitudes of the batch's bitstrings by the square partition),
+    sized so that warm-up plus timed steps take about two and a half minutes;
+    `value` is the amplitudes per second measured over the timed steps."""
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         if pg:
             pg.barrier()
         return
-    vals = []
-    desc = cores = None
     scheme = args.scheme if args.scheme != "auto" else "quadrants"
+    per_step = min(args.cpu_seconds, max(1.0, 150.0 / max(1, args.steps + args.warmup)))
+    nxt = 0
     for _ in range(args.warmup):
-        oracle_sample(max(2.0, args.cpu_seconds / 4), scheme)
+        _, _, _, _, _, k = oracle_sample(0.0 if scheme == "quadrants" else 1.0, scheme, nxt)
+        nxt += k
+    spent, amps, rates = 0.0, 0, []
+    desc = cores = None
+    projected = False
     for _ in range(args.steps):
-        v, desc, cores = oracle_sample(args.cpu_seconds, scheme)
-        vals.append(v)
-    value = sum(vals) / len(vals)
+        v, desc, cores, projected, dt, k = oracle_sample(per_step, scheme, nxt)
+        nxt += k
+        spent += dt
+        amps += k
+        rates.append(v)
+    value = amps / spent if not projected else sum(rates) / len(rates)
+    sample = (f"{args.steps} step(s) of about {per_step:.1f} s each; last step: {desc}"
+              if not projected else desc)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 512 / value * 1000, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
-                                   "columns 0-2", "seed": 4, "scheme": scheme},
+            "ms_per_step": spent / args.steps * 1000, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": dict(CONFIG),
+            "scheme": scheme, "projected": projected,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+                             "sample": sample, "projected": projected},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -381,10 +414,11 @@ def run_mine(args):
     ms_per_step = ms / args.steps
     value = world * n * args.steps / (ms / 1e3)
 
-    # correctness of the timed output is the job of tests/ (the same batch, both
-    # schemes, against the oracle); here it is only read back to be sure it is finite.
+    # the timed output against the oracle's values of this batch (outside the
+    # timed region)
     out = d_out.cpu().numpy()
     finite = bool(np.isfinite(out).all())
+    check = golden_check(out, bits)
 
     # e2e through the host C-ABI call with pinned buffers
     pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
@@ -438,11 +472,12 @@ def run_mine(args):
         q1.record(stream)
         stream.synchronize()
         mso = q0.elapsed_time(q1) / args.other_steps
+        check_o = golden_check(d_out.cpu().numpy(), bits)
         sim.amplitudes_device(d_bits, d_out, stream=stream, flags=B.PEPS_FLAG_TIMING, **kwo)
         stream.synchronize()
         sto = sim.stats()
         schemes[other] = {"value": world * n / (mso / 1e3), "ms_per_step": mso,
-                          "steps": args.other_steps,
+                          "steps": args.other_steps, "check": check_o,
                           "flops_per_step": sim.plan_info(n, **kwo)["flops_call"],
                           "roofline": roofline_of(sto["contract_tc_flops"], sto["contract_tc_ms"],
                                                   sto["launches_contract_tc"],
@@ -464,12 +499,13 @@ def run_mine(args):
         e1.record(stream)
         stream.synchronize()
         ms32 = e0.elapsed_time(e1) / args.fp32_steps
+        check32 = golden_check(d_o64.cpu().numpy(), bits)
         fl32 = sim.plan_info(64, **kw32)["flops_call"]
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         alu_peak = sms * 128 * 2 * 2070e6 / 1e12   # FP32 lanes x 2 flops x max SM clock
         f32 = {"value": 64 / (ms32 / 1e3), "unit": UNIT, "bitstrings": 64,
                "ms_per_step": ms32, "scheme": scheme,
-               "note": "plain FP32 CUDA-core form, one group of 64",
+               "note": "plain FP32 CUDA-core form, one group of 64", "check": check32,
                "roofline": {"bound": "alu", "achieved": fl32 / (ms32 / 1e3) / 1e12,
                             "peak": alu_peak, "unit": "TFLOP/s",
                             "frac": fl32 / (ms32 / 1e3) / 1e12 / alu_peak,
@@ -477,21 +513,20 @@ def run_mine(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, desc, cores = oracle_sample(args.cpu_seconds, scheme)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        v, desc, cores, projected, _, _ = oracle_sample(args.cpu_seconds, scheme)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "projected": projected}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "fp16x3" if args.precision == "fp16x3" else args.precision,
-                "data": "synthetic",
-                "config": {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing "
-                                       "columns 0-2, prefix reuse", "seed": 4,
-                           "precision": args.precision, "lanes": args.lanes, "scheme": scheme,
-                           "autotune": tuned,
-                           "l2": "inputs larger than L2 (2 GiB running tensor per lane for "
-                                 "columns, 128 MiB quarter tensors x 4 per lane for quadrants)"},
+                "data": "synthetic", "config": dict(CONFIG),
+                "tuning": {"precision": args.precision, "lanes": args.lanes, "scheme": scheme,
+                           "prefix_reuse": "columns 0-2 per group of 64", "autotune": tuned},
+                "rel_err": check["rel_err"] if check else None,
+                "rel_err_ok": check["rel_err_ok"] if check else None, "check": check,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 16 * n},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,

@@ -286,17 +286,20 @@ PEPS_API int peps_amplitudes_device(peps_ctx *ctx, const uint64_t *d_bitstrings,
  * GPU that loads the library holds it until the process exits.  The caller
  * still passes the device bitstrings (n uint64) and the device output (n
  * peps_c128), and the stream.  Calls whose workspace (peps_workspace_bytes)
- * exceeds 64 MiB return PEPS_ENOMEM with a message; PEPS_FLAG_TIMING is
- * rejected (PEPS_EINVAL).  The function calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * exceeds 64 MiB return PEPS_ENOMEM with a message; PEPS_FLAG_TIMING (which
+ * creates CUDA events) and PEPS_FLAG_GRAPH (which creates a capture stream and
+ * instantiates a graph) are rejected with PEPS_EINVAL.  The function calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call, from any context, shares the one array, which keeps the
  * previous call's contents: each call clears what must start at zero and
- * rebuilds the site tensors and tables it needs, so results never depend on an
- * earlier call -- but calls that overlap on the GPU (other streams, other
- * threads) race on the array and must be serialised by the caller. */
+ * rebuilds the site tensors and tables it needs (the tables are copied in on
+ * `stream`, after the work already enqueued there), so results never depend
+ * on an earlier call.  Calls on one stream are therefore safe back to back;
+ * calls that overlap on the GPU (other streams, other threads) race on the
+ * array and must be serialised by the caller. */
 PEPS_API int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrings, int64_t n,
                                      peps_c128 *d_out, const peps_opts *opts, void *stream);
 

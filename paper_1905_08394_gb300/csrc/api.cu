@@ -2097,8 +2097,12 @@ static int check_status(peps_ctx *c, Plan &P, cudaStream_t s) {
   return PEPS_OK;
 }
 
+// Plan the call (or reuse the context's plan) and upload the plan's tables
+// into the workspace.  The upload is ordered on the call's stream `s`, after
+// whatever the caller enqueued there before (an earlier call's kernels may
+// still be reading the tables of the same workspace).
 static int prepare(peps_ctx *c, int64_t n, const peps_opts *opts, void *ws, size_t ws_bytes,
-                   const uint64_t *bits_dev, bool host_bits) {
+                   const uint64_t *bits_dev, bool host_bits, cudaStream_t s) {
   peps_opts o{};
   if (opts) o = *opts;
   Plan *P = c->plan.get();
@@ -2123,10 +2127,12 @@ static int prepare(peps_ctx *c, int64_t n, const peps_opts *opts, void *ws, size
   if (rc) return rc;
   {
     const size_t part_a = NP->off_ops_begin - NP->off_site_ptrs;
-    CUDA_TRY(cudaMemcpy((char *)ws + NP->off_site_ptrs, NP->blob.data(), part_a,
-                        cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy((char *)ws + NP->off_opdesc, NP->blob.data() + part_a,
-                        NP->blob.size() - part_a, cudaMemcpyHostToDevice));
+    // pageable source: the copy is staged before the call returns, so the
+    // blob may be replaced by a later plan at any time
+    CUDA_TRY(cudaMemcpyAsync((char *)ws + NP->off_site_ptrs, NP->blob.data(), part_a,
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((char *)ws + NP->off_opdesc, NP->blob.data() + part_a,
+                             NP->blob.size() - part_a, cudaMemcpyHostToDevice, s));
   }
   c->plan = std::move(NP);
   c->built_generation = 0;  // site buffers may have moved: re-evolve
@@ -2142,7 +2148,7 @@ extern "C" int peps_amplitudes_device(peps_ctx *c, const uint64_t *d_bits, int64
     return fail(PEPS_EINVAL, "peps_amplitudes_device: bad arguments");
   if (n == 0) return PEPS_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = prepare(c, n, opts, ws, ws_bytes, d_bits, false);
+  int rc = prepare(c, n, opts, ws, ws_bytes, d_bits, false, s);
   if (rc) return rc;
   Plan &P = *c->plan;
   rc = run_plan(c, P, d_bits, s);
@@ -2168,7 +2174,7 @@ extern "C" int peps_amplitudes(peps_ctx *c, const uint64_t *bits, int64_t n, pep
   cudaStream_t s = (cudaStream_t)stream;
   // The staging area sits at a fixed place in the workspace; the plan's items
   // point there.
-  int rc = prepare(c, n, opts, ws, ws_bytes, nullptr, true);
+  int rc = prepare(c, n, opts, ws, ws_bytes, nullptr, true, s);
   if (rc) return rc;
   Plan &P = *c->plan;
   uint64_t *d_bits = (uint64_t *)((char *)ws + P.off_bits);

@@ -186,6 +186,20 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster_addr) {
                    bar_cluster_addr)
                : "memory");
 }
+// Arrive with release semantics on an mbarrier given by its shared::cluster
+// address: the stores to the cluster's shared memory before it are visible to
+// a thread that sees the phase complete.
+__device__ __forceinline__ void mbar_arrive_cluster_release(uint32_t bar_cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                   bar_cluster_addr)
+               : "memory");
+}
+// Count `bytes` of transactions as complete on a local mbarrier (bytes that
+// will never arrive: the pair's other CTA issued no load for that stage).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
 // TMA loads of a CTA pair: the data lands in this CTA's shared memory and the
 // completion is counted on the mbarrier at `bar_cluster_addr` (the even CTA's).
 __device__ __forceinline__ void tma_load_4d_cg2(void *dst, const CUtensorMap *map,
@@ -357,8 +371,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   uint64_t *tfull = bars + 2 * S;
   uint64_t *tempty = bars + 2 * S + 2;
   uint64_t *done = bars + 2 * S + 4;
-  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 5);
+  uint64_t *pdone = bars + 2 * S + 5;  // CG = 2: the odd producer has finished issuing
+  uint32_t *tmem_slot = (uint32_t *)(bars + 2 * S + 6);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  volatile uint32_t *odd_issued = tmem_slot + 2;  // CG = 2: stages the odd CTA issued
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = CG > 1 ? cluster_ctarank() : 0u;
@@ -374,7 +390,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       mbar_init(&tempty[a], CG == 2 ? 2 * EPI_WARPS : 32 * EPI_WARPS);
     }
     mbar_init(done, 1);
+    mbar_init(pdone, 1);
     *abort_flag = 0;
+    *odd_issued = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -465,14 +483,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         }
         if (!ok) break;
       }
-      // Every issued stage must have landed before the pair may exit: the
-      // even CTA waits (bounded) on the full barriers of the last S stages,
-      // which count the loads of both CTAs.
+      // Every issued stage must have landed before the pair may exit.  The
+      // full barriers live in the even CTA and count the loads of both CTAs;
+      // after an abort the two producers may have stopped at different
+      // stages (at most S apart: a stage is issued only after the MMAs of
+      // the stage S before it, which needed both CTAs' loads).  So the odd
+      // producer reports how many stages it issued, and the even one settles
+      // the difference: for a stage only the odd CTA issued it arrives with
+      // the odd share's bytes, for a stage only it issued it counts the
+      // missing odd share as complete; then it waits (bounded) on the full
+      // barriers of the last S stages.  The odd CTA leaves only after the
+      // teardown's cluster barrier, which the even CTA reaches after this.
+      if (CG == 2 && !leader) {
+        uint32_t slot;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(slot)
+                     : "r"(smem_u32((const void *)odd_issued)));
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(slot), "r"(it) : "memory");
+        mbar_arrive_cluster_release(cluster_addr(pdone, 0));
+      }
       if (leader) {
         Watch w2{abort_flag, p.st, globaltimer() + 100000000ull, p.sh.q, 1};
         volatile int zero = 0;
         w2.abort = &zero;
-        for (uint32_t j = it > (uint32_t)S ? it - S : 0u; j < it; ++j)
+        uint32_t end = it;
+        if (CG == 2 && mbar_wait(pdone, 0u, w2)) {
+          asm volatile("fence.acq_rel.cluster;" ::: "memory");
+          const uint32_t io = *odd_issued;
+          const uint32_t half = stage_bytes;   // one CTA's share of a stage
+          for (uint32_t j = it; j < io; ++j) mbar_expect_tx(&full[j % S], half);
+          for (uint32_t j = io; j < it; ++j) mbar_complete_tx(&full[j % S], half);
+          if (io > end) end = io;
+        }
+        for (uint32_t j = end > (uint32_t)S ? end - S : 0u; j < end; ++j)
           if (!mbar_wait(&full[j % S], (j / S) & 1u, w2)) break;
       }
     }
@@ -1005,7 +1047,7 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
   const int units = pair_tiles * cg < sm_count ? pair_tiles * cg : sm_count;
   const int np = np_of(prm.sh.fmt);
   const size_t smem = (size_t)prm.stages * np * (BM + prm.BN / cg) * d->rowb + 1024 +
-                      (2 * prm.stages + 5) * 8 + 16;
+                      (2 * prm.stages + 6) * 8 + 16;
   switch (prm.sh.fmt) {
     case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cg, units, smem, s);
     case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cg, units, smem, s);

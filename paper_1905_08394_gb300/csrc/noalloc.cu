@@ -60,6 +60,12 @@ extern "C" int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrin
     return peps::internal_fail(PEPS_EINVAL,
                                "peps_amplitudes_noalloc: PEPS_FLAG_TIMING is not available here "
                                "(it creates CUDA events)");
+  // A CUDA graph would be captured and instantiated anew on every call (the
+  // plan is rebuilt each time), which allocates and gains nothing.
+  if (o.flags & PEPS_FLAG_GRAPH)
+    return peps::internal_fail(PEPS_EINVAL,
+                               "peps_amplitudes_noalloc: PEPS_FLAG_GRAPH is not available here "
+                               "(it creates a capture stream and instantiates a graph)");
   size_t need = 0;
   int rc = peps_workspace_bytes(ctx, n, &o, &need);
   if (rc) return rc;
@@ -74,7 +80,9 @@ extern "C" int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrin
   // The scratch is shared by every context and keeps the previous call's
   // contents: drop this context's cached tables and site tensors so that the
   // call rebuilds them (status words, records and accumulators are cleared by
-  // every call of the device path).
+  // every call of the device path).  The new tables are uploaded on `stream`,
+  // behind the kernels of earlier calls enqueued there, which may still read
+  // the old ones.
   peps::internal_forget_workspace(ctx);
   o.flags |= PEPS_FLAG_REBUILD;
   return peps_amplitudes_device(ctx, d_bitstrings, n, d_out, &o, ws, kNoAllocBytes, stream);

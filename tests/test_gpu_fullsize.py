@@ -81,6 +81,20 @@ def test_fp32_path_on_the_oracle_groups(golden, sim):
     assert err < TOL
 
 
+def test_fp32_path_in_the_bench_configuration(golden, sim):
+    # the comparator form exactly as bench.py times it: group 0 (64 bitstrings)
+    # by the square partition, prefix reuse, 16 lanes; it holds golden indices
+    # 0, 21, 42 and 63
+    circ, bits, idx, ref = golden
+    out = sim.amplitudes(bits[:64], precision="fp32", prefix_cols=3, prefix_group=64,
+                         max_lanes=16, scheme="quadrants")
+    pos = [k for k, i in enumerate(idx) if i < 64]
+    assert [idx[k] for k in pos] == [0, 21, 42, 63]
+    err = float(np.linalg.norm(out[[idx[k] for k in pos]] - ref[pos]) / np.linalg.norm(ref[pos]))
+    print(f"6x6 d32 fp32 square partition, group 0: normwise rel.err {err:.3e}")
+    assert err < TOL
+
+
 # ---------------------------------------------------------------------------
 # 7x7 lattice
 # ---------------------------------------------------------------------------

@@ -68,3 +68,39 @@ def test_marginals_with_general_gates(sim_factory):
     sim = sim_factory(circ)
     got = sim.amplitudes(x, precision="fp32", measured_mask=0b111100001111)
     assert relerr(got.real, ref) < TOL
+
+
+def test_orientation_closed_forms(sim_factory):
+    """G[(t0 t1), (s0 s1)] with the first-named qubit first, through the C ABI:
+    CNOT (control first), a cyclic permutation (not symmetric, so a transposed
+    G fails) given in both qubit orders, and a random U whose action on |00>
+    is its first column.  Expected amplitudes written out, every other one 0."""
+    from types import SimpleNamespace
+
+    from rqc_inputs import Gate
+
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    CYC = np.zeros((4, 4), dtype=complex)
+    for s, t in ((0, 1), (1, 3), (3, 2), (2, 0)):
+        CYC[t, s] = 1.0
+    z = np.random.default_rng(5).normal(size=(4, 4, 2)) @ np.array([1, 1j])
+    U, _ = np.linalg.qr(z)
+    q0, q1 = 1, 3
+    bit = lambda t0, t1: (t0 << q0) | (t1 << q1)
+    g1 = lambda q, M: Gate("1q", (q,), "U", M)
+    g2 = lambda a, b, M: Gate("2q", (a, b), "G", M)
+    cases = [([g1(q0, X), g2(q0, q1, CNOT)], {bit(1, 1): 1.0}),
+             ([g1(q0, X), g2(q1, q0, CNOT)], {bit(1, 0): 1.0}),
+             ([g2(q0, q1, CYC)], {bit(0, 1): 1.0}),
+             ([g2(q1, q0, CYC)], {bit(1, 0): 1.0}),
+             ([g2(q0, q1, U)], {bit(a, b): U[2 * a + b, 0] for a in (0, 1) for b in (0, 1)})]
+    allx = np.arange(16, dtype=np.uint64)
+    for k, (gates, amps) in enumerate(cases):
+        ref = np.zeros(16, dtype=complex)
+        for x, a in amps.items():
+            ref[x] = a
+        sim = sim_factory(SimpleNamespace(R=2, C=2, gates=gates))
+        for prec in ("fp32", "fp16x3"):
+            got = sim.amplitudes(allx, precision=prec)
+            assert np.abs(got - ref).max() < 1e-6, (k, prec)

@@ -3,12 +3,13 @@
 Metric (the paper defines none): normwise relative error over the checked
 set, ||a_gpu - a_ref||_2 / ||a_ref||_2.  Tolerances:
   * FP32 and FP16X3 (the FP32-equivalent forms): 1e-5;
-  * the other forms: a bound from the arithmetic, 8 * u * sqrt(#site
-    absorptions), u the unit roundoff of the operand representation
-    (2^-11 for TF32 and FP16 inputs, 2^-8 for BF16, 2^-16 for the BF16 hi/lo
-    pair).  Independent per-step rounding errors add in quadrature over the
-    sweep; the factor 8 covers the input rounding of both operands and the
-    spread between amplitude sets.
+  * the other forms: about twice the largest error measured on GB300 at 6x6
+    (1+24+1) (TF32 1.2e-3, FP16 1.3e-3, BF16 8.4e-3, BF16X3 1.4e-5), so that
+    a tenfold regression of any form fails.  The single-pass forms miss the
+    1e-3 that the workload asks of them by their arithmetic: 11 (TF32, FP16)
+    or 8 (BF16) significand bits per operand over 36 absorptions give this
+    error already when the operands are rounded and the sums are exact (an
+    emulation gives 1.2e-3 and 4.9e-3).
 """
 import math
 
@@ -25,13 +26,16 @@ pytestmark = pytest.mark.gpu
 SPLIT_TOL = 1e-5
 
 
-UNIT_ROUNDOFF = {"bf16": 2.0 ** -8, "tf32": 2.0 ** -11, "fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16}
+MEASURED_TOL = {"tf32": 2.5e-3, "fp16": 2.5e-3, "bf16": 1.7e-2, "bf16x3": 3e-5}
 
 
 def tol_for(prec, n_steps):
+    """Tolerance of a form (n_steps: site absorptions per amplitude; the bounds
+    were measured at 36 and hold for fewer)."""
     if prec in ("fp32", "fp16x3"):
         return SPLIT_TOL
-    return 8 * UNIT_ROUNDOFF[prec] * math.sqrt(n_steps)
+    assert n_steps <= 36
+    return MEASURED_TOL[prec]
 
 
 def relerr(a, ref):

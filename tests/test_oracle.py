@@ -393,6 +393,99 @@ def test_peps_2q_gates_equal_statevector(R, C, seed):
     assert np.abs(a - ref).max() < 1e-13
 
 
+# Orientation of a general gate G[(t0 t1), (s0 s1)] (qubit q0 first), pinned by
+# closed forms that a shared convention mistake (G read transposed, or the two
+# qubits swapped) cannot pass: every expected value below is written out by
+# hand, not computed by either oracle.
+CNOT = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+ISWAP = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]], dtype=complex)
+X = np.array([[0, 1], [1, 0]], dtype=complex)
+
+
+CYCLE = np.zeros((4, 4), dtype=complex)     # |00> -> |01> -> |11> -> |10> -> |00>
+for _s, _t in ((0, 1), (1, 3), (3, 2), (2, 0)):
+    CYCLE[_t, _s] = 1.0
+
+
+def _orientation_cases():
+    """(gate list on 2x2 (n = 4), {bitstring: amplitude}) with every other
+    amplitude of the final state zero."""
+    q0, q1 = 1, 3          # vertical neighbours on a 2x2 lattice (q = r*2 + c)
+    rng = np.random.default_rng(77)
+    U = two_qubit_gates(rng)[3]
+    Us = U.reshape(2, 2, 2, 2).transpose(1, 0, 3, 2).reshape(4, 4)   # qubits swapped
+    bit = lambda t0, t1: (t0 << q0) | (t1 << q1)
+    return [
+        # CNOT, control q0: |q0=1, q1=0> -> |q0=1, q1=1>
+        ([g1(q0, X), g2(q0, q1, CNOT)], {bit(1, 1): 1.0}),
+        # the same gate given with q1 first: q1 is the control and is 0
+        ([g1(q0, X), g2(q1, q0, CNOT)], {bit(1, 0): 1.0}),
+        # iSWAP |q0=0, q1=1> = i |q0=1, q1=0>
+        ([g1(q1, X), g2(q0, q1, ISWAP)], {bit(1, 0): 1j}),
+        # a cyclic permutation (not symmetric): |00> -> |q0=0, q1=1>, and
+        # from |q0=1, q1=0> back to |00>
+        ([g2(q0, q1, CYCLE)], {bit(0, 1): 1.0}),
+        ([g1(q0, X), g2(q0, q1, CYCLE)], {bit(0, 0): 1.0}),
+        # the same permutation given with q1 first: |00> -> |q0=1, q1=0>
+        ([g2(q1, q0, CYCLE)], {bit(1, 0): 1.0}),
+        # a random U on |00>: the amplitudes are U's first column, entry
+        # (2 t0 + t1) at |q0=t0, q1=t1>
+        ([g2(q0, q1, U)], {bit(t0, t1): U[2 * t0 + t1, 0] for t0 in (0, 1) for t1 in (0, 1)}),
+        # U then U^dagger returns the start state, also with the qubit order of
+        # the second gate reversed (its matrix permuted to match)
+        ([g1(0, X), g2(q0, q1, U), g2(q0, q1, U.conj().T)], {1: 1.0}),
+        ([g1(0, X), g2(q0, q1, U), g2(q1, q0, Us.conj().T)], {1: 1.0}),
+    ]
+
+
+def _expected(amps):
+    ref = np.zeros(16, dtype=complex)
+    for x, a in amps.items():
+        ref[x] = a
+    return ref
+
+
+def err_2q_orientation_statevector():
+    worst = 0.0
+    for gates, amps in _orientation_cases():
+        psi = sv.run(4, gates)
+        worst = max(worst, float(np.abs(psi - _expected(amps)).max()))
+    return worst
+
+
+def err_2q_orientation_peps():
+    worst = 0.0
+    allx = np.arange(16, dtype=np.uint64)
+    for gates, amps in _orientation_cases():
+        a = op.amplitudes(op.build(2, 2, gates), allx)
+        worst = max(worst, float(np.abs(a - _expected(amps)).max()))
+    return worst
+
+
+def test_2q_orientation_closed_forms():
+    assert err_2q_orientation_statevector() < 1e-14
+    assert err_2q_orientation_peps() < 1e-13
+
+
+def test_planted_transposed_2q_gate_is_caught(monkeypatch):
+    orig_sv = sv.apply_2q
+    monkeypatch.setattr(sv, "apply_2q",
+                        lambda psi, n, q0, q1, G: orig_sv(psi, n, q0, q1, np.asarray(G).T))
+    assert err_2q_orientation_statevector() > 1e-3
+    monkeypatch.undo()
+    orig_op = op.PEPS.apply_2q
+    monkeypatch.setattr(op.PEPS, "apply_2q",
+                        lambda self, q0, q1, G: orig_op(self, q0, q1, np.asarray(G).T))
+    assert err_2q_orientation_peps() > 1e-3
+
+
+def test_planted_swapped_2q_qubits_are_caught(monkeypatch):
+    orig_sv = sv.apply_2q
+    monkeypatch.setattr(sv, "apply_2q",
+                        lambda psi, n, q0, q1, G: orig_sv(psi, n, q1, q0, G))
+    assert err_2q_orientation_statevector() > 1e-3
+
+
 def test_svd_split_ranks():
     rng = np.random.default_rng(4)
     iswap, cnot, rank3, rnd = two_qubit_gates(rng)
