@@ -114,6 +114,13 @@ def parse():
     ap.add_argument("--other-steps", type=int, default=2,
                     help="timed calls of the scheme not chosen (reported under 'schemes'; "
                          "0 = skip)")
+    ap.add_argument("--hold-ties", dest="hold_ties", action="store_true", default=True,
+                    help="hold the CZ bits that each output bitstring fixes (default)")
+    ap.add_argument("--no-hold-ties", dest="hold_ties", action="store_false")
+    ap.add_argument("--tune-tiles", dest="tune_tiles", action="store_true", default=True,
+                    help="after the contraction order, autotune lanes, K bytes per stage "
+                         "and CTA pairing on this batch (default)")
+    ap.add_argument("--no-tune-tiles", dest="tune_tiles", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
@@ -352,7 +359,8 @@ def run_mine(args):
     sim = Simulator(circ.R, circ.C, device=local)
     sim.apply_circuit(circ)
     stream = torch.cuda.Stream(device=dev)
-    base_kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes)
+    base_kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
+                   hold_ties=args.hold_ties)
     d_bits = torch.from_numpy(bits.view(np.int64)).to(dev)
     d_out = torch.empty(n, dtype=torch.complex128, device=dev)
     peaks, src = load_peaks()
@@ -375,6 +383,22 @@ def run_mine(args):
     else:
         scheme = args.scheme
     kw = dict(base_kw, scheme=scheme)
+    # tile configuration for that order: lanes per launch, K bytes per stage,
+    # CTA pairs (2-SM MMA) or single CTAs
+    if args.tune_tiles:
+        log = []
+        cands = [c for c in autotune.candidates(lanes=(16, 32, 64), kchunk=(128, 64),
+                                                cluster=(2, 1), schemes=(scheme,))]
+        best = autotune.tune(sim, d_bits, d_out, kw, cands=cands, repeats=1, stream=stream,
+                             log=log.append)
+        if pg:   # rank 0's choice everywhere
+            t = torch.tensor([best["max_lanes"], best["tc_kchunk"], best["tc_cluster"]],
+                             device=dev)
+            torch.distributed.broadcast(t, 0, group=pg)
+            best = {"scheme": scheme, "max_lanes": int(t[0]), "tc_kchunk": int(t[1]),
+                    "tc_cluster": int(t[2])}
+        kw.update(best)
+        tuned = dict(tuned or {}, tile=best, tile_trials=log)
     flags = B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING
 
     def step(s):
@@ -462,7 +486,7 @@ def run_mine(args):
     # the other contraction order on the same batch, for comparison
     other = "quadrants" if scheme == "columns" else "columns"
     if args.other_steps > 0:
-        kwo = dict(base_kw, scheme=other)
+        kwo = dict(base_kw, scheme=other)   # untuned tiles
         sim.amplitudes_device(d_bits, d_out, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kwo)
         stream.synchronize()
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -486,8 +510,9 @@ def run_mine(args):
     # FP32 CUDA-core form on one group of 64, same contraction order
     f32 = None
     if args.fp32_steps > 0:
-        kw32 = dict(precision="fp32", prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
-                    scheme=scheme)
+        kw32 = dict(precision="fp32", prefix_cols=3, prefix_group=64,
+                    max_lanes=kw.get("max_lanes", args.lanes), scheme=scheme,
+                    hold_ties=args.hold_ties)
         d_b64 = d_bits[:64].contiguous()
         d_o64 = torch.empty(64, dtype=torch.complex128, device=dev)
         sim.amplitudes_device(d_b64, d_o64, stream=stream, flags=B.PEPS_FLAG_REBUILD, **kw32)
@@ -523,7 +548,9 @@ def run_mine(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "fp16x3" if args.precision == "fp16x3" else args.precision,
                 "data": "synthetic", "config": dict(CONFIG),
-                "tuning": {"precision": args.precision, "lanes": args.lanes, "scheme": scheme,
+                "tuning": {"precision": args.precision, "lanes": kw.get("max_lanes", args.lanes),
+                           "scheme": scheme, "hold_ties": args.hold_ties,
+                           "tc_kchunk": kw.get("tc_kchunk", 0), "tc_cluster": kw.get("tc_cluster", 0),
                            "prefix_reuse": "columns 0-2 per group of 64", "autotune": tuned},
                 "rel_err": check["rel_err"] if check else None,
                 "rel_err_ok": check["rel_err_ok"] if check else None, "check": check,

@@ -93,7 +93,9 @@ enum {
     PEPS_FLAG_GRAPH = 8,    /* capture the call's launch sequence (evolution
                                included) into a CUDA graph on the first call
                                and replay it on later calls with the same
-                               plan; ignored together with PEPS_FLAG_TIMING */
+                               plan; with PEPS_FLAG_TIMING the graph also
+                               records the events around its contraction
+                               launches, and each replay reports their times */
     PEPS_FLAG_MARGINALS = 16, /* return marginal probabilities P(x_S) =
                                <psi| Pi_S |psi> instead of amplitudes: S = the
                                set bits of opts.measured_mask, their values
@@ -102,12 +104,24 @@ enum {
                                (every site sum_sigma A^sigma (x) conj(A^sigma),
                                every bond squared); out[i].re = P, .im ~ 0.
                                Not with slicing or held CZ bits.          */
-    PEPS_FLAG_ESTIMATE = 32 /* planning only: peps_plan_info_get and
+    PEPS_FLAG_ESTIMATE = 32,/* planning only: peps_plan_info_get and
                                peps_workspace_bytes report the figures of a
                                plan whose running tensor exceeds the 2^36
                                entries an amplitude call accepts (a slice-set
                                search starts there); an amplitude call with
                                this flag returns PEPS_EINVAL.              */
+    PEPS_FLAG_HOLD_TIES = 64 /* hold every CZ Schmidt bit that the output
+                               bitstring (or the initial state) fixes, as
+                               peps_output_ties lists them: the bond index of
+                               that bit takes only its tied value in each
+                               bitstring's contraction, which halves the bond
+                               for the whole sweep.  Exact: every dropped term
+                               of the bond sum is zero.  Each site operand
+                               then has a variant per value of the output bits
+                               it depends on (its own and those of the
+                               neighbours whose projector bits touch its
+                               legs).  Not with slicing, held CZ bits
+                               (n_fixed) or marginals (PEPS_EINVAL).        */
 };
 
 /* Options of an amplitude call.  All-zero means: FP32_SIMT, no prefix reuse,
@@ -302,6 +316,21 @@ PEPS_API int peps_amplitudes_device(peps_ctx *ctx, const uint64_t *d_bitstrings,
  * array and must be serialised by the caller. */
 PEPS_API int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrings, int64_t n,
                                      peps_c128 *d_out, const peps_opts *opts, void *stream);
+
+/* CZ Schmidt bits fixed by the circuit's output (an extension of the paper's
+ * exact contraction: zero terms of a bond sum are skipped).  The CZ split
+ * P_0 (x) I + P_1 (x) Z puts the projector P_s on the lower-index qubit q.
+ * Between two events on q every CZ factor acting on q is diagonal; where the
+ * single-qubit gates between them multiply to a monomial matrix (diagonal or
+ * anti-diagonal), a basis state of q stays a basis state, so consecutive
+ * projector bits on q are tied, the first to the initial |0> and the last to
+ * the measured output bit x_q.  Lists every tied CZ: its ordinal cz[i] (0 =
+ * the first CZ applied), kind[i] = 1 for s = flip[i] (constant) or 2 for
+ * s = x_q XOR flip[i] (q = that CZ's lower-index qubit), for every output
+ * bitstring x.  Writes at most `cap` entries (the arrays may be NULL when
+ * cap = 0) and the total count to *n_out.  Host only. */
+PEPS_API int peps_output_ties(const peps_ctx *ctx, uint32_t *cz, uint8_t *kind, uint8_t *flip,
+                              int64_t cap, int64_t *n_out);
 
 /* Counters of the last amplitude call on this context. */
 PEPS_API int peps_get_stats(const peps_ctx *ctx, peps_stats *out);

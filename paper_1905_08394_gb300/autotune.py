@@ -24,7 +24,7 @@ def signature(sim, n: int, kw: dict) -> str:
                 dims.append(sim.bond_dim(r, c, r, c + 1))
             if r + 1 < sim.R:
                 dims.append(sim.bond_dim(r, c, r + 1, c))
-    keys = ("precision", "prefix_cols", "prefix_group", "sliced_cz", "scheme")
+    keys = ("precision", "prefix_cols", "prefix_group", "sliced_cz", "scheme", "hold_ties")
     rest = {k: (list(kw[k]) if k == "sliced_cz" else kw[k]) for k in keys if k in kw and kw[k] is not None}
     return json.dumps({"R": sim.R, "C": sim.C, "dims": dims, "n": n, **rest}, sort_keys=True)
 

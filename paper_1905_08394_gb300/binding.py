@@ -46,12 +46,13 @@ PEPS_FLAG_TIMING = 2
 PEPS_FLAG_NO_TC = 4
 PEPS_FLAG_GRAPH = 8
 PEPS_FLAG_ESTIMATE = 32
+PEPS_FLAG_HOLD_TIES = 64
 
 EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_apply_2q",
             "peps_bond_dim",
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",
             "peps_get_stats", "peps_cz_count", "peps_last_error", "peps_version",
-            "peps_plan_info_get", "peps_amplitudes_noalloc")
+            "peps_plan_info_get", "peps_amplitudes_noalloc", "peps_output_ties")
 
 
 class peps_c128(ct.Structure):
@@ -133,6 +134,7 @@ def load() -> ct.CDLL:
     lib.peps_cz_count.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.peps_plan_info_get.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                        ct.POINTER(peps_plan_info)]
+    lib.peps_output_ties.argtypes = [P, P, P, P, ct.c_int64, ct.POINTER(ct.c_int64)]
     lib.peps_last_error.restype = ct.c_char_p
     lib.peps_version.restype = ct.c_char_p
     for name in EXPORTED:
@@ -195,13 +197,14 @@ def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_gro
               max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0,
               fixed_cz=None, fixed_s=None, tc_kchunk: int = 0, tc_cluster: int = 0,
               fuse_rows: int = 0, scheme="columns", tc_ksplit: int = 0,
-              measured_mask=None):
+              measured_mask=None, hold_ties: bool = False):
     """peps_opts plus the arrays it points to (keep both alive).  With
     measured_mask (an int, bit q = qubit q measured) the call returns the
-    marginal probabilities of the measured bits (PEPS_FLAG_MARGINALS)."""
+    marginal probabilities of the measured bits (PEPS_FLAG_MARGINALS); with
+    hold_ties the CZ bits the output fixes are held (PEPS_FLAG_HOLD_TIES)."""
     o = peps_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    o.flags = flags
+    o.flags = flags | (PEPS_FLAG_HOLD_TIES if hold_ties else 0)
     o.prefix_cols = prefix_cols
     o.prefix_group = prefix_group
     o.max_lanes = max_lanes
@@ -273,6 +276,21 @@ def peps_plan_info_get(h, n: int, opts: peps_opts) -> dict:
     i = peps_plan_info()
     _check(load().peps_plan_info_get(h, n, ct.byref(opts), ct.byref(i)))
     return i.as_dict()
+
+
+def peps_output_ties(h) -> list:
+    """[(cz ordinal, kind, flip)]: kind 1 = the Schmidt bit is `flip`, kind 2 =
+    it is x_q XOR flip for every output bitstring x (q = the CZ's lower-index
+    qubit)."""
+    n = ct.c_int64()
+    _check(load().peps_output_ties(h, None, None, None, 0, ct.byref(n)))
+    k = n.value
+    cz = np.zeros(max(k, 1), dtype=np.uint32)
+    kind = np.zeros(max(k, 1), dtype=np.uint8)
+    flip = np.zeros(max(k, 1), dtype=np.uint8)
+    _check(load().peps_output_ties(h, cz.ctypes.data, kind.ctypes.data, flip.ctypes.data, k,
+                                   ct.byref(n)))
+    return [(int(cz[i]), int(kind[i]), int(flip[i])) for i in range(k)]
 
 
 def peps_last_error() -> str:

@@ -169,8 +169,12 @@ struct Plan {
   std::vector<unsigned char> blob;
   size_t off_ops_begin = 0;
 
-  // CUDA graph of the whole launch sequence (PEPS_FLAG_GRAPH)
+  // CUDA graph of the whole launch sequence (PEPS_FLAG_GRAPH); with timing
+  // events around its contraction launches (graph_timed)
   cudaGraphExec_t graph_exec = nullptr;
+  bool graph_timed = false;
+  size_t graph_n_timed = 0;
+  std::vector<char> graph_timed_tc;
 
   ~Plan() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -474,7 +478,123 @@ int locate_cz(const peps_ctx *c, std::vector<CzPos> &pos) {
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Schmidt bits that the output bitstring fixes.  A CZ split as
+// P_0 (x) I + P_1 (x) Z puts the projector P_s on its lower-index qubit q and
+// Z^s on the other.  Between two events on q (CZ factors of either kind, or
+// the measurement) every CZ factor acting on q is diagonal in its basis; if
+// each run of single-qubit gates in between is a monomial matrix (diagonal or
+// anti-diagonal), a basis state of q is carried to a basis state.  So the
+// bits of consecutive projectors on q are tied (equal or flipped), the first
+// one to the initial |0> and the last one to the measured bit x_q, wherever
+// the runs between them are monomial.  Every term of the bond sum that breaks
+// such a tie is exactly zero: the bit can be held at its tied value.
+// ---------------------------------------------------------------------------
+struct CzTie {
+  int kind;   // 0 = free, 1 = constant (bit = flip), 2 = output (bit = x_q ^ flip)
+  int q;      // the projector's qubit (the CZ's lower-index qubit)
+  int flip;
+};
+
+// 0 = diagonal, 1 = anti-diagonal, -1 = neither (relative tolerance 1e-12)
+int monomial_kind(const std::complex<double> M[4]) {
+  double s = 0;
+  for (int i = 0; i < 4; ++i) s = std::max(s, std::abs(M[i]));
+  const double tol = 1e-12 * s;
+  if (std::abs(M[1]) <= tol && std::abs(M[2]) <= tol) return 0;
+  if (std::abs(M[0]) <= tol && std::abs(M[3]) <= tol) return 1;
+  return -1;
+}
+
+void output_ties(const peps_ctx *c, std::vector<CzTie> &ties) {
+  typedef std::complex<double> cd;
+  const int n = c->n;
+  std::vector<std::vector<int>> runs(n);   // per qubit: monomial kind of each closed run
+  std::vector<std::array<cd, 4>> cur(n, std::array<cd, 4>{cd(1), cd(0), cd(0), cd(1)});
+  struct Ev { int k, ev; };
+  std::vector<std::vector<Ev>> proj(n);    // per qubit: its projector events in order
+  auto close = [&](int q, bool bad) {
+    runs[q].push_back(bad ? -1 : monomial_kind(cur[q].data()));
+    cur[q] = {cd(1), cd(0), cd(0), cd(1)};
+  };
+  int k = 0;
+  for (auto &g : c->gates) {
+    if (g.kind == 0) {
+      const int q = g.q0;
+      cd U[4], M[4];
+      for (int i = 0; i < 4; ++i) U[i] = cd(g.U[2 * i], g.U[2 * i + 1]);
+      for (int r = 0; r < 2; ++r)
+        for (int col = 0; col < 2; ++col)
+          M[2 * r + col] = U[2 * r] * cur[q][col] + U[2 * r + 1] * cur[q][2 + col];
+      for (int i = 0; i < 4; ++i) cur[q][i] = M[i];
+    } else if (g.kind == 1) {
+      proj[g.q0].push_back({k++, (int)runs[g.q0].size()});
+      close(g.q0, false);
+      close(g.q1, false);
+    } else {
+      close(g.q0, true);
+      close(g.q1, true);
+    }
+  }
+  for (int q = 0; q < n; ++q) close(q, false);   // the last run ends at the measurement
+  ties.assign(k, CzTie{0, -1, 0});
+  for (int q = 0; q < n; ++q) {
+    const auto &R = runs[q];
+    // parity of runs lo .. hi-1, or -1 if one of them is not monomial
+    auto span = [&](int lo, int hi) {
+      int par = 0;
+      for (int i = lo; i < hi; ++i) {
+        if (R[i] < 0) return -1;
+        par ^= R[i];
+      }
+      return par;
+    };
+    const auto &E = proj[q];
+    const int m = (int)E.size();
+    if (!m) continue;
+    // forward from the initial |0>
+    int val = 0, prev = -1;
+    for (int i = 0; i < m; ++i) {
+      const int f = span(prev + 1, E[i].ev + 1);
+      if (f < 0) break;
+      val ^= f;
+      ties[E[i].k] = CzTie{1, q, val};
+      prev = E[i].ev;
+    }
+    // backward from the measured bit x_q
+    int flip = span(E[m - 1].ev + 1, (int)R.size());
+    for (int i = m - 1; i >= 0 && flip >= 0; --i) {
+      if (ties[E[i].k].kind == 0) ties[E[i].k] = CzTie{2, q, flip};
+      if (i > 0) {
+        const int f = span(E[i - 1].ev + 1, E[i].ev + 1);
+        flip = f < 0 ? -1 : flip ^ f;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+extern "C" int peps_output_ties(const peps_ctx *c, uint32_t *cz, uint8_t *kind, uint8_t *flip,
+                                int64_t cap, int64_t *n_out) {
+  if (!c || !n_out) return fail(PEPS_EINVAL, "peps_output_ties: NULL argument");
+  if (cap < 0) return fail(PEPS_EINVAL, "peps_output_ties: negative capacity");
+  std::vector<CzTie> ties;
+  output_ties(c, ties);
+  int64_t k = 0;
+  for (size_t j = 0; j < ties.size(); ++j) {
+    if (ties[j].kind == 0) continue;
+    if (k < cap) {
+      if (!cz || !kind || !flip) return fail(PEPS_EINVAL, "peps_output_ties: NULL output array");
+      cz[k] = (uint32_t)j;
+      kind[k] = (uint8_t)ties[j].kind;
+      flip[k] = (uint8_t)ties[j].flip;
+    }
+    ++k;
+  }
+  *n_out = k;
+  return PEPS_OK;
+}
 
 static bool opts_equal(const peps_opts &a, const peps_opts &b) {
   return a.precision == b.precision && (a.flags & ~PEPS_FLAG_TIMING) == (b.flags & ~PEPS_FLAG_TIMING) &&
@@ -577,6 +697,58 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     m |= 1u << p.bit;
     if (o.fixed_s[j]) (p.horiz ? fixval_h[p.edge] : fixval_v[p.edge]) |= 1u << p.bit;
   }
+  // held bits (PEPS_FLAG_HOLD_TIES): per edge the held mask joins the fixed
+  // mask (the bond shrinks), and the held values are hv0 / hv1 for the
+  // output bit 0 / 1 of the edge's projector qubit hq (-1: no held bit on
+  // the edge depends on the output; then hv0 == hv1)
+  const bool hold = (o.flags & PEPS_FLAG_HOLD_TIES) != 0;
+  if (hold && (o.n_sliced > 0 || o.n_fixed > 0 || dl))
+    return fail(PEPS_EINVAL, "PEPS_FLAG_HOLD_TIES does not combine with slicing, held CZ bits "
+                "or marginals");
+  std::vector<uint32_t> hv0_h(c->ncz_h.size(), 0u), hv1_h(c->ncz_h.size(), 0u);
+  std::vector<uint32_t> hv0_v(c->ncz_v.size(), 0u), hv1_v(c->ncz_v.size(), 0u);
+  std::vector<int> hq_h(c->ncz_h.size(), -1), hq_v(c->ncz_v.size(), -1);
+  if (hold) {
+    std::vector<CzTie> ties;
+    output_ties(c, ties);
+    for (size_t k = 0; k < ties.size(); ++k) {
+      const CzTie &t = ties[k];
+      if (t.kind == 0) continue;
+      const CzPos &p = czpos[k];
+      if (p.horiz ? c->ngen_h[p.edge] : c->ngen_v[p.edge]) continue;  // bit not addressable
+      (p.horiz ? L.fix_h[p.edge] : L.fix_v[p.edge]) |= 1u << p.bit;
+      const uint32_t v0 = (uint32_t)t.flip, v1 = t.kind == 2 ? (uint32_t)(t.flip ^ 1) : v0;
+      (p.horiz ? hv0_h[p.edge] : hv0_v[p.edge]) |= v0 << p.bit;
+      (p.horiz ? hv1_h[p.edge] : hv1_v[p.edge]) |= v1 << p.bit;
+      if (t.kind == 2) (p.horiz ? hq_h[p.edge] : hq_v[p.edge]) = t.q;
+    }
+  }
+  // Qubits other than the block's own sites whose output bits select a
+  // block's operand: the projector qubits of held bits on the sites' legs.
+  auto set_variant_qubits = [&](StepShape &sh) -> int {
+    sh.nx = 0;
+    if (!hold || sh.nq < 1) return PEPS_OK;
+    int sites[2] = {sh.q, sh.q + sh.qs};
+    for (int j = 0; j < sh.nq; ++j) {
+      const int q = sites[j], r = q / C, col = q % C;
+      int cand[4] = {-1, -1, -1, -1};
+      if (col > 0) cand[0] = hq_h[edge_h(c, r, col - 1)];
+      if (col < C - 1) cand[1] = hq_h[edge_h(c, r, col)];
+      if (r > 0) cand[2] = hq_v[edge_v(c, r - 1, col)];
+      if (r < R - 1) cand[3] = hq_v[edge_v(c, r, col)];
+      for (int a = 0; a < 4; ++a) {
+        const int x = cand[a];
+        if (x < 0) continue;
+        bool have = false;
+        for (int i = 0; i < sh.nq; ++i) have |= sites[i] == x;
+        for (int i = 0; i < sh.nx; ++i) have |= sh.xq[i] == x;
+        if (have) continue;
+        if (sh.nx == 4) return fail(PEPS_EINVAL, "internal: too many operand variant bits");
+        sh.xq[sh.nx++] = x;
+      }
+    }
+    return PEPS_OK;
+  };
   P.slice_list.clear();
   if (o.n_sliced > 0) {
     if (o.slice_ids) {
@@ -728,11 +900,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       sh.fmt = fmt;
       sh.target = scale_target(fmt);
       sh.Mr = M;
+      if (int rc = set_variant_qubits(sh)) return rc;
       P.steps.push_back(sh);
       P.step_roles.push_back({0, 1, 2, 3});
       P.step_site.push_back(r0 * C + col);
       P.step_opbase.push_back(n_ops_total);
-      n_ops_total += 1 << k;
+      n_ops_total += step_variants(sh);
       cap = std::max(cap, std::max(M * K, M * N));
       flops += 8.0 * (double)M * K * N;
       bytes += (double)bpe * (double)(M * K + M * N);
@@ -885,11 +1058,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         // order the operand's N with v' slowest there
         sh.nvs = (last && Pd == 1 && k == 1 && dh % 8 == 0) ? 1 : 0;
         sh.Mr = Mr;
+        if (int rc = set_variant_qubits(sh)) return rc;
         P.steps.push_back(sh);
         P.step_roles.push_back(f[0].roles);   // one orientation: the same for both sites
         P.step_site.push_back(f[0].q);
         P.step_opbase.push_back(n_ops_total);
-        n_ops_total += 1 << k;
+        n_ops_total += step_variants(sh);
         cap = std::max(cap, std::max(sh.M * K, sh.M * (int64_t)sh.N));
         Q.span = std::max(Q.span, std::max(sh.M * K, sh.M * (int64_t)sh.N));
         flops += 8.0 * (double)sh.M * K * sh.N;
@@ -1244,6 +1418,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
 
   // operands (restricted dims): 2^nq variants per step
   const int n_ops = n_ops_total;
+  if (n_ops > 65535) return fail(PEPS_EUNSUPPORTED, "too many site operands (%d)", n_ops);
   P.n_ops = n_ops;
   P.ec_off.assign(n_ops, 0);
   P.bt_off[0].assign(n_ops, 0);
@@ -1256,14 +1431,14 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     const StepShape &sh = P.steps[s];
     if (sh.nq == 1) {
       P.max_kn = std::max<int>(P.max_kn, sh.K * sh.N);
-      n1 += 2;
+      n1 += step_variants(sh);
     } else if (sh.nq == 2) {
       P.max_kn2 = std::max<int>(P.max_kn2, sh.K * sh.N);
-      n2 += 4;
+      n2 += step_variants(sh);
     }  // nq == 0: a merge operand, built from a stored tensor during the call
     // a tensor-core merge builds its planes straight from the stored tensor
     const bool merge_tc = sh.nq == 0 && want_tc && tc_supports(sh, fmt);
-    for (int t = 0; t < (1 << sh.nq); ++t) {
+    for (int t = 0; t < step_variants(sh); ++t) {
       const int op = P.step_opbase[s] + t;
       P.ec_off[op] = 0;
       if (!merge_tc) {
@@ -1624,14 +1799,22 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     if (l.kind != 0 || !l.tc) continue;
     const int q = l.shape.q;
     const int ob = l.op_base;
-    const void *bp[4][2] = {};
-    for (int t = 0; t < (1 << l.shape.nq); ++t)
+    // the variants' planes are equally spaced (allocated one after another
+    // with the same padded size)
+    const int nv = step_variants(l.shape);
+    const void *bb[2];
+    for (int pl = 0; pl < 2; ++pl)
+      bb[pl] = P.bt_off[pl][ob] ? (const void *)(base + P.bt_off[pl][ob])
+                                : (const void *)(base + P.bt_off[0][ob]);
+    const int64_t vst = nv > 1 ? (int64_t)(P.bt_off[0][ob + 1] - P.bt_off[0][ob]) : 0;
+    for (int t = 1; t < nv; ++t)
       for (int pl = 0; pl < 2; ++pl)
-        bp[t][pl] = P.bt_off[pl][ob + t] ? (const void *)(base + P.bt_off[pl][ob + t])
-                                         : (const void *)(base + P.bt_off[0][ob + t]);
+        if (P.bt_off[pl][ob] &&
+            (int64_t)(P.bt_off[pl][ob + t] - P.bt_off[pl][ob]) != (int64_t)t * vst)
+          return fail(PEPS_EINVAL, "internal: operand variants not equally spaced at site %d", q);
     int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
-                        (int64_t)(BPL * P.gbuf_bytes), P.plane * 2, bp, o.tc_kchunk, o.tc_cluster,
-                        &l.tc_handle);
+                        (int64_t)(BPL * P.gbuf_bytes), P.plane * 2, bb, nv, vst, o.tc_kchunk,
+                        o.tc_cluster, &l.tc_handle);
     if (rc != 0)
       return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
   }
@@ -1639,7 +1822,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<OpDesc> ops(n_ops);
   for (int s = 0; s < P.n_steps; ++s) {
     const StepShape &sh = P.steps[s];
-    for (int t = 0; t < (1 << sh.nq); ++t) {
+    for (int t = 0; t < step_variants(sh); ++t) {
       const int op = P.step_opbase[s] + t;
       OpDesc d{};
       d.Ec = P.ec_off[op] ? (const float2 *)(base + P.ec_off[op]) : nullptr;
@@ -1664,7 +1847,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     // the projected tensor of site q for bit t, legs restricted to the slice
     // roles[ro] = physical leg (0..3 = l, r, u, d) that plays role ro of the
     // absorbing sweep (identity for the column sweep)
-    auto site_entry = [&](int q, int t, int op, const std::array<int, 4> &roles) {
+    // xv: output bits of the operand variant (bit qq = output bit of qubit
+    // qq; only the variant's qubits are set), which select the held values
+    auto site_entry = [&](int q, int t, int op, const std::array<int, 4> &roles, uint64_t xv) {
       const int r = q / C, col = q % C;
       OpBuildEntry e{};
       const int fb = P.final_buf[q];
@@ -1680,6 +1865,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           const int eidx = horiz ? edge_h(c, rr, cc) : edge_v(c, rr, cc);
           fm = horiz ? L.fix_h[eidx] : L.fix_v[eidx];
           fv = horiz ? val_h[eidx] : val_v[eidx];
+          if (hold) {
+            const int hq = horiz ? hq_h[eidx] : hq_v[eidx];
+            const bool one = hq >= 0 && ((xv >> hq) & 1ull);
+            fv |= one ? (horiz ? hv1_h[eidx] : hv1_v[eidx]) : (horiz ? hv0_h[eidx] : hv0_v[eidx]);
+          }
         }
         pd[a] = sd[4 * q + a];
         // nothing fixed on this leg: the restricted index is the index
@@ -1714,19 +1904,29 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     for (int s = 0; s < P.n_steps; ++s) {
       const StepShape &sh = P.steps[s];
       const int ob = P.step_opbase[s];
+      // output bits of variant v (the inverse of block_variant)
+      auto variant_bits = [&](int v) {
+        uint64_t xv = 0;
+        for (int j = 0; j < sh.nq; ++j)
+          if ((v >> j) & 1) xv |= 1ull << (sh.q + j * sh.qs);
+        for (int i = 0; i < sh.nx; ++i)
+          if ((v >> (sh.nq + i)) & 1) xv |= 1ull << sh.xq[i];
+        return xv;
+      };
       if (sh.nq == 1) {
-        for (int t = 0; t < 2; ++t) {
-          OpBuildEntry e = site_entry(sh.q, t, ob + t, P.step_roles[s]);
+        for (int v = 0; v < step_variants(sh); ++v) {
+          OpBuildEntry e = site_entry(sh.q, v & 1, ob + v, P.step_roles[s], variant_bits(v));
           e.nvs = sh.nvs;
           obe.push_back(e);
         }
       } else if (sh.nq == 2) {
         // the block's sites are q and q + qs (qs = C for the column sweep; a
         // quarter's orientation can make it -C or +-1), same roles for both
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < step_variants(sh); ++v) {
           OpBuild2Entry e2{};
-          e2.a = site_entry(sh.q, v & 1, ob + v, P.step_roles[s]);
-          e2.b = site_entry(sh.q + sh.qs, (v >> 1) & 1, ob + v, P.step_roles[s]);
+          const uint64_t xv = variant_bits(v);
+          e2.a = site_entry(sh.q, v & 1, ob + v, P.step_roles[s], xv);
+          e2.b = site_entry(sh.q + sh.qs, (v >> 1) & 1, ob + v, P.step_roles[s], xv);
           e2.op = ob + v;
           obe2.push_back(e2);
         }
@@ -2012,7 +2212,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
 
 static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s) {
   const bool timing = (P.opts.flags & PEPS_FLAG_TIMING) != 0;
-  const bool graph = (P.opts.flags & PEPS_FLAG_GRAPH) != 0 && !timing;
+  const bool graph = (P.opts.flags & PEPS_FLAG_GRAPH) != 0;
   peps_stats S{};
   S.n_steps = P.n_steps;
   S.n_lanes = P.lanes;
@@ -2025,15 +2225,31 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
 
   if (graph) {
     // the graph always contains the evolution, so a replay never depends on
-    // what an earlier call left in the site tensors
+    // what an earlier call left in the site tensors.  With TIMING the capture
+    // also records the events around every contraction launch (event-record
+    // nodes), so that a replay times its own launches; a graph captured
+    // without them is captured again when timing is asked for.
+    if (P.graph_exec && timing && !P.graph_timed) {
+      CUDA_TRY(cudaGraphExecDestroy(P.graph_exec));
+      P.graph_exec = nullptr;
+    }
     if (!P.graph_exec) {
       for (auto &l : P.launches)
         if (l.kind == 0 && l.tc) CUDA_TRY(tc_warm(l.tc_handle));
+      if (timing) {
+        size_t nl = 0;
+        for (auto &l : P.launches) nl += l.kind == 0;
+        int rc = ensure_events(c, 2 * nl * P.slice_list.size());
+        if (rc) return rc;
+      }
       if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
       cudaStream_t cs = c->cap_stream;
       CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       peps_stats S2{};
-      int rc = enqueue_sequence(c, P, d_bits_in, cs, true, false, S2, nullptr, nullptr);
+      P.graph_n_timed = 0;
+      P.graph_timed_tc.clear();
+      int rc = enqueue_sequence(c, P, d_bits_in, cs, true, timing, S2, &P.graph_n_timed,
+                                &P.graph_timed_tc);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (rc) {
@@ -2044,10 +2260,20 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
       e = cudaGraphInstantiate(&P.graph_exec, g, 0);
       cudaGraphDestroy(g);
       CUDA_TRY(e);
+      P.graph_timed = timing;
     }
     CUDA_TRY(cudaGraphLaunch(P.graph_exec, s));
     int rc = enqueue_sequence_stats_only(P, S);
     if (rc) return rc;
+    if (timing) {
+      CUDA_TRY(cudaStreamSynchronize(s));
+      for (size_t i = 0; i < P.graph_n_timed; ++i) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+        S.contract_ms += ms;
+        if (P.graph_timed_tc[i]) S.contract_tc_ms += ms;
+      }
+    }
     c->built_generation = c->generation;
     c->built_ws = P.ws;
     c->stats = S;

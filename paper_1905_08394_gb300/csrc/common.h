@@ -118,22 +118,29 @@ struct StepShape {
   int32_t csep;   // tensor cores, split forms: the hi*lo and lo*hi products go
                   // to an accumulator of their own (a third of the updates of
                   // the main one; their own error is 2^-11 smaller)
-  int32_t pad2_;
+  int32_t nx;     // held bond bits (PEPS_FLAG_HOLD_TIES): other qubits whose
+                  // output bits select the operand variant, xq[0 .. nx)
   int64_t Mr;     // M = (batch) x Mr: the slowest M legs form a batch (open
                   // legs of a quarter that are never contracted in its
                   // sweep); 0 = no batch (Mr = M).  Row m = b * Mr + m_r;
                   // the P rotation acts on m_r only, and the output is
                   //   vb = 0: b * (Mr N) + ((m_lo dh' + h') P + m_hi) dv' + v'
                   //   vb = 1: (b dv' + v') (Mr dh') + (m_lo dh' + h') P + m_hi
+  int32_t xq[4];
 };
 
 // Operand index of a lane for a block: bit j = output bit of the block's
-// j-th site (for one site: tau).
+// j-th site (for one site: tau), then bit nq + i = output bit of qubit xq[i]
+// (the held bond bits of the block's legs that depend on a neighbour).
 __host__ __device__ inline int block_variant(uint64_t bits, const StepShape &sh) {
   int v = 0;
   for (int j = 0; j < sh.nq; ++j) v |= (int)((bits >> (sh.q + j * sh.qs)) & 1ull) << j;
+  for (int i = 0; i < sh.nx; ++i) v |= (int)((bits >> sh.xq[i]) & 1ull) << (sh.nq + i);
   return v;
 }
+
+// Operand variants of a step.
+__host__ __device__ inline int step_variants(const StepShape &sh) { return 1 << (sh.nq + sh.nx); }
 
 // Evolution tables.  Site tensors are kept as float-float pairs: a hi plane
 // and a lo plane (value = hi + lo), the lo plane `lo_off` entries after the
@@ -300,9 +307,11 @@ bool tc_supports(const StepShape &sh, int fmt);
 bool tc_tuning_valid(int kchunk, int cluster);
 // Encode the launch's tensor maps (A over the lanes' input buffers, Bt for
 // tau = 0/1 and each plane); returns 0 and an opaque handle, or < 0.
+// The B operands: plane pl of variant t at b_base[pl] + t * b_var_stride
+// bytes (n_var variants, equally spaced).
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
-               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[4][2],
-               int kchunk, int cluster, void **out_handle);
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_base[2],
+               int n_var, int64_t b_var_stride, int kchunk, int cluster, void **out_handle);
 void tc_release(void *handle);
 // One-time set-up of the kernel a handle launches (attributes, occupancy);
 // done before a stream capture so that no such call happens inside it.

@@ -57,7 +57,7 @@ template <> struct FormTraits<FMT_TF32>   { static constexpr int NP = 1, ESZ = 4
 
 struct __align__(64) TcParams {
   CUtensorMap mapA;        // {k, m, plane, lane}; m_hi-major steps: {k, m_hi, m_lo, b, plane/lane}
-  CUtensorMap mapB[4][2];  // [block variant][plane] {k, n}
+  CUtensorMap mapB[2];     // [plane] {k, n, operand variant}
   StepShape sh;
   const StepItem *items;
   const OpDesc *ops;
@@ -234,6 +234,23 @@ __device__ __forceinline__ void tma_load_2d_cg2(void *dst, const CUtensorMap *ma
       "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar_cluster_addr)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d_cg2(void *dst, const CUtensorMap *map,
+                                                uint32_t bar_cluster_addr, int c0, int c1,
+                                                int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar_cluster_addr)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -463,8 +480,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
                             si.a_lane * p.lp_mul + pl);
               else
                 tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
-              tma_load_2d(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl], &full[s], k0,
-                          nt * BN);
+              tma_load_3d(st + NP * a_bytes + pl * b_bytes, &p.mapB[pl], &full[s], k0,
+                          nt * BN, tau);
             }
           } else {
             // the even CTA's full barrier counts both CTAs' bytes
@@ -476,8 +493,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
               else
                 tma_load_4d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0,
                                 mt * BM, pl, si.a_lane);
-              tma_load_2d_cg2(st + NP * a_bytes + pl * b_bytes, &p.mapB[tau][pl],
-                              full0 + (uint32_t)s * 8u, k0, nt * BN + (int)rank * BNL);
+              tma_load_3d_cg2(st + NP * a_bytes + pl * b_bytes, &p.mapB[pl],
+                              full0 + (uint32_t)s * 8u, k0, nt * BN + (int)rank * BNL, tau);
             }
           }
         }
@@ -790,8 +807,8 @@ struct TcLaunchData {
 };
 
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
-               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_ptr[4][2],
-               int kchunk, int cluster, void **out_handle) {
+               int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_base[2],
+               int n_var, int64_t b_var_stride, int kchunk, int cluster, void **out_handle) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
   const int esz = esz_of(fmt), np = np_of(fmt);
@@ -892,25 +909,27 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   // The 2-SM UMMA when the 128-row tiles pair up and each CTA's half of the
   // Bt tile is a whole number of 8-row swizzle groups.
   d->cg = ((BN / 2) % 8 == 0 && tiles_m % 2 == 0 && cluster != 1) ? 2 : 1;
-  const int nvar = 1 << sh.nq;
-  if (nvar > 4) {
+  // B: one map per plane over every operand variant {k, n, variant}; the
+  // variants are equally spaced (a single variant gets the packed stride)
+  const int64_t bpacked = (int64_t)Kr * esz * Nr;
+  const int64_t vstride = n_var > 1 ? b_var_stride : bpacked;
+  if (n_var < 1 || n_var > 64 || vstride < bpacked || vstride % 16 != 0) {
     delete d;
     return -6;
   }
-  for (int t = 0; t < nvar; ++t)
-    for (int pl = 0; pl < np; ++pl) {
-      cuuint64_t dims[2] = {(cuuint64_t)Kr, (cuuint64_t)Nr};
-      cuuint64_t strides[1] = {(cuuint64_t)Kr * esz};
-      cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)(BN / d->cg)};
-      cuuint32_t es[2] = {1, 1};
-      CUresult r = enc(&d->prm.mapB[t][pl], dt, 2, const_cast<void *>(b_ptr[t][pl]), dims,
-                       strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS) {
-        delete d;
-        return -4;
-      }
+  for (int pl = 0; pl < np; ++pl) {
+    cuuint64_t dims[3] = {(cuuint64_t)Kr, (cuuint64_t)Nr, (cuuint64_t)n_var};
+    cuuint64_t strides[2] = {(cuuint64_t)Kr * esz, (cuuint64_t)vstride};
+    cuuint32_t box[3] = {(cuuint32_t)(rowb / esz), (cuuint32_t)(BN / d->cg), 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(&d->prm.mapB[pl], dt, 3, const_cast<void *>(b_base[pl]), dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      delete d;
+      return -4;
     }
+  }
   d->prm.sh = sh;
   d->prm.BN = BN;
   d->prm.tiles_m = (int)((sh.M + BM - 1) / BM);
