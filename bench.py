@@ -121,6 +121,10 @@ def parse():
                     help="after the contraction order, autotune lanes, K bytes per stage "
                          "and CTA pairing on this batch (default)")
     ap.add_argument("--no-tune-tiles", dest="tune_tiles", action="store_false")
+    ap.add_argument("--slices7", dest="slices7", action="store_true", default=True,
+                    help="also time the 7x7 (1+40+1) whole amplitude (180 GB slice set) and "
+                         "add it to the line as slices_7x7 (default; about 75 s)")
+    ap.add_argument("--no-slices7", dest="slices7", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
@@ -399,7 +403,9 @@ def run_mine(args):
                     "tc_cluster": int(t[2])}
         kw.update(best)
         tuned = dict(tuned or {}, tile=best, tile_trials=log)
-    flags = B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING
+    # every step replays the call's CUDA graph (circuit evolution included),
+    # which also records the events around each contraction launch
+    flags = B.PEPS_FLAG_GRAPH | B.PEPS_FLAG_TIMING
 
     def step(s):
         sim.amplitudes_device(d_bits, d_out, stream=s, flags=flags, **kw)
@@ -447,7 +453,7 @@ def run_mine(args):
     # e2e through the host C-ABI call with pinned buffers
     pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory()
     e2e_steps = max(1, min(args.steps, 2))
-    opts, keep = B.make_opts(flags=B.PEPS_FLAG_REBUILD, **kw)
+    opts, keep = B.make_opts(flags=B.PEPS_FLAG_GRAPH, **kw)
     ws, nbytes = sim.workspace(n, opts)
     out_host = torch.empty(n, dtype=torch.complex128).pin_memory()
     lib = B.load()
@@ -536,6 +542,15 @@ def run_mine(args):
                             "frac": fl32 / (ms32 / 1e3) / 1e12 / alu_peak,
                             "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz"}}
 
+    # the paper's large run, after this workload's memory is released
+    s7 = None
+    if args.slices7 and rank == 0:
+        sim.close()
+        del d_bits, d_out
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        s7 = slices_7x7(args, check=False, warm=False)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, desc, cores, projected, _, _ = oracle_sample(args.cpu_seconds, scheme)
@@ -557,7 +572,8 @@ def run_mine(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                         "d2h_bytes_per_step": 16 * n},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "fp32_path": f32, "schemes": schemes, "clocks": clk, "finite": finite}
+                "fp32_path": f32, "schemes": schemes, "clocks": clk, "finite": finite,
+                "slices_7x7": s7}
         print(json.dumps(line), flush=True)
     sim.close()
     if pg:
@@ -568,7 +584,8 @@ def run_mine(args):
 def run_profile_case(args):
     """One amplitude (bitstring 0) of the workload through one lane, by the
     given contraction scheme (auto = the square partition, which the
-    autotuner picks on this workload)."""
+    autotuner picks on this workload), with the tied bits held as in the
+    bench (--no-hold-ties: without)."""
     import numpy as np
 
     from paper_1905_08394_gb300 import Simulator
@@ -578,24 +595,27 @@ def run_profile_case(args):
     sim = Simulator(circ.R, circ.C)
     sim.apply_circuit(circ)
     scheme = "quadrants" if args.scheme == "auto" else args.scheme
-    out = sim.amplitudes(bits[:1], precision=args.precision, max_lanes=1, scheme=scheme)
+    out = sim.amplitudes(bits[:1], precision=args.precision, max_lanes=1, scheme=scheme,
+                         hold_ties=args.hold_ties)
     st = sim.stats()
-    print(json.dumps({"case": "profile", "scheme": scheme, "amplitude": [out[0].real, out[0].imag],
+    print(json.dumps({"case": "profile", "scheme": scheme, "hold_ties": args.hold_ties,
+                      "amplitude": [out[0].real, out[0].imag],
                       "launches": st["launches_total"], "tc_launches": st["launches_contract_tc"],
                       "finite": bool(np.isfinite(out).all())}))
     sim.close()
 
 
-def run_slices_case(args):
+def slices_7x7(args, check: bool = True, check_full: bool = False, warm: bool = True):
     """7x7 (1+40+1), one bitstring x, on the odd-side square partition (Fig.
     S2(c)): the whole amplitude.  The slice set is the square-partition
     chooser's under a 180 GB workspace, given x: the CZs whose bit x fixes
     are cut first (they add no slices), and only the slices that can be
     nonzero run (slicing.consistent_slice_ids), lower-half reuse included.
-    Timed in one call, the evolution included.  The same amplitude from a
-    second slice set (another budget and seed) is the cross-check; with
-    --check-full also from the slice set chosen without x (every slice of it
-    that can be nonzero, ~10 min)."""
+    Timed in one call, the evolution included, with clocks sampled meanwhile.
+    With `check`, the same amplitude from a second slice set (another budget
+    and seed) is the cross-check; with `check_full` also from the slice set
+    chosen without x (every slice of it that can be nonzero, ~10 min).
+    Returns the record (a dict)."""
     import numpy as np
     import torch
 
@@ -616,21 +636,22 @@ def run_slices_case(args):
     d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
     base = dict(precision=args.precision, scheme="quadrants")
     kw = dict(base, sliced_cz=ss.sliced_cz, slice_ids=ids)
+    ws_opts, ws_keep = B.make_opts(**kw)
+    ws_bytes = B.peps_workspace_bytes(sim.h, 1, ws_opts)
     # warm-up: one run of slices that share the lower half (evolution, kernels)
     group = [i for i in ids if (i & lmask) == (ids[0] & lmask)]
     t0 = time.time()
-    sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **dict(kw, slice_ids=group))
-    torch.cuda.synchronize()
+    if warm:
+        sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_TIMING, **dict(kw, slice_ids=group))
+        torch.cuda.synchronize()
     if args.group_only:
         st = sim.stats()
-        print(json.dumps({"case": "slices", "workload": "7x7 (1+40+1), one run of slices that "
-                          "share the lower half", "slices": len(group),
-                          "wall_seconds": time.time() - t0,
-                          "contract_seconds": st["contract_ms"] / 1e3,
-                          "flops": st["contract_flops"], "launches": st["launches_total"]}),
-              flush=True)
+        rec = {"case": "slices", "workload": "7x7 (1+40+1), one run of slices that share the "
+               "lower half", "slices": len(group), "wall_seconds": time.time() - t0,
+               "contract_seconds": st["contract_ms"] / 1e3, "flops": st["contract_flops"],
+               "launches": st["launches_total"]}
         sim.close()
-        return
+        return rec
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -642,47 +663,54 @@ def run_slices_case(args):
     t_call = e0.elapsed_time(e1) / 1e3
     st = sim.stats()
     amp = complex(out.cpu().numpy()[0])
-    ws_opts, ws_keep = B.make_opts(**kw)
-    ws_gib = B.peps_workspace_bytes(sim.h, 1, ws_opts) / 2 ** 30
-    # a second decomposition of the same amplitude
-    s2 = slicing.choose_quadrants(sim.h, circ, 120 * 2 ** 30, precision=args.precision, seed=7, x=x)
-    ids2 = slicing.consistent_slice_ids(circ, s2.sliced_cz, x)
-    t1 = time.time()
-    amp2 = complex(sim.amplitudes(bits, sliced_cz=s2.sliced_cz, slice_ids=ids2, **base)[0])
-    t2 = time.time() - t1
-    check = {"sliced_cz": len(s2.sliced_cz), "slices": len(ids2), "flops": s2.flops_total,
-             "amplitude": [amp2.real, amp2.imag], "wall_seconds": t2,
-             "rel_diff": abs(amp2 - amp) / abs(amp) if amp != 0 else None}
-    if args.check_full:
+    n = circ.R * circ.C
+    rec = {"workload": "7x7 (1+40+1), 1 bitstring, the whole amplitude (the paper's Table I run)",
+           "scheme": "quadrants (odd side)", "precision": args.precision,
+           "sliced_cz": len(ss.sliced_cz), "slices_run": len(ids),
+           "lower_groups": len({i & lmask for i in ids}),
+           "max_entries": ss.max_entries, "workspace_bytes": ws_bytes,
+           "workspace_within_180GB": bool(ws_bytes <= 180 * 10 ** 9),
+           "flops_total": ss.flops_total, "planned_flops_call": st["contract_flops"],
+           "chooser_seconds": choose_s, "seconds": t_call,
+           "seconds_per_slice": t_call / max(1, len(ids)),
+           "contract_seconds": st["contract_ms"] / 1e3, "launches": st["launches_total"],
+           "useful_tflops": st["contract_flops"] / t_call / 1e12,
+           "amplitude": [amp.real, amp.imag], "n_abs2": (2 ** n) * abs(amp) ** 2,
+           "clocks": clk,
+           "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
+                    "(odd-square partition, 92.51 TB)"}
+    if check:
+        # a second decomposition of the same amplitude
+        s2 = slicing.choose_quadrants(sim.h, circ, 120 * 2 ** 30, precision=args.precision, seed=7,
+                                      x=x)
+        ids2 = slicing.consistent_slice_ids(circ, s2.sliced_cz, x)
+        t1 = time.time()
+        amp2 = complex(sim.amplitudes(bits, sliced_cz=s2.sliced_cz, slice_ids=ids2, **base)[0])
+        rec["check"] = {"sliced_cz": len(s2.sliced_cz), "slices": len(ids2),
+                        "flops": s2.flops_total, "amplitude": [amp2.real, amp2.imag],
+                        "wall_seconds": time.time() - t1,
+                        "rel_diff": abs(amp2 - amp) / abs(amp) if amp != 0 else None}
+    if check_full:
         s3 = slicing.choose_quadrants(sim.h, circ, 180 * 10 ** 9, precision=args.precision, seed=5)
         ids3 = slicing.consistent_slice_ids(circ, s3.sliced_cz, x)
         t1 = time.time()
         amp3 = complex(sim.amplitudes(bits, sliced_cz=s3.sliced_cz, slice_ids=ids3, **base)[0])
-        check["without_x"] = {"sliced_cz": len(s3.sliced_cz), "slices": len(ids3),
-                              "amplitude": [amp3.real, amp3.imag],
-                              "wall_seconds": time.time() - t1,
-                              "rel_diff": abs(amp3 - amp) / abs(amp) if amp != 0 else None}
+        rec.setdefault("check", {})["without_x"] = {
+            "sliced_cz": len(s3.sliced_cz), "slices": len(ids3),
+            "amplitude": [amp3.real, amp3.imag], "wall_seconds": time.time() - t1,
+            "rel_diff": abs(amp3 - amp) / abs(amp) if amp != 0 else None}
     # the column sweep's slice set, for comparison (planner figures only)
     cs = slicing.choose(circ, 2 ** 33, seed=5)
-    col = {"sliced_cz": len(cs.sliced_cz), "max_entries": cs.max_entries,
-           "flops_per_slice": 8 * sum(cs.step_cmacs),
-           "flops_total": 8 * sum(cs.step_cmacs) * 2.0 ** len(cs.sliced_cz)}
-    n = circ.R * circ.C
-    line = {"case": "slices", "workload": "7x7 (1+40+1), 1 bitstring, the whole amplitude",
-            "scheme": "quadrants (odd side)", "precision": args.precision,
-            "sliced_cz": len(ss.sliced_cz), "slices_run": len(ids),
-            "lower_groups": len({i & lmask for i in ids}),
-            "max_entries": ss.max_entries, "flops_total": ss.flops_total,
-            "planned_flops_call": st["contract_flops"], "chooser_seconds": choose_s,
-            "seconds": t_call, "contract_seconds": st["contract_ms"] / 1e3,
-            "launches": st["launches_total"],
-            "useful_tflops": st["contract_flops"] / t_call / 1e12,
-            "amplitude": [amp.real, amp.imag], "n_abs2": (2 ** n) * abs(amp) ** 2,
-            "check": check, "workspace_gib": ws_gib, "columns": col, "clocks": clk,
-            "paper": "Tianhe-2, 4096 fat nodes, FP64: 31 min for one amplitude "
-                     "(odd-square partition, 92.51 TB)"}
-    print(json.dumps(line), flush=True)
+    rec["columns"] = {"sliced_cz": len(cs.sliced_cz), "max_entries": cs.max_entries,
+                      "flops_per_slice": 8 * sum(cs.step_cmacs),
+                      "flops_total": 8 * sum(cs.step_cmacs) * 2.0 ** len(cs.sliced_cz)}
     sim.close()
+    return rec
+
+
+def run_slices_case(args):
+    rec = slices_7x7(args, check=True, check_full=args.check_full)
+    print(json.dumps(dict({"case": "slices"}, **rec)), flush=True)
 
 
 def _time_calls(fn, reps):
@@ -753,7 +781,10 @@ def run_precision_case(args):
 
 def run_small_case(args):
     """4x4 (1+8+1) with 64 bitstrings and 5x5 (1+16+1) with 1024: launch-latency
-    bound; eager launch sequence vs the same sequence replayed as a CUDA graph."""
+    bound.  The whole-sweep path (the evolution as one launch with a block per
+    site, every bitstring's column sweep in one persistent launch with the
+    running tensor in shared memory) against the step-by-step launches
+    (STEPWISE), each eager and replayed as a CUDA graph."""
     import numpy as np
     import torch
 
@@ -769,11 +800,19 @@ def run_small_case(args):
         d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
         d_out = torch.empty(len(bits), dtype=torch.complex128, device="cuda")
         res = {"workload": name, "precision": prec, "bitstrings": len(bits)}
-        for mode, flags in (("eager", B.PEPS_FLAG_REBUILD), ("graph", B.PEPS_FLAG_GRAPH)):
+        ref = None
+        for mode, flags in (("eager", B.PEPS_FLAG_REBUILD), ("graph", B.PEPS_FLAG_GRAPH),
+                            ("stepwise_eager", B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_STEPWISE),
+                            ("stepwise_graph", B.PEPS_FLAG_GRAPH | B.PEPS_FLAG_STEPWISE)):
             kw = dict(precision=prec, max_lanes=64, flags=flags)
-            sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, **kw), 20)
+            sec = _time_calls(lambda: sim.amplitudes_device(d_bits, d_out, **kw), 50)
+            amps = d_out.cpu().numpy()
+            if ref is None:
+                ref = amps
             res[mode] = {"amplitudes_per_s": len(bits) / sec, "us_per_call": sec * 1e6,
-                         "launches_per_call": sim.stats()["launches_total"]}
+                         "launches_per_call": sim.stats()["launches_total"],
+                         "rel_diff_vs_eager": float(np.linalg.norm(amps - ref) /
+                                                    np.linalg.norm(ref))}
         out.append(res)
         sim.close()
     print(json.dumps({"case": "small", "results": out}), flush=True)

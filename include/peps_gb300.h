@@ -110,6 +110,14 @@ enum {
                                entries an amplitude call accepts (a slice-set
                                search starts there); an amplitude call with
                                this flag returns PEPS_EINVAL.              */
+    PEPS_FLAG_STEPWISE = 128,/* one launch per absorption step and per gate
+                               batch even where a small lattice's whole
+                               column sweep fits one block's shared memory
+                               (where it does, and the form is FP32 or a
+                               split form, the sweeps of all bitstrings run
+                               as one persistent launch in FP32, and the
+                               evolution of small site tensors as one launch
+                               with a block per site)                       */
     PEPS_FLAG_HOLD_TIES = 64 /* hold every CZ Schmidt bit that the output
                                bitstring (or the initial state) fixes, as
                                peps_output_ties lists them: the bond index of
@@ -209,8 +217,14 @@ typedef struct {
     int64_t n_lanes;             /* lanes used                                */
 } peps_stats;
 
-/* Create an empty circuit on an R x C lattice (state |0...0>, every bond of
- * dimension 1).  Host-only; no GPU work.  R, C >= 1, R*C <= 64. */
+/* Create an empty circuit on an R x C lattice: the state |0...0> as a PEPS of
+ * rank-5 site tensors A_q^sigma[l, r, u, d] with every auxiliary leg of
+ * dimension 1, A^0 = 1 and A^1 = 0 (paper, main text: the PEPS equation for
+ * the state as a product of site tensors summed over shared legs).  Host-only:
+ * no GPU work, no device memory; the workspace and the stream are arguments
+ * of the calls that run on the GPU.  R, C >= 1, R*C <= 64; *out receives the
+ * context (owned by the caller until peps_destroy).  PEPS_EINVAL on a bad
+ * size or a NULL out. */
 PEPS_API int peps_create(int R, int C, peps_ctx **out);
 
 /* Destroy a context.  Does not touch caller memory. */
@@ -275,10 +289,18 @@ PEPS_API int peps_plan_info_get(const peps_ctx *ctx, int64_t n_bitstrings, const
 PEPS_API int peps_workspace_bytes(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
                          size_t *bytes);
 
-/* Amplitudes <x_i| C |0...0> for host bitstrings[0..n) into host out[0..n).
+/* Amplitudes <x_i| C |0...0> for host bitstrings[0..n) into host out[0..n):
+ * each is the network of the evolved PEPS with every site projected on its
+ * output bit, E_q = A_q^{x_q}, contracted exactly (paper, main text: the
+ * "overlap" equation; supplementary: the exact contraction of the overlap,
+ * by the column sweep or the square partition as opts.scheme says).
  * Copies the bitstrings to the device on `stream`, runs the device path,
  * copies the results back and synchronises the stream before returning.
- * With slicing, out[i] is the FP64 sum over the selected slices. */
+ * d_workspace: caller-owned device memory of ws_bytes >= peps_workspace_bytes
+ * (PEPS_ENOMEM otherwise); it must stay allocated until the call returns and
+ * no other call may use it concurrently.  `stream` is a cudaStream_t.
+ * With slicing, out[i] is the FP64 sum over the selected slices.  On any
+ * error `out` is untouched. */
 PEPS_API int peps_amplitudes(peps_ctx *ctx, const uint64_t *bitstrings, int64_t n, peps_c128 *out,
                     const peps_opts *opts, void *d_workspace, size_t ws_bytes, void *stream);
 

@@ -18,6 +18,9 @@ Two independent computations of the same definition, a_x = <x| C |0...0>
   sweep), or the same sweep transposed (column sweep).  All FP64, no
   renormalisation, no truncation.
 
-Parity status: both are pinned by the CPU tests in `tests/test_oracle_*.py`
-(closed forms, brute force, invariants); nothing here is "parity unpinned".
+Parity status: both are pinned by the CPU tests in `tests/test_oracle.py`
+(closed forms, brute force, invariants, planted mistakes) and
+`tests/test_complexity.py` (the paper's memory figures); the tie rule that the
+held-bit contraction relies on is checked against O2/O3 in `tests/test_ties.py`
+and `tests/test_slicing.py`.  Nothing here is "parity unpinned".
 """

@@ -47,6 +47,7 @@ PEPS_FLAG_NO_TC = 4
 PEPS_FLAG_GRAPH = 8
 PEPS_FLAG_ESTIMATE = 32
 PEPS_FLAG_HOLD_TIES = 64
+PEPS_FLAG_STEPWISE = 128
 
 EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "peps_apply_2q",
             "peps_bond_dim",

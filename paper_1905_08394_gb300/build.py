@@ -19,7 +19,7 @@ PEAKS_LIB = PKG / "libpeps_peaks.so"
 PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "evolve.cu", "operands.cu", "contract_simt.cu", "contract_tc.cu",
-           "finalize.cu", "noalloc.cu"]
+           "contract_small.cu", "finalize.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -74,6 +74,7 @@ struct Launch {
   int64_t kn = 0;       // kind 2: K * N of that operand
   double flops, bytes;
   bool lower = false;   // odd side: a launch of the lower half (bl, br -> F_b)
+  bool small = false;   // kind 0: every step of every bitstring in one launch
 };
 
 struct Plan {
@@ -162,6 +163,16 @@ struct Plan {
   int max_kn = 0;
   std::vector<int64_t> slice_list;
   double flops_per_slice = 0, bytes_per_slice = 0;
+
+  // small lattices: the whole sweep of every bitstring in one launch
+  // (running tensors in shared memory), the evolution in one launch with a
+  // block per site
+  bool small = false;
+  int small_cap_g = 0, small_cap_e = 0;
+  size_t off_small_steps = 0, off_small_opbase = 0;
+  const uint64_t *small_bits = nullptr;
+  bool evo_sites = false;
+  size_t off_evo_refs = 0, off_evo_first = 0;
 
   // host copy of the tables (uploaded once): [off_site_ptrs, off_ops_begin)
   // then [off_opdesc, off_tables_end); the operand storage between them is
@@ -1272,6 +1283,23 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   int64_t gs = pc > 0 ? o.prefix_group : (quad ? 1 : std::max<int64_t>(n, 1));
   P.n_groups = ((pc > 0 || quad) && n > 0) ? (int)(n / gs) : 0;
   P.bufs_per_lane = quad ? 4 : 2;
+  // one launch for the sweeps of a small lattice: every running tensor and
+  // operand fits one block's shared memory (FP32 arithmetic: the FP32 form
+  // and the split forms, whose results it matches)
+  P.small = false;
+  if (!quad && pc == 0 && !(o.flags & PEPS_FLAG_STEPWISE) &&
+      (fmt == FMT_F32 || fmt == FMT_FP16X2 || fmt == FMT_BF16X2)) {
+    int64_t cg = 1, ce = 1;
+    for (auto &sh : P.steps) {
+      cg = std::max(cg, std::max(sh.M * sh.K, sh.M * (int64_t)sh.N));
+      ce = std::max(ce, (int64_t)sh.K * sh.N);
+    }
+    if ((2 * cg + ce) * (int64_t)sizeof(float2) <= (int64_t)kSmallSweepMaxSmem) {
+      P.small = true;
+      P.small_cap_g = (int)cg;
+      P.small_cap_e = (int)ce;
+    }
+  }
   int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
   lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, gs), 1));
   P.lanes = lanes;
@@ -1305,6 +1333,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<CzEntry> cz;
   std::vector<Gate2Entry> g2e;
   P.evo.clear();
+  std::vector<std::vector<EvoRef>> site_refs(NQ);
   {
     std::vector<int> cur(NQ, 0);
     std::vector<int> dims(4 * NQ, 1);
@@ -1344,6 +1373,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           e.U_lo[i] = make_float2((float)(g.U[2 * i] - (double)hr),
                                   (float)(g.U[2 * i + 1] - (double)hi_));
         }
+        site_refs[q].push_back(EvoRef{0, (int32_t)g1.size()});
         g1.push_back(e);
         eb.n++;
         eb.max_work = std::max(eb.max_work, e.half);
@@ -1374,6 +1404,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           const int64_t out_n =
               2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
           cur[q] ^= 1;
+          site_refs[q].push_back(EvoRef{2, (int32_t)g2e.size()});
           g2e.push_back(e);
           eb.n++;
           eb.max_work = std::max(eb.max_work, out_n);
@@ -1398,6 +1429,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           const int64_t out_n =
               2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
           cur[q] ^= 1;
+          site_refs[q].push_back(EvoRef{1, (int32_t)cz.size()});
           cz.push_back(e);
           eb.n++;
           eb.max_work = std::max(eb.max_work, out_n);
@@ -1414,6 +1446,22 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
   P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
   P.off_g2 = off; off = align_up(off + std::max<size_t>(g2e.size(), 1) * sizeof(Gate2Entry));
+  // the whole evolution as one launch (a block per site) where every site
+  // tensor is small enough for one block
+  std::vector<EvoRef> evo_refs;
+  std::vector<int32_t> evo_first(NQ + 1, 0);
+  for (int q = 0; q < NQ; ++q) {
+    evo_first[q] = (int32_t)evo_refs.size();
+    evo_refs.insert(evo_refs.end(), site_refs[q].begin(), site_refs[q].end());
+  }
+  evo_first[NQ] = (int32_t)evo_refs.size();
+  {
+    int64_t big = 0;
+    for (int q = 0; q < NQ; ++q) big = std::max(big, P.site_elems[q]);
+    P.evo_sites = big <= 16384 && !(o.flags & PEPS_FLAG_STEPWISE);
+  }
+  P.off_evo_refs = off; off = align_up(off + std::max<size_t>(evo_refs.size(), 1) * sizeof(EvoRef));
+  P.off_evo_first = off; off = align_up(off + (size_t)(NQ + 1) * sizeof(int32_t));
   P.off_ops_begin = off;
 
   // operands (restricted dims): 2^nq variants per step
@@ -1727,6 +1775,17 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         P.launches.push_back(fl);
       }
     }
+  } else if (P.small) {
+    Launch ln{};
+    ln.kind = 0;
+    ln.small = true;
+    ln.shape = P.steps[0];
+    ln.tc = false;
+    ln.items_off = 0;
+    ln.n_items = 0;
+    ln.flops = P.flops_per_slice * (double)n;
+    ln.bytes = P.bytes_per_slice * (double)n;
+    P.launches.push_back(ln);
   } else {
     for (int64_t base = 0; base < n; base += P.lanes) {
       const int nl = (int)std::min<int64_t>(P.lanes, n - base);
@@ -1766,13 +1825,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_dots = off; off = align_up(off + std::max<size_t>(dots.size(), 1) * sizeof(DotEntry));
   P.off_partials = off;
   off = align_up(off + (quad ? (size_t)kDotBlocks * P.lanes * sizeof(double2) : 16));
+  P.off_small_steps = off; off = align_up(off + (size_t)std::max(NS, (int64_t)1) * sizeof(StepShape));
+  P.off_small_opbase = off; off = align_up(off + (size_t)std::max(NS, (int64_t)1) * sizeof(int32_t));
   P.off_acc = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(double2));
   P.off_bits = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(uint64_t));
   P.off_out = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(peps_c128));
   P.off_tables_end = off;
   off = align_up(off, 4096);
   P.lane_off = off;
-  const int n_gbufs = quad ? 4 * P.lanes + 4 : 2 * P.lanes + (pc > 0 ? 2 : 0);
+  const int n_gbufs = P.small ? 0 : quad ? 4 * P.lanes + 4 : 2 * P.lanes + (pc > 0 ? 2 : 0);
   off += (quad && P.odd) ? P.odd_bytes : (size_t)n_gbufs * P.gbuf_bytes;
   P.need = off;
   if (!ws) return PEPS_OK;
@@ -1784,6 +1845,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   const DeviceStatus *st = (const DeviceStatus *)(base + P.off_status);
   (void)st;
   const uint64_t *bsrc = host_bits ? (const uint64_t *)(base + P.off_bits) : bits_dev;
+  P.small_bits = bsrc;
   for (size_t i = 0; i < items.size(); ++i) {
     items[i].bits = bsrc + rel[i].bit;
     items[i].A = rel[i].a_unit ? nullptr : (const void *)(base + P.lane_off + rel[i].a);
@@ -1979,6 +2041,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   put(P.off_g1, g1.data(), g1.size() * sizeof(Gate1Entry));
   put(P.off_cz, cz.data(), cz.size() * sizeof(CzEntry));
   put(P.off_g2, g2e.data(), g2e.size() * sizeof(Gate2Entry));
+  put(P.off_evo_refs, evo_refs.data(), evo_refs.size() * sizeof(EvoRef));
+  put(P.off_evo_first, evo_first.data(), evo_first.size() * sizeof(int32_t));
+  put(P.off_small_steps, P.steps.data(), P.steps.size() * sizeof(StepShape));
+  put(P.off_small_opbase, P.step_opbase.data(), P.step_opbase.size() * sizeof(int32_t));
   put(P.off_opdesc, ops.data(), ops.size() * sizeof(OpDesc));
   put(P.off_opbuild, obe.data(), obe.size() * sizeof(OpBuildEntry));
   put(P.off_opbuild2, obe2.data(), obe2.size() * sizeof(OpBuild2Entry));
@@ -2057,7 +2123,7 @@ static int ensure_events(peps_ctx *c, size_t n) {
 // Launch counters of one graph replay (the same sequence as an eager call
 // with the evolution included).
 static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
-  S.launches_evolve = 1 + (int64_t)P.evo.size();
+  S.launches_evolve = P.evo_sites ? 1 : 1 + (int64_t)P.evo.size();
   if (P.opts.prefix_cols > 0 && P.n > 0) S.launches_finalize++;
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
@@ -2095,12 +2161,27 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
 // contraction launch (their count goes to *n_timed, their kind to timed_tc).
 static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s,
                             bool rebuild, bool timing, peps_stats &S, size_t *n_timed,
-                            std::vector<char> *timed_tc) {
+                            std::vector<char> *timed_tc, bool capturing = false) {
+  // inside a stream capture an event record becomes a graph node only when
+  // recorded as an external event (a plain record orders streams)
+  auto record = [&](cudaEvent_t e) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                     : cudaEventRecord(e, s);
+  };
   char *base = (char *)P.ws;
   DeviceStatus *st = (DeviceStatus *)(base + P.off_status);
   const int64_t wd_ns = P.opts.watchdog_ns > 0 ? P.opts.watchdog_ns : 2000000000LL;
   CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
-  if (rebuild) {
+  if (rebuild && P.evo_sites) {
+    CUDA_TRY(launch_evolve_sites((const Gate1Entry *)(base + P.off_g1),
+                                 (const CzEntry *)(base + P.off_cz),
+                                 (const Gate2Entry *)(base + P.off_g2),
+                                 (const EvoRef *)(base + P.off_evo_refs),
+                                 (const int32_t *)(base + P.off_evo_first),
+                                 (float2 *const *)(base + P.off_site_ptrs),
+                                 (const int64_t *)(base + P.off_site_lo), c->n, st, s));
+    S.launches_evolve++;
+  } else if (rebuild) {
     CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
                                (const int64_t *)(base + P.off_site_lo), c->n, st, s));
     S.launches_evolve++;
@@ -2167,8 +2248,20 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
     for (auto &l : P.launches) {
       if (skip_lower && l.lower) continue;
       if (l.kind == 0) {
-        if (timing) CUDA_TRY(cudaEventRecord(c->ev[2 * *n_timed], s));
-        if (l.tc) {
+        if (timing) CUDA_TRY(record(c->ev[2 * *n_timed]));
+        if (l.small) {
+          SmallSweep sw{};
+          sw.steps = (const StepShape *)(base + P.off_small_steps);
+          sw.op_base = (const int32_t *)(base + P.off_small_opbase);
+          sw.ops = ops;
+          sw.bits = P.small_bits;
+          sw.acc = acc;
+          sw.n = P.n;
+          sw.n_steps = P.n_steps;
+          sw.cap_g = P.small_cap_g;
+          sw.cap_e = P.small_cap_e;
+          CUDA_TRY(launch_sweep_small(sw, c->sm_count, s));
+        } else if (l.tc) {
           CUDA_TRY(launch_contract_tc(l.tc_handle, items + l.items_off, l.n_items, ops, recs,
                                       st, wd_ns, c->sm_count, s));
           S.launches_contract_tc++;
@@ -2178,7 +2271,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
           CUDA_TRY(launch_contract_simt(l.shape, items + l.items_off, l.n_items, ops, recs, st, s));
         }
         if (timing) {
-          CUDA_TRY(cudaEventRecord(c->ev[2 * *n_timed + 1], s));
+          CUDA_TRY(record(c->ev[2 * *n_timed + 1]));
           timed_tc->push_back(l.tc);
           ++*n_timed;
         }
@@ -2249,7 +2342,7 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
       P.graph_n_timed = 0;
       P.graph_timed_tc.clear();
       int rc = enqueue_sequence(c, P, d_bits_in, cs, true, timing, S2, &P.graph_n_timed,
-                                &P.graph_timed_tc);
+                                &P.graph_timed_tc, true);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (rc) {

@@ -180,6 +180,13 @@ struct Gate2Entry {
   float2 W_lo[4][4];
 };
 
+// One gate half of a site's evolution list (the per-site evolution kernel):
+// kind 0 = Gate1Entry, 1 = CzEntry, 2 = Gate2Entry; idx into that table.
+struct EvoRef {
+  int32_t kind;
+  int32_t idx;
+};
+
 // Operand build entry (one site, one tau, one slice variant).  The four legs
 // are given by their role in the sweep that absorbs the site: l and u are
 // contracted (K = l u), r and d are new (N = r d).  For the column sweep the
@@ -269,6 +276,12 @@ cudaError_t launch_init_sites(float2 *const *bufs, const int64_t *lo_off, int n_
                               DeviceStatus *st, cudaStream_t s);
 cudaError_t launch_gate1(const Gate1Entry *d_entries, int n, int64_t max_half,
                          cudaStream_t s);
+// The whole evolution in one launch: block q applies site q's gate halves
+// refs[first[q] .. first[q+1]) in order, from |0> in bufs[q].
+cudaError_t launch_evolve_sites(const Gate1Entry *g1, const CzEntry *cz, const Gate2Entry *g2,
+                               const EvoRef *refs, const int32_t *first, float2 *const *bufs,
+                               const int64_t *lo_off, int n_sites, DeviceStatus *st,
+                               cudaStream_t s);
 cudaError_t launch_cz(const CzEntry *d_entries, int n, int64_t max_out, cudaStream_t s);
 cudaError_t launch_gate2(const Gate2Entry *d_entries, int n, int64_t max_out, cudaStream_t s);
 cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_kn,
@@ -295,6 +308,26 @@ cudaError_t launch_build_tc_operands(int n_ops, int64_t max_kn, OpDesc *d_ops, i
 cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, int n_items,
                                  const OpDesc *d_ops, Rec *d_recs, const DeviceStatus *st,
                                  cudaStream_t s);
+// Whole sweeps of small lattices in one persistent launch (contract_small.cu):
+// the plan's steps and their first operand index, the bitstrings and the
+// FP64 amplitude accumulators; cap_g / cap_e = entries of the largest running
+// tensor / operand (shared memory: two running tensors and one operand).
+struct SmallSweep {
+  const StepShape *steps;
+  const int32_t *op_base;
+  const OpDesc *ops;
+  const uint64_t *bits;
+  double2 *acc;
+  int64_t n;
+  int32_t n_steps;
+  int32_t cap_g;
+  int32_t cap_e;
+  int32_t pad_;
+};
+constexpr size_t kSmallSweepMaxSmem = 96 * 1024;
+size_t small_sweep_smem(int cap_g, int cap_e);
+cudaError_t launch_sweep_small(const SmallSweep &p, int sm_count, cudaStream_t s);
+
 cudaError_t launch_finalize(const FinalEntry *d_entries, int n, int fmt, int64_t plane,
                             const Rec *d_recs, double2 *d_acc, cudaStream_t s);
 cudaError_t launch_store_out(const double2 *d_acc, peps_c128 *d_out, int64_t n,

@@ -74,11 +74,10 @@ __device__ __forceinline__ void cmul_ff(ff ur, ff ui, ff ar, ff ai, ff &re, ff &
 }
 
 // K1: A'^tau = sum_sigma U[tau][sigma] A^sigma (paper, main-text "onebody"
-// equation), in place, for every entry of a batch of gates on distinct sites.
-// The tensor is [2][half]; each thread mixes the two sigma slices at one
-// position, in float-float complex arithmetic.
-__global__ void k_gate1(const Gate1Entry *__restrict__ entries) {
-  const Gate1Entry &g = entries[blockIdx.y];
+// equation), in place.  The tensor is [2][half]; each thread mixes the two
+// sigma slices at positions e0, e0 + de, ..., in float-float complex
+// arithmetic.
+__device__ __forceinline__ void gate1_apply(const Gate1Entry &g, int64_t e0, int64_t de) {
   const int64_t half = g.half, lo = g.lo_off;
   float2 *A = g.A;
   ff ur[4], ui[4];
@@ -87,8 +86,7 @@ __global__ void k_gate1(const Gate1Entry *__restrict__ entries) {
     ur[i] = {g.U_hi[i].x, g.U_lo[i].x};
     ui[i] = {g.U_hi[i].y, g.U_lo[i].y};
   }
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < half;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = e0; e < half; e += de) {
     const float2 h0 = A[e], h1 = A[half + e], l0 = A[lo + e], l1 = A[lo + half + e];
     const ff a0r = {h0.x, l0.x}, a0i = {h0.y, l0.y}, a1r = {h1.x, l1.x}, a1i = {h1.y, l1.y};
     ff out[2][2];
@@ -107,22 +105,26 @@ __global__ void k_gate1(const Gate1Entry *__restrict__ entries) {
   }
 }
 
+// A batch of single-qubit gates on distinct sites (one per blockIdx.y).
+__global__ void k_gate1(const Gate1Entry *__restrict__ entries) {
+  gate1_apply(entries[blockIdx.y], (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+              (int64_t)gridDim.x * blockDim.x);
+}
+
 // K2: one half of a CZ (paper, main-text "twoqubita/b" with the exact
 // projector split of CZ).  The leg `axis` grows from d to 2d with the new
 // Schmidt bit s as its least significant bit:
 //   projector side:  A'^tau[..., 2*i + s, ...] = delta(tau, s) A^tau[..., i, ...]
 //   phase side:      A'^tau[..., 2*i + s, ...] = (-1)^(s*tau) A^tau[..., i, ...]
 // With fixed_s >= 0 (a sliced CZ) the leg keeps its size and only the term
-// s = fixed_s is applied.  One thread per output entry.
-__global__ void k_cz(const CzEntry *__restrict__ entries) {
-  const CzEntry &g = entries[blockIdx.y];
+// s = fixed_s is applied.  One thread per output entry (e0, e0 + de, ...).
+__device__ __forceinline__ void cz_apply(const CzEntry &g, int64_t e0, int64_t de) {
   int od[4] = {g.dims[0], g.dims[1], g.dims[2], g.dims[3]};
   const bool bundle = g.fixed_s < 0;
   if (bundle) od[g.axis] *= 2;
   const int64_t half_out = (int64_t)od[0] * od[1] * od[2] * od[3];
   const int64_t total = 2 * half_out;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = e0; e < total; e += de) {
     int64_t rem = e;
     int idx[4];
     idx[3] = (int)(rem % od[3]); rem /= od[3];
@@ -149,17 +151,20 @@ __global__ void k_cz(const CzEntry *__restrict__ entries) {
   }
 }
 
+__global__ void k_cz(const CzEntry *__restrict__ entries) {
+  cz_apply(entries[blockIdx.y], (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+           (int64_t)gridDim.x * blockDim.x);
+}
+
 // General two-qubit gate, one half (see Gate2Entry): each thread writes one
 // output entry, mixing the two sigma slices of its input position with
 // W_s[tau][.] in float-float complex arithmetic.
-__global__ void k_gate2(const Gate2Entry *__restrict__ entries) {
-  const Gate2Entry &g = entries[blockIdx.y];
+__device__ __forceinline__ void gate2_apply(const Gate2Entry &g, int64_t e0, int64_t de) {
   int od[4] = {g.dims[0], g.dims[1], g.dims[2], g.dims[3]};
   od[g.axis] *= g.chi;
   const int64_t half_in = (int64_t)g.dims[0] * g.dims[1] * g.dims[2] * g.dims[3];
   const int64_t half_out = (int64_t)od[0] * od[1] * od[2] * od[3];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * half_out;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = e0; e < 2 * half_out; e += de) {
     int64_t rem = e;
     int idx[4];
     idx[3] = (int)(rem % od[3]); rem /= od[3];
@@ -187,6 +192,50 @@ __global__ void k_gate2(const Gate2Entry *__restrict__ entries) {
   }
 }
 
+__global__ void k_gate2(const Gate2Entry *__restrict__ entries) {
+  gate2_apply(entries[blockIdx.y], (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+              (int64_t)gridDim.x * blockDim.x);
+}
+
+// The whole evolution in one launch, one block per site (small site tensors):
+// a site's tensor evolves through its own gate halves only (a single-qubit
+// gate, or one side of a CZ or general gate split), so every block applies
+// its site's list in circuit order with a barrier between gates, starting
+// from |0> (A^0 = 1, A^1 = 0) in its first buffer.  Block 0 also writes the
+// status block's unit scalars.
+__global__ void __launch_bounds__(256) k_evolve_sites(
+    const Gate1Entry *__restrict__ g1, const CzEntry *__restrict__ cz,
+    const Gate2Entry *__restrict__ g2, const EvoRef *__restrict__ refs,
+    const int32_t *__restrict__ first, float2 *const *bufs, const int64_t *lo_off,
+    DeviceStatus *st) {
+  const int q = blockIdx.x;
+  if (threadIdx.x == 0) {
+    float2 *a = bufs[q];
+    a[0] = make_float2(1.f, 0.f);
+    a[1] = make_float2(0.f, 0.f);
+    a[lo_off[q]] = make_float2(0.f, 0.f);
+    a[lo_off[q] + 1] = make_float2(0.f, 0.f);
+    if (q == 0) {
+      st->error = 0;
+      st->error_info = 0;
+      st->timeout = 0;
+      st->unit_f32 = make_float2(1.f, 0.f);
+      st->unit_h16[0] = pack_bf16(1.f, 0.f);
+      st->unit_h16[1] = 0u;
+      st->unit_f16[0] = pack_f16(1.f, 0.f);
+      st->unit_f16[1] = 0u;
+    }
+  }
+  __syncthreads();
+  for (int i = first[q]; i < first[q + 1]; ++i) {
+    const EvoRef r = refs[i];
+    if (r.kind == 0) gate1_apply(g1[r.idx], threadIdx.x, blockDim.x);
+    else if (r.kind == 1) cz_apply(cz[r.idx], threadIdx.x, blockDim.x);
+    else gate2_apply(g2[r.idx], threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
 static int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b > 4096) b = 4096;
@@ -200,6 +249,15 @@ cudaError_t launch_init_sites(float2 *const *bufs, const int64_t *lo_off, int n_
   int blocks = (n_sites + threads - 1) / threads;
   if (blocks < 1) blocks = 1;
   k_init_sites<<<blocks, threads, 0, s>>>(bufs, lo_off, n_sites, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_evolve_sites(const Gate1Entry *g1, const CzEntry *cz, const Gate2Entry *g2,
+                               const EvoRef *refs, const int32_t *first, float2 *const *bufs,
+                               const int64_t *lo_off, int n_sites, DeviceStatus *st,
+                               cudaStream_t s) {
+  if (n_sites <= 0) return cudaSuccess;
+  k_evolve_sites<<<n_sites, 256, 0, s>>>(g1, cz, g2, refs, first, bufs, lo_off, st);
   return cudaGetLastError();
 }
 

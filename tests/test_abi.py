@@ -297,3 +297,30 @@ def test_seven_by_seven_needs_slicing():
         B.peps_workspace_bytes(h, 1, o)
     assert e.value.code == B.PEPS_EUNSUPPORTED
     B.peps_destroy(h)
+
+
+def test_small_lattices_plan_one_contraction_launch():
+    # every running tensor and operand of a 5x5 (1+16+1) sweep fits one
+    # block's shared memory: one contraction launch for all bitstrings (FP32
+    # and the split forms), and a smaller workspace (no running-tensor
+    # buffers); STEPWISE, a single-pass form or a larger lattice plan one
+    # launch per step and lane chunk
+    c, h = make(5, 5, 16, 2)
+    o, k = B.make_opts(precision="fp32")
+    small = B.peps_plan_info_get(h, 1024, o)
+    assert small["n_launches"] == 1 and small["n_tc_launches"] == 0
+    ws_small = B.peps_workspace_bytes(h, 1024, o)
+    o, k = B.make_opts(precision="fp32", flags=B.PEPS_FLAG_STEPWISE)
+    step = B.peps_plan_info_get(h, 1024, o)
+    assert step["n_launches"] == step["n_steps"] * (1024 // 16)
+    assert step["flops_call"] == small["flops_call"]
+    assert B.peps_workspace_bytes(h, 1024, o) > ws_small
+    o, k = B.make_opts(precision="fp16x3")
+    assert B.peps_plan_info_get(h, 1024, o)["n_launches"] == 1
+    o, k = B.make_opts(precision="bf16")
+    assert B.peps_plan_info_get(h, 1024, o)["n_launches"] > 1
+    B.peps_destroy(h)
+    c, h = make(6, 6, 24, 3)
+    o, k = B.make_opts(precision="fp32")
+    assert B.peps_plan_info_get(h, 64, o)["n_launches"] > 1
+    B.peps_destroy(h)

@@ -263,30 +263,70 @@ def test_slices_sum_to_unsliced(sim_factory):
 def test_timing_and_launch_counters(sim_factory):
     circ, bits = workload("5x5_d16")
     sim = sim_factory(circ)
-    sim.amplitudes(bits[:32], precision="fp32", flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
+    step = B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_STEPWISE
+    sim.amplitudes(bits[:32], precision="fp32", flags=step)
     st = sim.stats()
     ns = sim.plan_info(32, precision="fp32")["n_steps"]
     assert 10 <= ns < 25   # some boundary row pairs absorbed together
     assert st["contract_ms"] > 0
     assert st["launches_contract"] == ns * 2   # 2 lane chunks of 16
-    sim.amplitudes(bits[:32], precision="fp32", fuse_rows=1,
-                   flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
+    sim.amplitudes(bits[:32], precision="fp32", fuse_rows=1, flags=step)
     assert sim.stats()["launches_contract"] == 25 * 2   # one site per step
     assert st["launches_evolve"] > 10
     assert st["launches_total"] >= st["launches_contract"] + st["launches_evolve"]
+    # without STEPWISE a lattice this small is one evolution launch (a block
+    # per site) and one contraction launch for every bitstring's whole sweep
+    sim.amplitudes(bits[:32], precision="fp32", flags=B.PEPS_FLAG_TIMING | B.PEPS_FLAG_REBUILD)
+    st = sim.stats()
+    assert st["launches_contract"] == 1 and st["launches_evolve"] == 1
+    assert st["contract_ms"] > 0
+    assert st["contract_flops"] == sim.plan_info(32, precision="fp32")["flops_call"]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
-def test_cuda_graph_replay_matches_eager(sim_factory, prec):
+@pytest.mark.parametrize("stepwise", [False, True])
+def test_cuda_graph_replay_matches_eager(sim_factory, prec, stepwise):
     circ, bits = workload("5x5_d16")
     sim = sim_factory(circ)
-    eager = sim.amplitudes(bits[:40], precision=prec)
-    g1 = sim.amplitudes(bits[:40], precision=prec, flags=B.PEPS_FLAG_GRAPH)   # capture + replay
-    g2 = sim.amplitudes(bits[:40], precision=prec, flags=B.PEPS_FLAG_GRAPH)   # replay
+    f = B.PEPS_FLAG_STEPWISE if stepwise else 0
+    eager = sim.amplitudes(bits[:40], precision=prec, flags=f)
+    g1 = sim.amplitudes(bits[:40], precision=prec, flags=f | B.PEPS_FLAG_GRAPH)  # capture + replay
+    g2 = sim.amplitudes(bits[:40], precision=prec, flags=f | B.PEPS_FLAG_GRAPH)  # replay
     assert np.array_equal(g1, eager) and np.array_equal(g2, eager)
     st = sim.stats()
-    ns = sim.plan_info(40, precision=prec)["n_steps"]
-    assert st["launches_contract"] == ns * 3   # 40 bitstrings in lanes of 16
+    ns = sim.plan_info(40, precision=prec, flags=f)["n_steps"]
+    assert st["launches_contract"] == (ns * 3 if stepwise else 1)   # lanes of 16
+    # a graph that also times its contraction launches
+    g3 = sim.amplitudes(bits[:40], precision=prec,
+                        flags=f | B.PEPS_FLAG_GRAPH | B.PEPS_FLAG_TIMING)
+    assert np.array_equal(g3, eager)
+    assert sim.stats()["contract_ms"] > 0
+
+
+@pytest.mark.parametrize("R,C,d,seed", [(4, 4, 8, 1), (5, 5, 16, 2), (1, 6, 10, 2), (6, 1, 10, 3),
+                                        (2, 7, 20, 4), (3, 3, 22, 6), (4, 5, 16, 5)])
+def test_whole_sweep_launch_matches_stepwise(sim_factory, R, C, d, seed):
+    # the small-lattice path (evolution in one launch, every bitstring's sweep
+    # in one launch) against the step-by-step launches and the state vector
+    circ = make_circuit(R, C, d, seed)
+    n = R * C
+    bits = uniform_bitstrings(n, 301, seed)   # a ragged count
+    ref = sv.amplitudes(n, circ.gates, bits)
+    sim = sim_factory(circ)
+    for prec in ("fp32", "fp16x3"):
+        whole = sim.amplitudes(bits, precision=prec)
+        assert sim.stats()["launches_contract"] == 1, prec
+        step = sim.amplitudes(bits, precision=prec, flags=B.PEPS_FLAG_STEPWISE)
+        assert relerr(whole, ref) < SPLIT_TOL, prec
+        assert relerr(step, ref) < SPLIT_TOL, prec
+    # slices and held bits through the same launch
+    ncz = sum(1 for g in circ.gates if g.kind == "cz")
+    if ncz >= 3:
+        sl = [0, ncz // 2, ncz - 1]
+        tot = sim.amplitudes(bits, precision="fp32", sliced_cz=sl)
+        assert relerr(tot, ref) < SPLIT_TOL
+    held = sim.amplitudes(bits, precision="fp32", hold_ties=True)
+    assert relerr(held, ref) < SPLIT_TOL
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16x3", "bf16x3"])
