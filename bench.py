@@ -129,7 +129,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", default="bench",
                     choices=["bench", "profile", "slices", "precision", "small", "peaks",
-                             "quadrants", "pt8x8", "marginals"],
+                             "quadrants", "pt8x8", "marginals", "evolution", "group"],
                     help="profile: one amplitude of the workload on one lane, no timing "
                          "(the small case for ncu captures, about 4 GiB on the device); "
                          "slices: 7x7 (1+40+1), the whole amplitude of one bitstring on "
@@ -144,7 +144,11 @@ def parse():
                          "paper's workstation experiment, 10000 amplitudes of an 8x8 (1+25+1) "
                          "circuit and their Porter-Thomas statistics; marginals: marginal "
                          "probabilities of the top half's 18 qubits of a 6x6 (1+16+1) "
-                         "circuit (the double-layer network), 512 bitstrings")
+                         "circuit (the double-layer network), 512 bitstrings; evolution: the "
+                         "7x7 (1+40+1) circuit's evolution and operand build at full size (the "
+                         "bandwidth kernels' case for ncu), one small slice contracted; group: "
+                         "one prefix group of the bench batch with --lanes lanes (the tensor-"
+                         "core kernel's case for ncu)")
     ap.add_argument("--check-full", action="store_true",
                     help="--case slices: also the amplitude from the slice set chosen without x")
     ap.add_argument("--group-only", action="store_true",
@@ -708,6 +712,34 @@ def slices_7x7(args, check: bool = True, check_full: bool = False, warm: bool = 
     return rec
 
 
+def run_group_case(args):
+    """One prefix group of the bench batch (its first 64 bitstrings, sharing
+    columns 0-2) in the bench's configuration (square partition, tied bits
+    held, --lanes lanes per launch): the small case whose kernel launches
+    have the bench's shapes per lane, for ncu counter captures."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload(WORKLOAD)
+    sim = Simulator(circ.R, circ.C)
+    sim.apply_circuit(circ)
+    kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
+              scheme="quadrants", hold_ties=args.hold_ties)
+    out = sim.amplitudes(bits[:64], **kw)
+    check = golden_check(out, bits)
+    st = sim.stats()
+    o, keep = B.make_opts(**kw)
+    print(json.dumps({"case": "group", "lanes": args.lanes, "hold_ties": args.hold_ties,
+                      "launches": st["launches_total"], "tc_launches": st["launches_contract_tc"],
+                      "workspace_bytes": B.peps_workspace_bytes(sim.h, 64, o),
+                      "check": check, "finite": bool(np.isfinite(out).all())}), flush=True)
+    sim.close()
+
+
 def run_slices_case(args):
     rec = slices_7x7(args, check=True, check_full=args.check_full)
     print(json.dumps(dict({"case": "slices"}, **rec)), flush=True)
@@ -951,6 +983,47 @@ def run_marginals_case(args):
     sim.close()
 
 
+def run_evolution_case(args):
+    """The bandwidth kernels at the paper's size: the circuit evolution (PEPS
+    init, single-qubit gate absorption, CZ absorption with bond doubling) and
+    the projection / operand build of the 7x7 (1+40+1) circuit, whose site
+    tensors reach 2 x 32^4 complex entries (32 MiB each as float-float).  The
+    contraction is kept small by holding the 80 CZ bits of the column sweep's
+    cut set under 2^24 entries (one sub-slice).  One timed call; the
+    evolution's share is reported from its launch count and the
+    contraction's event time."""
+    import numpy as np
+    import torch
+
+    from paper_1905_08394_gb300 import Simulator, slicing
+    from paper_1905_08394_gb300 import binding as B
+    from rqc_inputs import workload
+
+    circ, bits = workload("7x7_d40")
+    sim = Simulator(circ.R, circ.C)
+    sim.apply_circuit(circ)
+    cs = slicing.choose(circ, 2 ** 24, seed=5)
+    kw = dict(precision=args.precision, fixed_cz=cs.sliced_cz, fixed_s=[0] * len(cs.sliced_cz),
+              fuse_rows=1)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_REBUILD, **kw)   # plan + warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.amplitudes_device(d_bits, flags=B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    st = sim.stats()
+    o, keep = B.make_opts(**kw)
+    print(json.dumps({"case": "evolution", "workload": "7x7 (1+40+1): evolution and operand "
+                      "build at full size, one sub-slice of an 80-bit cut set",
+                      "call_ms": e0.elapsed_time(e1), "contract_ms": st["contract_ms"],
+                      "launches_evolve": st["launches_evolve"],
+                      "launches_operand": st["launches_operand"],
+                      "workspace_bytes": B.peps_workspace_bytes(sim.h, 1, o)}), flush=True)
+    sim.close()
+
+
 def run_peaks_case(args):
     """Peak rates measured by this repository's own microbenchmarks: the FP32
     FMA rate of the CUDA cores and the dense tcgen05 rate for kind::f16 and
@@ -1010,6 +1083,10 @@ def main():
         run_marginals_case(args)
     elif args.case == "small":
         run_small_case(args)
+    elif args.case == "evolution":
+        run_evolution_case(args)
+    elif args.case == "group":
+        run_group_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

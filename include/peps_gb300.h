@@ -285,6 +285,28 @@ typedef struct {
 PEPS_API int peps_plan_info_get(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
                                 peps_plan_info *info);
 
+/* One contraction step of a plan: the complex GEMM out[M x N] = G[M x K] E[K x N]
+ * that absorbs a block of `sites` sites (0: a merge of two stored tensors),
+ * with `variants` operands selected per bitstring, and where it runs. */
+typedef struct {
+    int64_t M;
+    int32_t K, N;
+    int32_t sites;            /* 1, 2, or 0 for a merge                      */
+    int32_t variants;         /* operands of the step (per output bits)      */
+    int32_t tensor_cores;     /* 1: tcgen05 kernel, 0: CUDA-core kernel      */
+    int32_t part;             /* column sweep: -1; square partition: the
+                                 quarter 0..3 (ul, bl, ur, br) or 4 = merge  */
+    int64_t launches;         /* launches of the step in the call            */
+    double flops;             /* algorithmic real flops of the step over the
+                                 call (8 per complex multiply-add)           */
+} peps_step_info;
+
+/* The steps of the plan of an amplitude call, in sweep order: writes at most
+ * `cap` entries (steps may be NULL when cap = 0) and the number of steps to
+ * *n_out.  Host only. */
+PEPS_API int peps_plan_steps(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
+                             peps_step_info *steps, int64_t cap, int64_t *n_out);
+
 /* Device workspace needed for an amplitude call on n_bitstrings with opts. */
 PEPS_API int peps_workspace_bytes(const peps_ctx *ctx, int64_t n_bitstrings, const peps_opts *opts,
                          size_t *bytes);

@@ -53,7 +53,8 @@ EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "pe
             "peps_bond_dim",
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",
             "peps_get_stats", "peps_cz_count", "peps_last_error", "peps_version",
-            "peps_plan_info_get", "peps_amplitudes_noalloc", "peps_output_ties")
+            "peps_plan_info_get", "peps_amplitudes_noalloc", "peps_output_ties",
+            "peps_plan_steps")
 
 
 class peps_c128(ct.Structure):
@@ -98,6 +99,15 @@ class peps_plan_info(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class peps_step_info(ct.Structure):
+    _fields_ = [("M", ct.c_int64), ("K", ct.c_int32), ("N", ct.c_int32),
+                ("sites", ct.c_int32), ("variants", ct.c_int32), ("tensor_cores", ct.c_int32),
+                ("part", ct.c_int32), ("launches", ct.c_int64), ("flops", ct.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PepsError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"peps error {code}: {msg}")
@@ -136,6 +146,9 @@ def load() -> ct.CDLL:
     lib.peps_plan_info_get.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                        ct.POINTER(peps_plan_info)]
     lib.peps_output_ties.argtypes = [P, P, P, P, ct.c_int64, ct.POINTER(ct.c_int64)]
+    lib.peps_plan_steps.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
+                                    ct.POINTER(peps_step_info), ct.c_int64,
+                                    ct.POINTER(ct.c_int64)]
     lib.peps_last_error.restype = ct.c_char_p
     lib.peps_version.restype = ct.c_char_p
     for name in EXPORTED:
@@ -292,6 +305,15 @@ def peps_output_ties(h) -> list:
     _check(load().peps_output_ties(h, cz.ctypes.data, kind.ctypes.data, flip.ctypes.data, k,
                                    ct.byref(n)))
     return [(int(cz[i]), int(kind[i]), int(flip[i])) for i in range(k)]
+
+
+def peps_plan_steps(h, n: int, opts: peps_opts) -> list:
+    """The plan's contraction steps (peps_step_info as dicts), in sweep order."""
+    k = ct.c_int64()
+    _check(load().peps_plan_steps(h, n, ct.byref(opts), None, 0, ct.byref(k)))
+    arr = (peps_step_info * max(k.value, 1))()
+    _check(load().peps_plan_steps(h, n, ct.byref(opts), arr, k.value, ct.byref(k)))
+    return [arr[i].as_dict() for i in range(k.value)]
 
 
 def peps_last_error() -> str:

@@ -75,6 +75,9 @@ struct Launch {
   double flops, bytes;
   bool lower = false;   // odd side: a launch of the lower half (bl, br -> F_b)
   bool small = false;   // kind 0: every step of every bitstring in one launch
+  int step = -1;        // kind 0: the plan step it runs (-1: the whole sweep)
+  int fused_merge = -1; // kind 3: index of the merge launch whose epilogue wrote
+                        // the dot's partial sums (-1: the separate dot kernel)
 };
 
 struct Plan {
@@ -1539,6 +1542,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
                              int a_lanes) {
     Launch ln{};
     ln.kind = 0;
+    ln.step = s;
     ln.shape = P.steps[s];
     ln.tc = want_tc && tc_supports(P.steps[s], fmt);
     ln.a_base_rel = rs[0].a;
@@ -1665,6 +1669,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         d.rec_y = rec_u;
         d.rec_f = rec_b;
         d.out_index = (int)i;
+        d.nslots = kDotBlocks;
         dots.push_back(d);
         P.launches.push_back(dl);
       }
@@ -1698,23 +1703,29 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         {
           std::vector<StepItem> its;
           std::vector<RelItem> rs;
+          // on the tensor cores the merge's epilogue forms the dot product
+          // with F_ur itself (Y is never stored): its items point at F_ur
+          const bool fuse = want_tc && tc_supports(P.steps[P.s_m2], fmt);
           for (int l = 0; l < nl; ++l) {
             const int64_t ch = mch(l);
             StepItem it{};
             it.op_base = P.op_m2;
             it.in_rec = (int)(ch * NS + br.first + br.count - 1);
             it.out_rec = (int)(ch * NS + P.s_m2);
-            RelItem ri{lane_buf(l, 2 + bbr), lane_buf(l, 2 + (bbr ^ 1)), false, mbit(l)};
+            RelItem ri{lane_buf(l, 2 + bbr), fuse ? lane_buf(l, bur) : lane_buf(l, 2 + (bbr ^ 1)),
+                       false, mbit(l)};
             its.push_back(it);
             rs.push_back(ri);
           }
           add_step_launch(P.s_m2, its, rs, nl);
+          if (fuse) P.launches.back().shape.dot = 1;
         }
         Launch dl{};
         dl.kind = 3;
         dl.aux_off = (int64_t)dots.size();
         dl.n_aux = nl;
         dl.flops = dl.bytes = 0;
+        if (P.launches.back().shape.dot) dl.fused_merge = (int)P.launches.size() - 1;
         for (int l = 0; l < nl; ++l) {
           const int64_t ch = mch(l);
           DotEntry d{};
@@ -1724,6 +1735,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           d.rec_y = (int)(ch * NS + P.s_m2);
           d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
           d.out_index = (int)mbit(l);
+          d.nslots = kDotBlocks;   // fused: set once the merge's tiles are known
           dots.push_back(d);
         }
         P.launches.push_back(dl);
@@ -1824,7 +1836,16 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_tops = off; off = align_up(off + std::max<size_t>(tops.size(), 1) * sizeof(TensorOpEntry));
   P.off_dots = off; off = align_up(off + std::max<size_t>(dots.size(), 1) * sizeof(DotEntry));
   P.off_partials = off;
-  off = align_up(off + (quad ? (size_t)kDotBlocks * P.lanes * sizeof(double2) : 16));
+  {
+    // per lane: the separate dot kernel's blocks, or a fused merge's slots
+    // (at most ceil(M / 128) x (2N / 16) tiles x 4 warps)
+    size_t per_lane = kDotBlocks;
+    if (quad && !P.odd) {
+      const StepShape &m2 = P.steps[P.s_m2];
+      per_lane = std::max(per_lane, (size_t)((m2.M + 127) / 128) * (size_t)(2 * m2.N / 16) * 4);
+    }
+    off = align_up(off + (quad ? per_lane * P.lanes * sizeof(double2) : 16));
+  }
   P.off_small_steps = off; off = align_up(off + (size_t)std::max(NS, (int64_t)1) * sizeof(StepShape));
   P.off_small_opbase = off; off = align_up(off + (size_t)std::max(NS, (int64_t)1) * sizeof(int32_t));
   P.off_acc = off; off = align_up(off + std::max<int64_t>(n, 1) * sizeof(double2));
@@ -1879,6 +1900,12 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
                         o.tc_cluster, &l.tc_handle);
     if (rc != 0)
       return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
+  }
+  // fused dots: the merge's partial-sum slots per item
+  for (auto &l : P.launches) {
+    if (l.kind != 3 || l.fused_merge < 0) continue;
+    const int slots = tc_dot_slots(P.launches[l.fused_merge].tc_handle);
+    for (int k = 0; k < l.n_aux; ++k) dots[l.aux_off + k].nslots = slots;
   }
 
   std::vector<OpDesc> ops(n_ops);
@@ -2108,6 +2135,55 @@ extern "C" int peps_plan_info_get(const peps_ctx *c, int64_t n, const peps_opts 
   return PEPS_OK;
 }
 
+extern "C" int peps_plan_steps(const peps_ctx *c, int64_t n, const peps_opts *opts,
+                               peps_step_info *steps, int64_t cap, int64_t *n_out) {
+  if (!c || !n_out) return fail(PEPS_EINVAL, "peps_plan_steps: NULL argument");
+  if (cap < 0 || (cap > 0 && !steps)) return fail(PEPS_EINVAL, "peps_plan_steps: bad output array");
+  peps_opts o{};
+  if (opts) o = *opts;
+  Plan P;
+  int rc = build_plan(const_cast<peps_ctx *>(c), n, o, nullptr, 0, nullptr, false, P);
+  if (rc) return rc;
+  const bool want_tc = o.precision != PEPS_FP32_SIMT && !(o.flags & PEPS_FLAG_NO_TC);
+  const int64_t ns = (int64_t)P.slice_list.size(), nl = lower_runs(P);
+  std::vector<peps_step_info> out(P.n_steps);
+  for (int s = 0; s < P.n_steps; ++s) {
+    const StepShape &sh = P.steps[s];
+    peps_step_info &i = out[s];
+    i.M = sh.M;
+    i.K = sh.K;
+    i.N = sh.N;
+    i.sites = sh.nq;
+    i.variants = step_variants(sh);
+    i.tensor_cores = (!P.small && want_tc && tc_supports(sh, P.fmt)) ? 1 : 0;
+    i.part = -1;
+    if (P.scheme == PEPS_SCHEME_QUADRANTS) {
+      i.part = 4;
+      for (int qi = 0; qi < 4; ++qi)
+        if (s >= P.quarter[qi].first && s < P.quarter[qi].first + P.quarter[qi].count) i.part = qi;
+    }
+  }
+  // launches and flops per step (a whole-sweep launch counts for no step's
+  // launches but carries every step's flops)
+  for (auto &l : P.launches) {
+    if (l.kind != 0) continue;
+    const int64_t k = l.lower ? nl : ns;
+    if (l.small) {
+      for (int s = 0; s < P.n_steps; ++s)
+        out[s].flops += (double)k * 8.0 * (double)P.steps[s].M * P.steps[s].K * P.steps[s].N *
+                        (double)P.n;
+      continue;
+    }
+    if (l.step >= 0 && l.step < P.n_steps) {
+      out[l.step].launches += k;
+      out[l.step].flops += (double)k * l.flops;
+    }
+  }
+  for (int64_t s = 0; s < std::min<int64_t>(cap, P.n_steps); ++s) steps[s] = out[s];
+  *n_out = P.n_steps;
+  return PEPS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Execution
 // ---------------------------------------------------------------------------
@@ -2146,7 +2222,7 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
     } else if (l.kind == 2) {
       S.launches_operand += k * (l.tc ? 3 : 2);
     } else if (l.kind == 3) {
-      S.launches_finalize += 2 * k;
+      S.launches_finalize += (l.fused_merge >= 0 ? 1 : 2) * k;
     } else {
       S.launches_finalize += k;
     }
@@ -2263,7 +2339,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
           CUDA_TRY(launch_sweep_small(sw, c->sm_count, s));
         } else if (l.tc) {
           CUDA_TRY(launch_contract_tc(l.tc_handle, items + l.items_off, l.n_items, ops, recs,
-                                      st, wd_ns, c->sm_count, s));
+                                      st, wd_ns, c->sm_count, s, l.shape.dot ? partials : nullptr));
           S.launches_contract_tc++;
           S.contract_tc_flops += l.flops;
           S.contract_tc_bytes += l.bytes;
@@ -2290,6 +2366,9 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
           CUDA_TRY(launch_operand_bounds(1, ops + l.op, s, l.shape.N));
           S.launches_operand += 2;
         }
+      } else if (l.kind == 3 && l.fused_merge >= 0) {
+        CUDA_TRY(launch_dot_final(dots + l.aux_off, l.n_aux, recs, partials, acc, s));
+        S.launches_finalize += 1;
       } else if (l.kind == 3) {
         CUDA_TRY(launch_dot(dots + l.aux_off, l.n_aux, P.fmt, P.plane, recs, partials, acc, s));
         S.launches_finalize += 2;

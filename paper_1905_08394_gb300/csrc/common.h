@@ -127,6 +127,12 @@ struct StepShape {
                   //   vb = 0: b * (Mr N) + ((m_lo dh' + h') P + m_hi) dv' + v'
                   //   vb = 1: (b dv' + v') (Mr dh') + (m_lo dh' + h') P + m_hi
   int32_t xq[4];
+  int32_t dot;    // tensor cores, a merge whose output is only dotted with a
+                  // stored tensor (the square partition's last contraction):
+                  // the item's D is that tensor, read; the epilogue writes
+                  // the partial sums sum_n out[m, n] D[m N + n] (unscaled) per
+                  // (tile, CTA, warp) instead of storing the output
+  int32_t pad3_;
 };
 
 // Operand index of a lane for a block: bit j = output bit of the block's
@@ -244,12 +250,14 @@ struct TensorOpEntry {
 
 // amplitude += sum_i Y[i] F[i] 2^-(S_Y + S_F): the final contraction of the
 // square partition (Y and F in the running-tensor format, same layout).
+// nslots: partial sums of the entry to add (kDotBlocks for the separate dot
+// kernel; the fused merge's slot count otherwise).
 struct DotEntry {
   const void *Y, *F;
   int64_t n;
   int32_t rec_y, rec_f;
   int32_t out_index;
-  int32_t pad_;
+  int32_t nslots;
 };
 
 struct FinalEntry {     // one output amplitude contribution
@@ -295,6 +303,9 @@ cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int 
 constexpr int kDotBlocks = 256;
 cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
                        const Rec *d_recs, double2 *d_partials, double2 *d_acc, cudaStream_t s);
+// Only the final pass (the partial sums were written by a fused merge).
+cudaError_t launch_dot_final(const DotEntry *d_entries, int n, const Rec *d_recs,
+                             const double2 *d_partials, double2 *d_acc, cudaStream_t s);
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s);
 // A merge operand's tensor-core planes and bound straight from the stored
@@ -351,7 +362,10 @@ void tc_release(void *handle);
 cudaError_t tc_warm(void *handle);
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
                                const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,
-                               int64_t watchdog_ns, int sm_count, cudaStream_t s);
+                               int64_t watchdog_ns, int sm_count, cudaStream_t s,
+                               double2 *dot_partials = nullptr);
+// Partial-sum slots per item of a fused-dot launch (sh.dot).
+int tc_dot_slots(const void *handle);
 int tc_Kr_pad(int K);   // real K of a tensor-core operand
 int tc_Nr_pad(int N);   // real N
 

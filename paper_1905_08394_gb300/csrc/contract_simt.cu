@@ -137,6 +137,52 @@ k_contract_simt(const StepShape sh, const StepItem *__restrict__ items,
   if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) recs[it.out_rec].exp = s_in + x + op.e_c;
 }
 
+// The same step for a running tensor of at most a few rows (the first steps
+// of a sweep, M = 1 .. 8): one thread per output entry, no tiling.
+template <int FMT>
+__global__ void __launch_bounds__(256)
+k_contract_rows(const StepShape sh, const StepItem *__restrict__ items,
+                const OpDesc *__restrict__ ops, Rec *__restrict__ recs) {
+  const StepItem it = items[blockIdx.y];
+  const uint64_t bits = *it.bits;
+  const OpDesc &op = ops[it.op_base + block_variant(bits, sh)];
+  const int M = (int)sh.M, K = sh.K, N = sh.N;
+  const bool unit_in = it.in_rec < 0;
+  const float mu = unit_in ? 1.f : __uint_as_float(recs[it.in_rec].maxbits);
+  const int s_in = unit_in ? 0 : recs[it.in_rec].exp;
+  const int x = step_scale_exp(mu, __uint_as_float(op.beta_c_bits), sh.target);
+  const float sc = pow2f(x);
+  const int64_t Mr = sh.Mr > 0 ? sh.Mr : sh.M;
+  const bool batched = Mr != sh.M;
+  const int64_t Mlo = Mr / sh.P;
+  const int dv = sh.dv_out, dh = sh.dh_out;
+  float vmax = 0.f;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < M * N) {
+    const int m = e / N, n = e - m * N;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < K; ++k) {
+      float2 a;
+      if (unit_in) a = (m == 0 && k == 0) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+      else a = load_g<FMT>(it.A, (int64_t)m * K + k, sh.plane);
+      const float2 w = op.Ec[(int64_t)k * N + n];
+      re = fmaf(a.x, w.x, fmaf(-a.y, w.y, re));
+      im = fmaf(a.x, w.y, fmaf(a.y, w.x, im));
+    }
+    const int64_t b = batched ? m / Mr : 0, mr = m - b * Mr;
+    const int64_t m_hi = mr / Mlo, m_lo = mr - m_hi * Mlo;
+    const int hh = sh.nvs ? n % dh : n / dv, vv = sh.nvs ? n / dh : n % dv;
+    const int64_t rot = (m_lo * dh + hh) * sh.P + m_hi;
+    const int64_t dest = sh.vb ? (b * dv + vv) * (Mr * dh) + rot : b * (Mr * N) + rot * dv + vv;
+    const float2 v = make_float2(re * sc, im * sc);
+    store_g<FMT>(it.D, dest, sh.plane, v);
+    vmax = max_abs2(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&recs[it.out_rec].maxbits, __float_as_uint(vmax));
+  if (blockIdx.x == 0 && threadIdx.x == 0) recs[it.out_rec].exp = s_in + x + op.e_c;
+}
+
 }  // namespace
 
 cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, int n_items,
@@ -144,6 +190,21 @@ cudaError_t launch_contract_simt(const StepShape &sh, const StepItem *d_items, i
                                  cudaStream_t s) {
   (void)st;
   if (n_items <= 0) return cudaSuccess;
+  if (sh.M <= 8 && n_items <= 65535) {
+    const int64_t blocks = (sh.M * sh.N + 255) / 256;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)blocks, n_items);
+    switch (sh.fmt) {
+      case FMT_F32: k_contract_rows<FMT_F32><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      case FMT_TF32: k_contract_rows<FMT_TF32><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      case FMT_BF16: k_contract_rows<FMT_BF16><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      case FMT_FP16: k_contract_rows<FMT_FP16><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      case FMT_BF16X2: k_contract_rows<FMT_BF16X2><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      case FMT_FP16X2: k_contract_rows<FMT_FP16X2><<<grid, 256, 0, s>>>(sh, d_items, d_ops, d_recs); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   const int64_t mt = (sh.M + BM - 1) / BM;
   const int nt = (sh.N + BN - 1) / BN;
   if (mt > 0x7fffffffLL || nt > 65535 || n_items > 65535) return cudaErrorInvalidValue;

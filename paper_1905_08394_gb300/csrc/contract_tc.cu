@@ -84,6 +84,7 @@ struct __align__(64) TcParams {
                 // (1: n fastest over a whole row group)
   int64_t mlo;  // m_hi-major: Mr / P
   int64_t watchdog_ns;
+  double2 *dot_partials;   // sh.dot: [item][tiles_per_item * CG * EPI_WARPS]
 };
 
 // ---------------------------------------------------------------------------
@@ -625,7 +626,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         const bool unit_in = si->in_rec < 0;
         const float mu = unit_in ? 1.f : __uint_as_float(p.recs[si->in_rec].maxbits);
         s_in = unit_in ? 0 : p.recs[si->in_rec].exp;
-        x = step_scale_exp(mu, __uint_as_float(op->beta_t_bits), p.sh.target);
+        // a fused dot keeps the accumulator unscaled (nothing is stored)
+        x = p.sh.dot ? 0 : step_scale_exp(mu, __uint_as_float(op->beta_t_bits), p.sh.target);
         sc = pow2f(x);
       }
       const int acc = p.nbuf == 2 ? (int)(local & 1) : 0;
@@ -667,12 +669,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       const int64_t row_base = m_lo * dh;
       const int64_t bofs = b * MrN;
       void *D = si->D;
+      const bool dotm = p.sh.dot != 0;
+      float dre = 0.f, dim = 0.f;   // fused dot: this row's partial sum
+      // fused dot: the partner entries of row m (P = 1, row-major m N + n),
+      // loaded one chunk ahead of their use
+      const int64_t dot_e = m_lo * (int64_t)p.sh.N + ((nt * BN) >> 1);
+      Raw8 fcur, fnext;
+      if (dotm && live) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
       uint32_t ra[16], rb[16];
       tmem_ld16_issue(tbase, ra);
       tmem_wait(ra);
       for (int c = 0; c < BN; c += 16) {
         const bool more = c + 16 < BN;
         if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), rb);
+        if (dotm && live && more) load8_raw<FMT>(D, dot_e + ((c + 16) >> 1), p.sh.plane, fnext);
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
@@ -684,7 +694,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(rc[i]);
         }
-        if (live) {
+        if (live && dotm) {
+          // merge output row m times the stored tensor's entries at the same place
+          float2 f[8];
+          unpack8<FMT>(fcur, f);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            dre = fmaf(v[2 * j], f[j].x, fmaf(-v[2 * j + 1], f[j].y, dre));
+            dim = fmaf(v[2 * j], f[j].y, fmaf(v[2 * j + 1], f[j].x, dim));
+          }
+          fcur = fnext;
+        } else if (live) {
           const int nc0 = (nt * BN + c) >> 1;
           if (vec) {
             int64_t dest0;
@@ -696,6 +716,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
               dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
             }
             vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
+          } else if (vbm && !nvs && (dv & 7) == 0) {
+            // open-leg store with dv' a multiple of 8: the chunk's 8 columns
+            // share h' and are 8 consecutive v', each a whole batch slice
+            // (Mr dh' entries) apart; a warp's rows are consecutive m_hi
+            const int hh = nc0 / dv, vv0 = nc0 - hh * dv;
+            const int64_t base = (b * dv + vv0) * Mrdh + (row_base + hh) * P + m_hi;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
+              store_g<FMT>(D, base + (int64_t)j * Mrdh, p.sh.plane, o);
+              vmax = fmaxf(vmax, max_abs2(o));
+            }
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -722,8 +754,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)acc * 8u);
       }
-      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-      if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
+      if (dotm) {
+        // the warp's 32 rows summed in FP64, one slot per (tile, CTA, warp)
+        double r = (double)dre, i = (double)dim;
+        for (int o = 16; o > 0; o >>= 1) {
+          r += __shfl_xor_sync(0xffffffffu, r, o);
+          i += __shfl_xor_sync(0xffffffffu, i, o);
+        }
+        if (lane == 0)
+          p.dot_partials[((int64_t)item * tiles_per_item + rem) * (CG * EPI_WARPS) +
+                         (int)rank * EPI_WARPS + quad] = make_double2(r, i);
+      } else {
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
+      }
       if (mt == 0 && nt == 0 && warp == 2 && lane == 0) p.recs[si->out_rec].exp = s_in + op->b_t + x + op->e_c;
     }
   }
@@ -1049,11 +1093,19 @@ static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cg, int units, 
                  : launch_one<FMT, 64, 1>(prm, units, smem, s);
 }
 
+int tc_dot_slots(const void *handle) {
+  const TcLaunchData *d = (const TcLaunchData *)handle;
+  return d->prm.tiles_m * d->prm.tiles_n * EPI_WARPS;
+}
+
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
                                const OpDesc *d_ops, Rec *d_recs, DeviceStatus *st,
-                               int64_t watchdog_ns, int sm_count, cudaStream_t s) {
+                               int64_t watchdog_ns, int sm_count, cudaStream_t s,
+                               double2 *dot_partials) {
   TcLaunchData *d = (TcLaunchData *)handle;
   TcParams prm = d->prm;
+  prm.dot_partials = dot_partials;
+  if (prm.sh.dot && !dot_partials) return cudaErrorInvalidValue;
   prm.items = d_items;
   prm.n_items = n_items;
   prm.ops = d_ops;

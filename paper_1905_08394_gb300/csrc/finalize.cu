@@ -40,8 +40,10 @@ cudaError_t launch_finalize(const FinalEntry *d_entries, int n, int fmt, int64_t
 
 // Square partition, last contraction: sum_i Y[i] F[i] for each entry.  Pass
 // 1: block b of entry e sums a fixed slice of the products into
-// partials[e][b]; pass 2 adds the partials in order, applies 2^-(S_Y + S_F)
-// and accumulates into the amplitude.  Both passes have a fixed order, so
+// partials[e][b]; pass 2 adds the entry's nslots partials in order, applies
+// 2^-(S_Y + S_F) and accumulates into the amplitude.  Where the merge that
+// makes Y runs on the tensor cores, its epilogue writes the partials itself
+// (Y is never stored) and only pass 2 runs.  Both passes have a fixed order, so
 // repeated calls give identical results.  A thread sums its terms (n / 65536
 // of them, 256 at 6x6 (1+32+1)) in FP32 on two chains; the sums across
 // threads and blocks are FP64.  With terms of random phase the FP32 part
@@ -82,21 +84,38 @@ __global__ void __launch_bounds__(256) k_dot(const DotEntry *__restrict__ entrie
   if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = make_double2(sre[0], sim[0]);
 }
 
-__global__ void k_dot_final(const DotEntry *__restrict__ entries, int n, const Rec *__restrict__ recs,
-                            const double2 *__restrict__ partials, double2 *acc) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
+// One block per entry: thread t adds slots t, t + 128, ... in order, then a
+// fixed tree over the threads (the same order on every call).
+__global__ void __launch_bounds__(128) k_dot_final(const DotEntry *__restrict__ entries,
+                                                   const Rec *__restrict__ recs,
+                                                   const double2 *__restrict__ partials,
+                                                   double2 *acc) {
+  const int e = blockIdx.x;
   const DotEntry d = entries[e];
+  const int ns = d.nslots;
   double re = 0.0, im = 0.0;
-  for (int b = 0; b < kDotBlocks; ++b) {
-    re += partials[(int64_t)e * kDotBlocks + b].x;
-    im += partials[(int64_t)e * kDotBlocks + b].y;
+  for (int b = threadIdx.x; b < ns; b += blockDim.x) {
+    re += partials[(int64_t)e * ns + b].x;
+    im += partials[(int64_t)e * ns + b].y;
   }
-  const int S = recs[d.rec_y].exp + recs[d.rec_f].exp;
-  double2 a = acc[d.out_index];
-  a.x += ldexp(re, -S);
-  a.y += ldexp(im, -S);
-  acc[d.out_index] = a;
+  __shared__ double sre[128], sim[128];
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sre[threadIdx.x] += sre[threadIdx.x + w];
+      sim[threadIdx.x] += sim[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int S = recs[d.rec_y].exp + recs[d.rec_f].exp;
+    double2 a = acc[d.out_index];
+    a.x += ldexp(sre[0], -S);
+    a.y += ldexp(sim[0], -S);
+    acc[d.out_index] = a;
+  }
 }
 
 cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
@@ -114,7 +133,14 @@ cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_dot_final<<<(n + 127) / 128, 128, 0, s>>>(d_entries, n, d_recs, d_partials, d_acc);
+  k_dot_final<<<n, 128, 0, s>>>(d_entries, d_recs, d_partials, d_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_final(const DotEntry *d_entries, int n, const Rec *d_recs,
+                             const double2 *d_partials, double2 *d_acc, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_dot_final<<<n, 128, 0, s>>>(d_entries, d_recs, d_partials, d_acc);
   return cudaGetLastError();
 }
 

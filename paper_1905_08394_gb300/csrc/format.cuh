@@ -168,6 +168,54 @@ __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t pla
   return m;
 }
 
+// 8 consecutive complex entries e0 .. e0+7 (e0 % 8 == 0) in a storage
+// format, loaded with 16-byte vector loads into raw words (so that a load can
+// be issued early and unpacked later), and unpacked to float2.
+struct Raw8 {
+  uint4 w[4];
+};
+template <int FMT>
+__device__ __forceinline__ void load8_raw(const void *base, int64_t e0, int64_t plane, Raw8 &r) {
+  if (FMT == FMT_F32 || FMT == FMT_TF32) {
+    const uint4 *s = reinterpret_cast<const uint4 *>(reinterpret_cast<const float2 *>(base) + e0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r.w[i] = s[i];
+  } else if (FMT == FMT_BF16 || FMT == FMT_FP16) {
+    const uint4 *s = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint32_t *>(base) + e0);
+    r.w[0] = s[0];
+    r.w[1] = s[1];
+  } else {
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(base);
+    const uint4 *sh = reinterpret_cast<const uint4 *>(p + e0);
+    const uint4 *sl = reinterpret_cast<const uint4 *>(p + plane / 2 + e0);
+    r.w[0] = sh[0];
+    r.w[1] = sh[1];
+    r.w[2] = sl[0];
+    r.w[3] = sl[1];
+  }
+}
+template <int FMT>
+__device__ __forceinline__ void unpack8(const Raw8 &r, float2 (&f)[8]) {
+  const uint32_t *w = reinterpret_cast<const uint32_t *>(r.w);
+  if (FMT == FMT_F32 || FMT == FMT_TF32) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = make_float2(__uint_as_float(w[2 * j]), __uint_as_float(w[2 * j + 1]));
+  } else if (FMT == FMT_BF16) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = unpack_bf16(w[j]);
+  } else if (FMT == FMT_FP16) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f[j] = unpack_f16(w[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float2 h = FMT == FMT_BF16X2 ? unpack_bf16(w[j]) : unpack_f16(w[j]);
+      const float2 l = FMT == FMT_BF16X2 ? unpack_bf16(w[8 + j]) : unpack_f16(w[8 + j]);
+      f[j] = make_float2(h.x + l.x, h.y + l.y);
+    }
+  }
+}
+
 // Power-of-two scale of one absorption step.  The input's entries are bounded
 // by mu (max of |Re|, |Im| of the previous step's scaled output, taken before
 // rounding to the storage format; the factor 1 + 2^-7 covers that rounding,

@@ -118,6 +118,10 @@ __device__ __forceinline__ ff2 ffmul(ff2 x, ff2 y) {
   return ff_fast(p, e);
 }
 
+// legs of a two-site block operand whose element offsets are tabulated in
+// shared memory (longer legs compute them per entry)
+constexpr int kMaxLeg2 = 256;
+
 // Two-site block operand W (see OpBuild2Entry), summed over the internal
 // vertical bond in float-float from the float-float site tensors, rounded
 // once to FP32.  k = (l_a * Lb + l_b) * Ua + u_a, n = (r_a * Rb + r_b) * Db + d_b.
@@ -128,11 +132,28 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
   const int Lb = g.b.rdims[0], Rb = g.b.rdims[1], Db = g.b.rdims[3];
   const int K = La * Lb * Ua, N = Ra * Rb * Db;
   if (blockIdx.x * blockDim.x >= K * N) return;
-  // full index of every restricted value of the shared bond, on both sites
+  // full index of every restricted value of the shared bond, on both sites,
+  // and (where the legs are short enough) element offsets of the other legs
   __shared__ int mid_a[kMaxMid], mid_b[kMaxMid];
+  __shared__ int64_t off_la[kMaxLeg2], off_ra[kMaxLeg2], off_ua[kMaxLeg2];
+  __shared__ int64_t off_lb[kMaxLeg2], off_rb[kMaxLeg2], off_db[kMaxLeg2];
   for (int m = threadIdx.x; m < Mid; m += blockDim.x) {
     mid_a[m] = (int)g.a.fixed_val[3] | deposit_bits(m, g.a.free_mask[3]);
     mid_b[m] = (int)g.b.fixed_val[2] | deposit_bits(m, g.b.free_mask[2]);
+  }
+  const bool tab = La <= kMaxLeg2 && Ra <= kMaxLeg2 && Ua <= kMaxLeg2 && Lb <= kMaxLeg2 &&
+                   Rb <= kMaxLeg2 && Db <= kMaxLeg2;
+  if (tab) {
+    auto fill = [&](int64_t *t, const OpBuildEntry &e, int role, int n) {
+      for (int v = threadIdx.x; v < n; v += blockDim.x)
+        t[v] = (int64_t)((int)e.fixed_val[role] | deposit_bits(v, e.free_mask[role])) * e.stride[role];
+    };
+    fill(off_la, g.a, 0, La);
+    fill(off_ra, g.a, 1, Ra);
+    fill(off_ua, g.a, 2, Ua);
+    fill(off_lb, g.b, 0, Lb);
+    fill(off_rb, g.b, 1, Rb);
+    fill(off_db, g.b, 3, Db);
   }
   __syncthreads();
   float2 *Ec = const_cast<float2 *>(op.Ec);
@@ -148,8 +169,14 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
     const int k = i / N, n = i - k * N;
     const int ua = k % Ua, lb = (k / Ua) % Lb, la = k / (Ua * Lb);
     const int db = n % Db, rb = (n / Db) % Rb, ra = n / (Db * Rb);
-    const int64_t pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
-    const int64_t pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
+    int64_t pa0, pb0;
+    if (tab) {
+      pa0 = (int64_t)g.a.tau * g.a.tau_stride + off_la[la] + off_ra[ra] + off_ua[ua];
+      pb0 = (int64_t)g.b.tau * g.b.tau_stride + off_lb[lb] + off_rb[rb] + off_db[db];
+    } else {
+      pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
+      pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
+    }
     ff2 re = {0.f, 0.f}, im = {0.f, 0.f};
     for (int m = 0; m < Mid; ++m) {
       const int64_t pa = pa0 + (int64_t)mid_a[m] * a_sd, pb = pb0 + (int64_t)mid_b[m] * b_su;

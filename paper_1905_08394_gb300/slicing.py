@@ -136,7 +136,7 @@ def seeded_slice_ids(n_sliced: int, count: int, seed: int):
 
 
 def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: int = 0,
-                     beam: int = 16, max_bits: int = 24, x=None) -> SliceSet:
+                     beam: int = 16, max_bits: int = 24, x=None, keep: int = 1):
     """Slice set for the square partition on the planner of handle `h` (the
     circuit `circ` applied to it): the cheapest total flops found whose
     workspace is at most `ws_budget` bytes.  Each beam level adds one cut bit
@@ -144,7 +144,9 @@ def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: i
     / budget) above the budget.  Which CZ of an edge is cut next: a seeded
     order, or, for one output bitstring `x`, first the CZs whose bit `x`
     fixes (slice_constraints), so that the cut costs no extra slices; the
-    total then counts only the slices that can be nonzero."""
+    total then counts only the slices that can be nonzero.  With keep > 1 the
+    `keep` cheapest sets found are returned (a list, cheapest first), for a
+    choice by measured time."""
     import math
 
     from . import binding as B
@@ -174,6 +176,7 @@ def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: i
         return sl, info, ws
 
     best = None
+    found = {}
     frontier = [{}]
     seen = set()
     for _ in range(max_bits + 1):
@@ -196,6 +199,8 @@ def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: i
                 total = call_flops(info, len(sl), circ, sl, x)
                 if ws <= ws_budget and (best is None or total < best[0]):
                     best = (total, sl, info, ws)
+                if ws <= ws_budget:
+                    found[tuple(sl)] = (total, sl, info, ws)
                 over = max(0.0, math.log2(ws / ws_budget))
                 scored.append((math.log2(total) + 2.0 * over, tag, nc))
         if not scored:
@@ -204,9 +209,17 @@ def choose_quadrants(h, circ, ws_budget: int, precision: str = "fp16x3", seed: i
         frontier = [nc for _, _, nc in scored[:beam]]
     if best is None:
         raise ValueError("no slice set within the budget was found")
-    total, sl, info, ws = best
-    return SliceSet(sl, int(info["max_entries"]), 2 ** len(sl), [], float(info["flops_per_chain"]),
-                    int(ws), float(total), int(info["n_lower_bits"]))
+
+    def as_set(entry):
+        total, sl, info, ws = entry
+        return SliceSet(sl, int(info["max_entries"]), 2 ** len(sl), [],
+                        float(info["flops_per_chain"]), int(ws), float(total),
+                        int(info["n_lower_bits"]))
+
+    if keep > 1:
+        ranked = sorted(found.values(), key=lambda e: (e[0], e[1]))[:keep]
+        return [as_set(e) for e in ranked]
+    return as_set(best)
 
 
 def call_flops(info: dict, n_sliced: int, circ=None, sliced_cz=None, x=None) -> float:

@@ -196,3 +196,17 @@ def test_the_7x7_d40_amplitude_slice_set():
     again = slicing.choose_quadrants(h, circ, 180 * 10 ** 9, seed=5, x=x)
     assert again.sliced_cz == ss.sliced_cz
     B.peps_destroy(h)
+
+
+def test_square_partition_chooser_keeps_the_cheapest_sets():
+    # keep > 1: the cheapest sets found within the budget, cheapest first, each
+    # within the budget; the first is the single choice
+    circ, bits = workload("6x6_d32")
+    h = ctx_for(circ)
+    one = slicing.choose_quadrants(h, circ, 2 * 10 ** 9, seed=3)
+    many = slicing.choose_quadrants(h, circ, 2 * 10 ** 9, seed=3, keep=3)
+    assert 1 <= len(many) <= 3
+    assert many[0].flops_total == one.flops_total
+    assert all(a.flops_total <= b.flops_total for a, b in zip(many, many[1:]))
+    assert all(s.workspace_bytes <= 2 * 10 ** 9 for s in many)
+    B.peps_destroy(h)
