@@ -102,6 +102,7 @@ struct Plan {
   int n_steps = 0;
   int lanes = 0;
   int n_groups = 0;
+  int glanes = 1;           // square partition: groups whose left quarters share a launch
   size_t off_status = 0, off_site_ptrs = 0, off_site_lo = 0, off_g1 = 0, off_cz = 0, off_g2 = 0, off_opdesc = 0,
          off_opbuild = 0, off_recs = 0, off_items = 0, off_fin = 0, off_acc = 0,
          off_bits = 0, off_out = 0, off_tables_end = 0;
@@ -1304,6 +1305,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     }
   }
   int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
+  // square partition: the left quarters of up to this many groups share a launch
+  P.glanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(P.n_groups, 1));
   lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, gs), 1));
   P.lanes = lanes;
 
@@ -1535,6 +1538,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     return (size_t)(BPL * lane + b) * P.gbuf_bytes;
   };
   auto pre_buf = [&](int b) -> size_t { return (size_t)(BPL * P.lanes + b) * P.gbuf_bytes; };
+  // square partition: group g's buffers, laid out like a lane's after the lanes'
+  auto grp_buf = [&](int g, int b) -> size_t {
+    return (size_t)(BPL * (P.lanes + g) + b) * P.gbuf_bytes;
+  };
   const size_t REL = (size_t)1 << 62;  // marker: relative to the buffer area
   struct RelItem { size_t a, d; bool a_unit; int64_t bit; };
   std::vector<RelItem> rel;
@@ -1674,26 +1681,36 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         P.launches.push_back(dl);
       }
     }
-    for (int g = 0; g < (P.odd ? 0 : P.n_groups); ++g) {
+    // the left quarters of up to `lanes` groups in one sweep each (a lane per
+    // group; group slot j's four buffers sit after the member lanes' with the
+    // same per-lane layout), then per group the left half F_l and its members
+    const int G = P.odd ? 0 : P.n_groups;
+    int bul = 0, bbl = 0;
+    for (int g = 0; g < G; ++g) {
+      const int gslot = g % P.glanes;
+      if (gslot == 0) {
+        const int gc = std::min(P.glanes, G - g);
+        auto gch = [&](int l) { return (int64_t)(g + l); };
+        auto gbit = [&](int l) { return (int64_t)(g + l) * gs; };
+        bul = sweep(ul, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, b); });
+        bbl = sweep(bl, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, 2 + b); });
+      }
+      auto grp = [&](int b) { return grp_buf(gslot, b); };
       const int64_t chain = g, first = (int64_t)g * gs;
-      auto gch = [&](int) { return chain; };
-      auto gbit = [&](int) { return first; };
-      const int bul = sweep(ul, 1, gch, gbit, [&](int, int b) { return pre_buf(b); });
-      const int bbl = sweep(bl, 1, gch, gbit, [&](int, int b) { return pre_buf(2 + b); });
       const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
       const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
       const int rec_l = (int)(chain * NS + P.s_m1);
-      tensor_op(pre_buf(2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
+      tensor_op(grp(2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
       {
         StepItem it{};
         it.op_base = P.op_m1;
         it.in_rec = rec_ul;
         it.out_rec = rec_l;
-        RelItem ri{pre_buf(bul), pre_buf(2 + (bbl ^ 1)), false, first};
+        RelItem ri{grp(bul), grp(2 + (bbl ^ 1)), false, first};
         add_step_launch(P.s_m1, {it}, {ri}, 1);
       }
       // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
-      tensor_op(pre_buf(2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2, P.s_m2);
+      tensor_op(grp(2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2, P.s_m2);
       for (int64_t base = 0; base < gs; base += P.lanes) {
         const int nl = (int)std::min<int64_t>(P.lanes, gs - base);
         auto mch = [&](int l) { return (int64_t)P.n_groups + first + base + l; };
@@ -1854,7 +1871,9 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_tables_end = off;
   off = align_up(off, 4096);
   P.lane_off = off;
-  const int n_gbufs = P.small ? 0 : quad ? 4 * P.lanes + 4 : 2 * P.lanes + (pc > 0 ? 2 : 0);
+  const int n_gbufs = P.small ? 0
+                      : quad ? 4 * P.lanes + 4 * P.glanes
+                             : 2 * P.lanes + (pc > 0 ? 2 : 0);
   off += (quad && P.odd) ? P.odd_bytes : (size_t)n_gbufs * P.gbuf_bytes;
   P.need = off;
   if (!ws) return PEPS_OK;

@@ -77,6 +77,25 @@ __device__ __forceinline__ void cmul_ff(ff ur, ff ui, ff ar, ff ai, ff &re, ff &
 // equation), in place.  The tensor is [2][half]; each thread mixes the two
 // sigma slices at positions e0, e0 + de, ..., in float-float complex
 // arithmetic.
+__device__ __forceinline__ void gate1_mix(const ff (&ur)[4], const ff (&ui)[4], float2 h0, float2 h1,
+                                          float2 l0, float2 l1, float2 &o0h, float2 &o0l,
+                                          float2 &o1h, float2 &o1l) {
+  const ff a0r = {h0.x, l0.x}, a0i = {h0.y, l0.y}, a1r = {h1.x, l1.x}, a1i = {h1.y, l1.y};
+  ff out[2][2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    ff r0, i0, r1, i1;
+    cmul_ff(ur[2 * t], ui[2 * t], a0r, a0i, r0, i0);
+    cmul_ff(ur[2 * t + 1], ui[2 * t + 1], a1r, a1i, r1, i1);
+    out[t][0] = ff_add(r0, r1);
+    out[t][1] = ff_add(i0, i1);
+  }
+  o0h = make_float2(out[0][0].hi, out[0][1].hi);
+  o0l = make_float2(out[0][0].lo, out[0][1].lo);
+  o1h = make_float2(out[1][0].hi, out[1][1].hi);
+  o1l = make_float2(out[1][0].lo, out[1][1].lo);
+}
+
 __device__ __forceinline__ void gate1_apply(const Gate1Entry &g, int64_t e0, int64_t de) {
   const int64_t half = g.half, lo = g.lo_off;
   float2 *A = g.A;
@@ -85,6 +104,24 @@ __device__ __forceinline__ void gate1_apply(const Gate1Entry &g, int64_t e0, int
   for (int i = 0; i < 4; ++i) {
     ur[i] = {g.U_hi[i].x, g.U_lo[i].x};
     ui[i] = {g.U_hi[i].y, g.U_lo[i].y};
+  }
+  if ((half & 1) == 0 && (lo & 1) == 0) {
+    // two neighbouring positions per thread: 16-byte loads and stores
+    float4 *A4 = reinterpret_cast<float4 *>(A);
+    const int64_t h4 = half >> 1, l4 = lo >> 1;
+    for (int64_t p = e0; p < h4; p += de) {
+      const float4 h0 = A4[p], h1 = A4[h4 + p], l0 = A4[l4 + p], l1 = A4[l4 + h4 + p];
+      float2 a0h, a0l, a1h, a1l, b0h, b0l, b1h, b1l;
+      gate1_mix(ur, ui, make_float2(h0.x, h0.y), make_float2(h1.x, h1.y), make_float2(l0.x, l0.y),
+                make_float2(l1.x, l1.y), a0h, a0l, a1h, a1l);
+      gate1_mix(ur, ui, make_float2(h0.z, h0.w), make_float2(h1.z, h1.w), make_float2(l0.z, l0.w),
+                make_float2(l1.z, l1.w), b0h, b0l, b1h, b1l);
+      A4[p] = make_float4(a0h.x, a0h.y, b0h.x, b0h.y);
+      A4[l4 + p] = make_float4(a0l.x, a0l.y, b0l.x, b0l.y);
+      A4[h4 + p] = make_float4(a1h.x, a1h.y, b1h.x, b1h.y);
+      A4[l4 + h4 + p] = make_float4(a1l.x, a1l.y, b1l.x, b1l.y);
+    }
+    return;
   }
   for (int64_t e = e0; e < half; e += de) {
     const float2 h0 = A[e], h1 = A[half + e], l0 = A[lo + e], l1 = A[lo + half + e];
@@ -119,6 +156,39 @@ __global__ void k_gate1(const Gate1Entry *__restrict__ entries) {
 // With fixed_s >= 0 (a sliced CZ) the leg keeps its size and only the term
 // s = fixed_s is applied.  One thread per output entry (e0, e0 + de, ...).
 __device__ __forceinline__ void cz_apply(const CzEntry &g, int64_t e0, int64_t de) {
+  if (g.fixed_s < 0) {
+    // Bundled split, by input element: [pre][D][post] -> [pre][2D][post]
+    // with pre = (tau, the legs before the axis), post = the legs after it;
+    // each input element gives the outputs s = 0 and s = 1, post entries
+    // apart (adjacent when the axis is the fastest leg: one 16-byte store).
+    int pre_inner = 1, post = 1;
+    for (int a = 0; a < g.axis; ++a) pre_inner *= g.dims[a];
+    for (int a = g.axis + 1; a < 4; ++a) post *= g.dims[a];
+    const int D = g.dims[g.axis];
+    const int64_t total = (int64_t)2 * pre_inner * D * post;
+    for (int64_t u = e0; u < total; u += de) {
+      const int64_t r = u / post;
+      const int post_i = (int)(u - r * post);
+      const int64_t pre_i = r / D;
+      const int i = (int)(r - pre_i * D);
+      const int tau = (int)(pre_i / pre_inner);
+      const float2 v = g.in[u], vl = g.in[g.lo_off + u];
+      const float f0 = g.kind == 0 ? (tau == 0 ? 1.f : 0.f) : 1.f;
+      const float f1 = g.kind == 0 ? (tau == 1 ? 1.f : 0.f) : (tau ? -1.f : 1.f);
+      const int64_t o0 = (pre_i * (2 * D) + 2 * i) * post + post_i;
+      if (post == 1) {
+        reinterpret_cast<float4 *>(g.out)[o0 >> 1] = make_float4(f0 * v.x, f0 * v.y, f1 * v.x, f1 * v.y);
+        reinterpret_cast<float4 *>(g.out + g.lo_off)[o0 >> 1] =
+            make_float4(f0 * vl.x, f0 * vl.y, f1 * vl.x, f1 * vl.y);
+      } else {
+        g.out[o0] = make_float2(f0 * v.x, f0 * v.y);
+        g.out[o0 + post] = make_float2(f1 * v.x, f1 * v.y);
+        g.out[g.lo_off + o0] = make_float2(f0 * vl.x, f0 * vl.y);
+        g.out[g.lo_off + o0 + post] = make_float2(f1 * vl.x, f1 * vl.y);
+      }
+    }
+    return;
+  }
   int od[4] = {g.dims[0], g.dims[1], g.dims[2], g.dims[3]};
   const bool bundle = g.fixed_s < 0;
   if (bundle) od[g.axis] *= 2;
