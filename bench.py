@@ -49,8 +49,9 @@ REL_ERR_GATE = 1e-5
 # the workload, identical in both arms' lines
 CONFIG = {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing columns 0-2",
           "seed": 4, "bitstrings": 512,
-          "l2": "inputs larger than L2 (128 MiB quarter tensors x 4 per lane for the square "
-                "partition, 2 GiB running tensor per lane for the column sweep)"}
+          "l2": "inputs larger than L2: running tensors of up to 2^23 entries (64 MiB) x 4 "
+                "buffers per lane x 64 lanes (17 GB) for the square partition, 2 GiB per lane "
+                "for the column sweep"}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_6x6_d32.json")
 
 
@@ -77,13 +78,17 @@ def golden_check(out, bits, first=0):
             "checked": len(idx), "indices": idx,
             "against": "FP64 oracle values of these bitstrings (tests/golden/oracle_6x6_d32.json)"}
 
-# ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
-# dram__bytes_write.sum; one pass) of `bench.py --no-cpu --fp32-steps 0
-# --steps 1 --warmup 1 --other-steps 1`: mean DRAM bytes per k_contract_tc
-# launch, per contraction scheme (2200 column-sweep launches in 5 calls, 2640
-# square-partition launches in 6 calls).
-TRAFFIC = {"sources_sha256_16": "d2d8f442fc786027",
-           "bytes_per_launch": {"columns": 36.36e9, "quadrants": 2.562e9}}
+# DRAM bytes (read + write) per k_contract_tc launch of this bench line, from
+# one ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
+# dram__bytes_write.sum) of the small case `bench.py --case group --lanes 8`
+# (one prefix group, 8 lanes per launch, 3.3 GB on the device), scaled to the
+# bench's launches by the units each processes: the left quarters' sweeps run
+# 8 groups per launch here (8x the captured one-group launch), the left-half
+# merges one group each (as captured), the members' steps 64 lanes (8x the
+# captured 8-lane launches); then the mean over the 107 launches of a call.
+# Valid while the kernel's sources hash to the captured version.
+TRAFFIC = {"sources_sha256_16": "15c05225d23e805e",
+           "bytes_per_launch": {"quadrants": 1.3932e9}}
 TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
 
 

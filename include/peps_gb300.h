@@ -119,12 +119,13 @@ enum {
                                evolution of small site tensors as one launch
                                with a block per site)                       */
     PEPS_FLAG_HOLD_TIES = 64 /* hold every CZ Schmidt bit that the output
-                               bitstring (or the initial state) fixes, as
-                               peps_output_ties lists them: the bond index of
-                               that bit takes only its tied value in each
+                               bitstring (or the initial state) fixes, and
+                               tie every linked bit to its source bit, as
+                               peps_output_ties lists them: the bond index
+                               takes only the values these ties allow in each
                                bitstring's contraction, which halves the bond
-                               for the whole sweep.  Exact: every dropped term
-                               of the bond sum is zero.  Each site operand
+                               per tied bit for the whole sweep.  Exact: every
+                               dropped term of the bond sum is zero.  Each site operand
                                then has a variant per value of the output bits
                                it depends on (its own and those of the
                                neighbours whose projector bits touch its
@@ -361,20 +362,27 @@ PEPS_API int peps_amplitudes_device(peps_ctx *ctx, const uint64_t *d_bitstrings,
 PEPS_API int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrings, int64_t n,
                                      peps_c128 *d_out, const peps_opts *opts, void *stream);
 
-/* CZ Schmidt bits fixed by the circuit's output (an extension of the paper's
- * exact contraction: zero terms of a bond sum are skipped).  The CZ split
- * P_0 (x) I + P_1 (x) Z puts the projector P_s on the lower-index qubit q.
- * Between two events on q every CZ factor acting on q is diagonal; where the
- * single-qubit gates between them multiply to a monomial matrix (diagonal or
- * anti-diagonal), a basis state of q stays a basis state, so consecutive
- * projector bits on q are tied, the first to the initial |0> and the last to
- * the measured output bit x_q.  Lists every tied CZ: its ordinal cz[i] (0 =
- * the first CZ applied), kind[i] = 1 for s = flip[i] (constant) or 2 for
- * s = x_q XOR flip[i] (q = that CZ's lower-index qubit), for every output
- * bitstring x.  Writes at most `cap` entries (the arrays may be NULL when
- * cap = 0) and the total count to *n_out.  Host only. */
+/* CZ Schmidt bits fixed by the circuit's output or tied to one another (an
+ * extension of the paper's exact contraction: zero terms of a bond sum are
+ * skipped).  The CZ split P_0 (x) I + P_1 (x) Z puts the projector P_s on the
+ * lower-index qubit q.  Between two events on q every CZ factor acting on q
+ * is diagonal; where the single-qubit gates between them multiply to a
+ * monomial matrix (diagonal or anti-diagonal), a basis state of q stays a
+ * basis state, so consecutive projector bits on q are tied, the first to the
+ * initial |0> and the last to the measured output bit x_q.  Lists every tied
+ * CZ: its ordinal cz[i] (0 = the first CZ applied) and kind[i]:
+ *   1: s = flip[i] (tied to the initial state);
+ *   2: s = x_q XOR flip[i] for every output bitstring x (q = that CZ's
+ *      lower-index qubit);
+ *   3: s = (the bit of CZ src[i]) XOR flip[i], where src[i] is an earlier
+ *      CZ on the same edge whose bit is free: a run of tied projectors that
+ *      reaches neither end, with two of its bits in one bond index, so that
+ *      index only takes half its values.
+ * src[i] = 0xFFFFFFFF for kinds 1 and 2.  Writes at most `cap` entries (the
+ * arrays may be NULL when cap = 0) and the total count to *n_out.  Host
+ * only. */
 PEPS_API int peps_output_ties(const peps_ctx *ctx, uint32_t *cz, uint8_t *kind, uint8_t *flip,
-                              int64_t cap, int64_t *n_out);
+                              uint32_t *src, int64_t cap, int64_t *n_out);
 
 /* Counters of the last amplitude call on this context. */
 PEPS_API int peps_get_stats(const peps_ctx *ctx, peps_stats *out);

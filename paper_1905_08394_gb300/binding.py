@@ -145,7 +145,7 @@ def load() -> ct.CDLL:
     lib.peps_cz_count.argtypes = [P, ct.POINTER(ct.c_int64)]
     lib.peps_plan_info_get.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                        ct.POINTER(peps_plan_info)]
-    lib.peps_output_ties.argtypes = [P, P, P, P, ct.c_int64, ct.POINTER(ct.c_int64)]
+    lib.peps_output_ties.argtypes = [P, P, P, P, P, ct.c_int64, ct.POINTER(ct.c_int64)]
     lib.peps_plan_steps.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                     ct.POINTER(peps_step_info), ct.c_int64,
                                     ct.POINTER(ct.c_int64)]
@@ -292,18 +292,23 @@ def peps_plan_info_get(h, n: int, opts: peps_opts) -> dict:
     return i.as_dict()
 
 
-def peps_output_ties(h) -> list:
-    """[(cz ordinal, kind, flip)]: kind 1 = the Schmidt bit is `flip`, kind 2 =
-    it is x_q XOR flip for every output bitstring x (q = the CZ's lower-index
-    qubit)."""
+def peps_output_ties(h, with_src: bool = False) -> list:
+    """[(cz ordinal, kind, flip)] (with_src: a fourth item, the source CZ of a
+    linked bit, else -1): kind 1 = the Schmidt bit is `flip`, kind 2 = it is
+    x_q XOR flip for every output bitstring x (q = the CZ's lower-index qubit),
+    kind 3 = it is the bit of CZ `src` (same edge) XOR flip."""
     n = ct.c_int64()
-    _check(load().peps_output_ties(h, None, None, None, 0, ct.byref(n)))
+    _check(load().peps_output_ties(h, None, None, None, None, 0, ct.byref(n)))
     k = n.value
     cz = np.zeros(max(k, 1), dtype=np.uint32)
     kind = np.zeros(max(k, 1), dtype=np.uint8)
     flip = np.zeros(max(k, 1), dtype=np.uint8)
-    _check(load().peps_output_ties(h, cz.ctypes.data, kind.ctypes.data, flip.ctypes.data, k,
-                                   ct.byref(n)))
+    src = np.zeros(max(k, 1), dtype=np.uint32)
+    _check(load().peps_output_ties(h, cz.ctypes.data, kind.ctypes.data, flip.ctypes.data,
+                                   src.ctypes.data, k, ct.byref(n)))
+    if with_src:
+        return [(int(cz[i]), int(kind[i]), int(flip[i]),
+                 -1 if int(src[i]) == 0xFFFFFFFF else int(src[i])) for i in range(k)]
     return [(int(cz[i]), int(kind[i]), int(flip[i])) for i in range(k)]
 
 

@@ -503,12 +503,18 @@ int locate_cz(const peps_ctx *c, std::vector<CzPos> &pos) {
 // bits of consecutive projectors on q are tied (equal or flipped), the first
 // one to the initial |0> and the last one to the measured bit x_q, wherever
 // the runs between them are monomial.  Every term of the bond sum that breaks
-// such a tie is exactly zero: the bit can be held at its tied value.
+// such a tie is exactly zero: the bit can be held at its tied value.  A run
+// of tied projectors that reaches neither end is free as a whole, but where
+// two of its bits belong to one bond (the same edge), that bond index only
+// takes the values in which the later bit equals the earlier one (or its
+// flip): the bond keeps half its values per such linked bit.
 // ---------------------------------------------------------------------------
 struct CzTie {
-  int kind;   // 0 = free, 1 = constant (bit = flip), 2 = output (bit = x_q ^ flip)
+  int kind;   // 0 = free, 1 = constant (bit = flip), 2 = output (bit = x_q ^ flip),
+              // 3 = linked (bit = bit of CZ `src` ^ flip, src on the same edge)
   int q;      // the projector's qubit (the CZ's lower-index qubit)
   int flip;
+  int src = -1;
 };
 
 // 0 = diagonal, 1 = anti-diagonal, -1 = neither (relative tolerance 1e-12)
@@ -533,7 +539,12 @@ void output_ties(const peps_ctx *c, std::vector<CzTie> &ties) {
     cur[q] = {cd(1), cd(0), cd(0), cd(1)};
   };
   int k = 0;
+  std::vector<int> cz_edge;   // per CZ ordinal: its edge (h edges, then v edges)
   for (auto &g : c->gates) {
+    if (g.kind == 1) {
+      const int ra = g.q0 / c->C, ca = g.q0 % c->C;
+      cz_edge.push_back(g.horiz ? edge_h(c, ra, ca) : (int)c->ncz_h.size() + edge_v(c, ra, ca));
+    }
     if (g.kind == 0) {
       const int q = g.q0;
       cd U[4], M[4];
@@ -585,13 +596,36 @@ void output_ties(const peps_ctx *c, std::vector<CzTie> &ties) {
         flip = f < 0 ? -1 : flip ^ f;
       }
     }
+    // free runs: link later bits of one edge to the run's first bit on it
+    int a = 0;
+    while (a < m) {
+      int b = a + 1;
+      std::vector<int> par(1, 0);
+      while (b < m) {
+        const int f = span(E[b - 1].ev + 1, E[b].ev + 1);
+        if (f < 0) break;
+        par.push_back(par.back() ^ f);
+        ++b;
+      }
+      if (ties[E[a].k].kind == 0) {
+        for (int i = a; i < b; ++i)
+          for (int j = a; j < i; ++j)
+            if (cz_edge[E[j].k] == cz_edge[E[i].k] && ties[E[j].k].kind == 0) {
+              CzTie t{3, q, par[i - a] ^ par[j - a]};
+              t.src = E[j].k;
+              ties[E[i].k] = t;
+              break;
+            }
+      }
+      a = b;
+    }
   }
 }
 
 }  // namespace
 
 extern "C" int peps_output_ties(const peps_ctx *c, uint32_t *cz, uint8_t *kind, uint8_t *flip,
-                                int64_t cap, int64_t *n_out) {
+                                uint32_t *src, int64_t cap, int64_t *n_out) {
   if (!c || !n_out) return fail(PEPS_EINVAL, "peps_output_ties: NULL argument");
   if (cap < 0) return fail(PEPS_EINVAL, "peps_output_ties: negative capacity");
   std::vector<CzTie> ties;
@@ -600,10 +634,12 @@ extern "C" int peps_output_ties(const peps_ctx *c, uint32_t *cz, uint8_t *kind, 
   for (size_t j = 0; j < ties.size(); ++j) {
     if (ties[j].kind == 0) continue;
     if (k < cap) {
-      if (!cz || !kind || !flip) return fail(PEPS_EINVAL, "peps_output_ties: NULL output array");
+      if (!cz || !kind || !flip || !src)
+        return fail(PEPS_EINVAL, "peps_output_ties: NULL output array");
       cz[k] = (uint32_t)j;
       kind[k] = (uint8_t)ties[j].kind;
       flip[k] = (uint8_t)ties[j].flip;
+      src[k] = ties[j].src < 0 ? 0xFFFFFFFFu : (uint32_t)ties[j].src;
     }
     ++k;
   }
@@ -723,6 +759,10 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<uint32_t> hv0_h(c->ncz_h.size(), 0u), hv1_h(c->ncz_h.size(), 0u);
   std::vector<uint32_t> hv0_v(c->ncz_v.size(), 0u), hv1_v(c->ncz_v.size(), 0u);
   std::vector<int> hq_h(c->ncz_h.size(), -1), hq_v(c->ncz_v.size(), -1);
+  // linked bits: per edge, (source bit, linked bit) pairs; the linked bit's
+  // value is the source bit's XOR its flip (the flip sits in hv0/hv1)
+  typedef std::vector<std::pair<int, int>> Links;
+  std::vector<Links> lk_h(c->ncz_h.size()), lk_v(c->ncz_v.size());
   if (hold) {
     std::vector<CzTie> ties;
     output_ties(c, ties);
@@ -736,6 +776,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       (p.horiz ? hv0_h[p.edge] : hv0_v[p.edge]) |= v0 << p.bit;
       (p.horiz ? hv1_h[p.edge] : hv1_v[p.edge]) |= v1 << p.bit;
       if (t.kind == 2) (p.horiz ? hq_h[p.edge] : hq_v[p.edge]) = t.q;
+      if (t.kind == 3) {
+        const CzPos &ps = czpos[t.src];
+        if (ps.horiz != p.horiz || ps.edge != p.edge)
+          return fail(PEPS_EINVAL, "internal: linked CZ bits on different edges");
+        Links &lk = p.horiz ? lk_h[p.edge] : lk_v[p.edge];
+        if ((int)lk.size() >= kMaxLinks)
+          return fail(PEPS_EUNSUPPORTED, "more than %d linked bits on one edge", kMaxLinks);
+        lk.push_back({ps.bit, p.bit});
+      }
     }
   }
   // Qubits other than the block's own sites whose output bits select a
@@ -1959,13 +2008,15 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     // qq; only the variant's qubits are set), which select the held values
     auto site_entry = [&](int q, int t, int op, const std::array<int, 4> &roles, uint64_t xv) {
       const int r = q / C, col = q % C;
-      OpBuildEntry e{};
+      OpBuildEntry e;
+      std::memset(&e, 0, sizeof e);   // padding too: entries are compared bytewise
       const int fb = P.final_buf[q];
       e.A = (const float2 *)(base + P.site_buf_off[fb][q]);
       e.lo_off = P.site_elems[q];
       // physical legs: l = h(r, col-1), r = h(r, col), u = v(r-1, col), d = v(r, col)
       int32_t pd[4], prd[4];
       uint32_t pfm[4], pfv[4];
+      const Links *plk[4] = {nullptr, nullptr, nullptr, nullptr};
       auto leg = [&](int a, bool horiz, int rr, int cc) {
         bool inside = horiz ? (cc >= 0 && cc < C - 1) : (rr >= 0 && rr < R - 1);
         uint32_t fm = 0, fv = 0;
@@ -1977,6 +2028,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
             const int hq = horiz ? hq_h[eidx] : hq_v[eidx];
             const bool one = hq >= 0 && ((xv >> hq) & 1ull);
             fv |= one ? (horiz ? hv1_h[eidx] : hv1_v[eidx]) : (horiz ? hv0_h[eidx] : hv0_v[eidx]);
+            plk[a] = horiz ? &lk_h[eidx] : &lk_v[eidx];
           }
         }
         pd[a] = sd[4 * q + a];
@@ -1998,6 +2050,13 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         e.free_mask[ro] = pfm[a];
         e.fixed_val[ro] = pfv[a];
         e.stride[ro] = pst[a];
+        e.n_links[ro] = 0;
+        if (plk[a])
+          for (const auto &pr : *plk[a]) {
+            e.link_src[ro][e.n_links[ro]] = (uint8_t)pr.first;
+            e.link_dst[ro][e.n_links[ro]] = (uint8_t)pr.second;
+            ++e.n_links[ro];
+          }
       }
       e.tau_stride = (int64_t)pd[0] * pd[1] * pd[2] * pd[3];
       e.tau = t;

@@ -198,6 +198,9 @@ struct EvoRef {
 // contracted (K = l u), r and d are new (N = r d).  For the column sweep the
 // roles are the physical legs; a quarter swept from another corner or
 // transposed maps them to other physical legs through `stride`.
+// most linked bits on one leg (bond bits tied to another bit of the same bond)
+constexpr int kMaxLinks = 6;
+
 struct OpBuildEntry {
   const float2 *A;      // site tensor [2][l][r][u][d] (full dims), hi plane
   int64_t lo_off;       // entries from the hi plane to the lo plane
@@ -206,6 +209,9 @@ struct OpBuildEntry {
   uint32_t free_mask[4];// bits of the full index that vary (by role); all ones
                         // = nothing fixed (the index is the full index)
   uint32_t fixed_val[4];// value of the fixed bits (by role)
+  uint8_t n_links[4];   // linked bits by role: bit link_dst = bit link_src XOR
+  uint8_t link_src[4][kMaxLinks];  // (the dst bit's value in fixed_val)
+  uint8_t link_dst[4][kMaxLinks];
   int64_t stride[4];    // element stride of each role's physical leg
   int64_t tau_stride;   // elements per sigma slice
   int32_t tau;

@@ -838,7 +838,9 @@ bool tc_supports(const StepShape &sh, int fmt) {
     return false;
   const int Kr = 2 * sh.K, Nr = 2 * sh.N;
   if (rowb_for(Kr, esz_of(fmt)) == 0) return false;
-  if (sh.M < BM) return false;
+  // fewer rows than a tile: the A box reaches past the tensor's M extent,
+  // where TMA fills zeros, and the epilogue stores live rows only
+  if (sh.M < 32) return false;
   if (!(Nr % 256 == 0 || (Nr % 16 == 0 && Nr <= 256))) return false;
   if (sh.M > 0x7fffffffLL) return false;
   return true;

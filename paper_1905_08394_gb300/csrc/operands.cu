@@ -31,13 +31,23 @@ __device__ __forceinline__ int deposit_bits(uint32_t v, uint32_t mask) {
   return (int)out;
 }
 
+// Full index of restricted value v of a role's leg: the free bits take v's
+// bits, the fixed bits their values, and each linked bit the value of its
+// source bit XOR the flip held in fixed_val.
+__device__ __forceinline__ int expand_leg(const OpBuildEntry &g, int role, int v) {
+  int full = (int)g.fixed_val[role] | deposit_bits(v, g.free_mask[role]);
+  for (int i = 0; i < g.n_links[role]; ++i)
+    full ^= ((full >> g.link_src[role][i]) & 1) << g.link_dst[role][i];
+  return full;
+}
+
 // Element position of E[l][r][u][d] (legs by role; restricted indices mapped
 // back to full ones, then through each role's physical stride).
 __device__ __forceinline__ int64_t pos_E(const OpBuildEntry &g, int l_, int r_, int u_, int d_) {
-  const int l = (int)g.fixed_val[0] | deposit_bits(l_, g.free_mask[0]);
-  const int r = (int)g.fixed_val[1] | deposit_bits(r_, g.free_mask[1]);
-  const int u = (int)g.fixed_val[2] | deposit_bits(u_, g.free_mask[2]);
-  const int d = (int)g.fixed_val[3] | deposit_bits(d_, g.free_mask[3]);
+  const int l = expand_leg(g, 0, l_);
+  const int r = expand_leg(g, 1, r_);
+  const int u = expand_leg(g, 2, u_);
+  const int d = expand_leg(g, 3, d_);
   return (int64_t)g.tau * g.tau_stride + l * g.stride[0] + r * g.stride[1] + u * g.stride[2] +
          d * g.stride[3];
 }
@@ -138,15 +148,15 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
   __shared__ int64_t off_la[kMaxLeg2], off_ra[kMaxLeg2], off_ua[kMaxLeg2];
   __shared__ int64_t off_lb[kMaxLeg2], off_rb[kMaxLeg2], off_db[kMaxLeg2];
   for (int m = threadIdx.x; m < Mid; m += blockDim.x) {
-    mid_a[m] = (int)g.a.fixed_val[3] | deposit_bits(m, g.a.free_mask[3]);
-    mid_b[m] = (int)g.b.fixed_val[2] | deposit_bits(m, g.b.free_mask[2]);
+    mid_a[m] = expand_leg(g.a, 3, m);
+    mid_b[m] = expand_leg(g.b, 2, m);
   }
   const bool tab = La <= kMaxLeg2 && Ra <= kMaxLeg2 && Ua <= kMaxLeg2 && Lb <= kMaxLeg2 &&
                    Rb <= kMaxLeg2 && Db <= kMaxLeg2;
   if (tab) {
     auto fill = [&](int64_t *t, const OpBuildEntry &e, int role, int n) {
       for (int v = threadIdx.x; v < n; v += blockDim.x)
-        t[v] = (int64_t)((int)e.fixed_val[role] | deposit_bits(v, e.free_mask[role])) * e.stride[role];
+        t[v] = (int64_t)expand_leg(e, role, v) * e.stride[role];
     };
     fill(off_la, g.a, 0, La);
     fill(off_ra, g.a, 1, Ra);

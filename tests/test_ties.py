@@ -34,9 +34,13 @@ def cz_lower_qubits(circ):
 
 
 def held_values(ties, lower, x):
-    """{cz ordinal: held Schmidt bit} for output bitstring x."""
+    """{cz ordinal: held Schmidt bit} for output bitstring x (kinds 1 and 2;
+    linked bits, kind 3, have no value of their own)."""
     out = {}
-    for k, kind, flip in ties:
+    for t in ties:
+        k, kind, flip = t[:3]
+        if kind == 3:
+            continue
         out[k] = flip if kind == 1 else ((int(x) >> lower[k]) & 1) ^ flip
     return out
 
@@ -82,15 +86,42 @@ def _circ(name, spec):
     return make_circuit(*spec)
 
 
+def python_links(circ, x):
+    """{(cz, src): flip} for every pair of bits on one edge that the slicing
+    module's rule ties to each other but not to a constant, src the first
+    bit of its class on that edge."""
+    from paper_1905_08394_gb300.slicing import cz_edges
+
+    edges, _ = cz_edges(circ)
+    ncz = len(edges)
+    find = slicing._tie_components(circ, list(range(ncz)), x)
+    const = find(ncz)[0]
+    first = {}
+    out = {}
+    for j in range(ncz):
+        r, p = find(j)
+        if r == const:
+            continue
+        key = (r, edges[j])
+        if key in first:
+            s, ps = first[key]
+            out[(j, s)] = p ^ ps
+        else:
+            first[key] = (j, p)
+    return out
+
+
 @pytest.mark.parametrize("name,spec", CIRCUITS)
 def test_c_ties_equal_the_slicing_rule(name, spec):
     circ = _circ(name, spec)
     h = ctx_for(circ)
-    ties = B.peps_output_ties(h)
+    ties = B.peps_output_ties(h, with_src=True)
     lower = cz_lower_qubits(circ)
     assert len(ties) > 0
+    links = {(k, src): flip for k, kind, flip, src in ties if kind == 3}
     for x in uniform_bitstrings(circ.R * circ.C, 4, 17):
         assert held_values(ties, lower, x) == python_tied_values(circ, int(x))
+        assert links == python_links(circ, int(x))
     B.peps_destroy(h)
 
 
@@ -120,7 +151,7 @@ def test_held_bits_give_the_amplitude_in_the_oracle(spec):
     circ = make_circuit(*spec)
     R, C, n = circ.R, circ.C, circ.R * circ.C
     h = ctx_for(circ)
-    ties = B.peps_output_ties(h)
+    ties = [t for t in B.peps_output_ties(h) if t[1] in (1, 2)]
     B.peps_destroy(h)
     assert ties
     lower = cz_lower_qubits(circ)
@@ -139,11 +170,50 @@ def test_held_bits_give_the_amplitude_in_the_oracle(spec):
         assert abs(other) <= 1e-14
 
 
+@pytest.mark.parametrize("spec", [(4, 4, 24, 3), (3, 4, 40, 2), (4, 4, 32, 11)])
+def test_linked_bits_in_the_oracle(spec):
+    # a linked bit at the other value than its source's (XOR flip) gives
+    # exactly zero; with every held and linked bit restricted, the sum over
+    # the sources' values is the amplitude
+    circ = make_circuit(*spec)
+    R, C, n = circ.R, circ.C, circ.R * circ.C
+    h = ctx_for(circ)
+    ties = B.peps_output_ties(h, with_src=True)
+    B.peps_destroy(h)
+    links = [(k, flip, src) for k, kind, flip, src in ties if kind == 3]
+    assert links, "the circuit has no linked bits"
+    lower = cz_lower_qubits(circ)
+    held = [t for t in ties if t[1] in (1, 2)]
+    srcs = sorted({s for _, _, s in links})
+    sl = [k for k, _, _, _ in held] + srcs + [k for k, _, _ in links]
+    for x in uniform_bitstrings(n, 3, spec[3]):
+        ref = sv.amplitudes(n, circ.gates, [x])[0] if n <= 20 else None
+        hv = held_values(held, lower, x)
+        base = sum(hv[k] << j for j, k in enumerate(sl[:len(held)]))
+        total = 0
+        for t in range(1 << len(srcs)):
+            sid = base
+            sv_ = {s: (t >> i) & 1 for i, s in enumerate(srcs)}
+            for i, s in enumerate(srcs):
+                sid |= sv_[s] << (len(held) + i)
+            for i, (k, flip, s) in enumerate(links):
+                sid |= (sv_[s] ^ flip) << (len(held) + len(srcs) + i)
+            total += op.amplitudes(op.build(R, C, circ.gates, sliced=sl, slice_id=sid), [x])[0]
+            # the first link broken: exactly zero
+            bad = sid ^ (1 << (len(held) + len(srcs)))
+            assert abs(op.amplitudes(op.build(R, C, circ.gates, sliced=sl, slice_id=bad),
+                                     [x])[0]) <= 1e-14
+        full = op.amplitudes(op.build(R, C, circ.gates), [x])[0]
+        assert abs(total - full) <= 1e-12 * max(1.0, abs(full) * 1e3)
+        if ref is not None:
+            assert abs(full - ref) <= 1e-12
+
+
 def test_planted_wrong_flip_is_caught():
     # the same oracle check with one tie's flip inverted must fail
     circ = make_circuit(3, 3, 16, 4)
     h = ctx_for(circ)
-    ties = B.peps_output_ties(h)
+    ties = [t for t in B.peps_output_ties(h) if t[1] in (1, 2)]
     B.peps_destroy(h)
     bad = [(k, kind, flip ^ (1 if i == 0 else 0)) for i, (k, kind, flip) in enumerate(ties)]
     lower = cz_lower_qubits(circ)
@@ -169,9 +239,9 @@ def test_hold_ties_plan_shrinks_the_work():
         o1, k1 = B.make_opts(hold_ties=True, **kw)
         f0 = B.peps_plan_info_get(h, 512, o0)["flops_call"]
         f1 = B.peps_plan_info_get(h, 512, o1)["flops_call"]
-        # the same figure as holding the tied bits at fixed values
+        # the same figure as holding the tied and linked bits at fixed values
         ties = B.peps_output_ties(h)
-        o2, k2 = B.make_opts(fixed_cz=[k for k, _, _ in ties], fixed_s=[0] * len(ties), **kw)
+        o2, k2 = B.make_opts(fixed_cz=[t[0] for t in ties], fixed_s=[0] * len(ties), **kw)
         assert f1 == B.peps_plan_info_get(h, 512, o2)["flops_call"]
         assert f1 < f0
     o, k = B.make_opts(hold_ties=True, sliced_cz=[0], slice_ids=[0])
