@@ -384,6 +384,26 @@ PEPS_API int peps_amplitudes_noalloc(peps_ctx *ctx, const uint64_t *d_bitstrings
 PEPS_API int peps_output_ties(const peps_ctx *ctx, uint32_t *cz, uint8_t *kind, uint8_t *flip,
                               uint32_t *src, int64_t cap, int64_t *n_out);
 
+/* One contraction launch of a timed call: its algorithmic work (real flops,
+ * 8 per complex multiply-add; bytes of the running tensor read and written in
+ * its storage format), its CUDA-event time, the kernel and the plan step. */
+typedef struct {
+    double flops;
+    double bytes;
+    float ms;
+    int32_t tensor_cores;     /* 1: tcgen05 kernel, 0: CUDA-core kernels      */
+    int32_t step;             /* peps_plan_steps index (-1: a whole-sweep
+                                 launch of a small lattice)                   */
+    int32_t pad_;
+} peps_launch_info;
+
+/* The contraction launches of the last amplitude call made with
+ * PEPS_FLAG_TIMING (eager or as a CUDA graph), in launch order: writes at
+ * most `cap` entries (out may be NULL when cap = 0) and the count to *n_out.
+ * Host only; the call has synchronised its stream. */
+PEPS_API int peps_launch_log(const peps_ctx *ctx, peps_launch_info *out, int64_t cap,
+                             int64_t *n_out);
+
 /* Counters of the last amplitude call on this context. */
 PEPS_API int peps_get_stats(const peps_ctx *ctx, peps_stats *out);
 

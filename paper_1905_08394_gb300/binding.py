@@ -54,7 +54,7 @@ EXPORTED = ("peps_create", "peps_destroy", "peps_apply_1q", "peps_apply_cz", "pe
             "peps_workspace_bytes", "peps_amplitudes", "peps_amplitudes_device",
             "peps_get_stats", "peps_cz_count", "peps_last_error", "peps_version",
             "peps_plan_info_get", "peps_amplitudes_noalloc", "peps_output_ties",
-            "peps_plan_steps")
+            "peps_plan_steps", "peps_launch_log")
 
 
 class peps_c128(ct.Structure):
@@ -108,6 +108,14 @@ class peps_step_info(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class peps_launch_info(ct.Structure):
+    _fields_ = [("flops", ct.c_double), ("bytes", ct.c_double), ("ms", ct.c_float),
+                ("tensor_cores", ct.c_int32), ("step", ct.c_int32), ("pad_", ct.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
 class PepsError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"peps error {code}: {msg}")
@@ -146,6 +154,8 @@ def load() -> ct.CDLL:
     lib.peps_plan_info_get.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                        ct.POINTER(peps_plan_info)]
     lib.peps_output_ties.argtypes = [P, P, P, P, P, ct.c_int64, ct.POINTER(ct.c_int64)]
+    lib.peps_launch_log.argtypes = [P, ct.POINTER(peps_launch_info), ct.c_int64,
+                                    ct.POINTER(ct.c_int64)]
     lib.peps_plan_steps.argtypes = [P, ct.c_int64, ct.POINTER(peps_opts),
                                     ct.POINTER(peps_step_info), ct.c_int64,
                                     ct.POINTER(ct.c_int64)]
@@ -318,6 +328,15 @@ def peps_plan_steps(h, n: int, opts: peps_opts) -> list:
     _check(load().peps_plan_steps(h, n, ct.byref(opts), None, 0, ct.byref(k)))
     arr = (peps_step_info * max(k.value, 1))()
     _check(load().peps_plan_steps(h, n, ct.byref(opts), arr, k.value, ct.byref(k)))
+    return [arr[i].as_dict() for i in range(k.value)]
+
+
+def peps_launch_log(h) -> list:
+    """Contraction launches of the last timed call (peps_launch_info as dicts)."""
+    k = ct.c_int64()
+    _check(load().peps_launch_log(h, None, 0, ct.byref(k)))
+    arr = (peps_launch_info * max(k.value, 1))()
+    _check(load().peps_launch_log(h, arr, k.value, ct.byref(k)))
     return [arr[i].as_dict() for i in range(k.value)]
 
 

@@ -189,7 +189,7 @@ struct Plan {
   cudaGraphExec_t graph_exec = nullptr;
   bool graph_timed = false;
   size_t graph_n_timed = 0;
-  std::vector<char> graph_timed_tc;
+  std::vector<int> graph_timed_idx;   // launch index of each timed launch
 
   ~Plan() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -214,6 +214,7 @@ struct peps_ctx {
   bool broken = false;
   std::vector<cudaEvent_t> ev;
   int sm_count = 0;
+  std::vector<peps_launch_info> launch_log;  // contraction launches of the last timed call
   cudaStream_t cap_stream = nullptr;  // records CUDA graphs (the caller's stream
                                       // may be the legacy default stream)
 };
@@ -443,6 +444,16 @@ extern "C" int peps_cz_count(const peps_ctx *c, int64_t *n) {
 
 extern "C" const char *peps_last_error(void) { return g_last_error.c_str(); }
 extern "C" const char *peps_version(void) { return "peps_gb300 0.1 (sm_103a)"; }
+
+extern "C" int peps_launch_log(const peps_ctx *c, peps_launch_info *out, int64_t cap,
+                               int64_t *n_out) {
+  if (!c || !n_out) return fail(PEPS_EINVAL, "peps_launch_log: NULL argument");
+  if (cap < 0 || (cap > 0 && !out)) return fail(PEPS_EINVAL, "peps_launch_log: bad output array");
+  const int64_t n = (int64_t)c->launch_log.size();
+  for (int64_t i = 0; i < std::min(cap, n); ++i) out[i] = c->launch_log[i];
+  *n_out = n;
+  return PEPS_OK;
+}
 
 extern "C" int peps_get_stats(const peps_ctx *c, peps_stats *out) {
   if (!c || !out) return fail(PEPS_EINVAL, "peps_get_stats: NULL argument");
@@ -1354,9 +1365,11 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     }
   }
   int lanes = o.max_lanes > 0 ? o.max_lanes : 16;
-  // square partition: the left quarters of up to this many groups share a launch
+  // square partition: the left quarters of up to this many groups share a
+  // launch, and the members of those groups may share their lanes' launches
   P.glanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(P.n_groups, 1));
-  lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, gs), 1));
+  const int64_t span = (quad && !odd) ? gs * P.glanes : gs;
+  lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, span), 1));
   P.lanes = lanes;
 
   // ---- site tensors ----
@@ -1734,45 +1747,53 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     // group; group slot j's four buffers sit after the member lanes' with the
     // same per-lane layout), then per group the left half F_l and its members
     const int G = P.odd ? 0 : P.n_groups;
-    int bul = 0, bbl = 0;
-    for (int g = 0; g < G; ++g) {
-      const int gslot = g % P.glanes;
-      if (gslot == 0) {
-        const int gc = std::min(P.glanes, G - g);
-        auto gch = [&](int l) { return (int64_t)(g + l); };
-        auto gbit = [&](int l) { return (int64_t)(g + l) * gs; };
-        bul = sweep(ul, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, b); });
-        bbl = sweep(bl, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, 2 + b); });
-      }
-      auto grp = [&](int b) { return grp_buf(gslot, b); };
-      const int64_t chain = g, first = (int64_t)g * gs;
-      const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
-      const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
-      const int rec_l = (int)(chain * NS + P.s_m1);
-      tensor_op(grp(2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
-      {
+    // Groups in chunks of glanes: their left quarters swept together (a lane
+    // per group), each group's left half F_l merged and kept in the group's
+    // buffers; then the chunk's members in chunks of `lanes` bitstrings
+    // (which may span groups): their right quarters swept together, and per
+    // group the merge Y = F_br F_l^T of its members in the chunk with the
+    // dot product against F_ur.
+    for (int g0 = 0; g0 < G; g0 += P.glanes) {
+      const int gc = std::min(P.glanes, G - g0);
+      auto gch = [&](int l) { return (int64_t)(g0 + l); };
+      auto gbit = [&](int l) { return (int64_t)(g0 + l) * gs; };
+      const int bul = sweep(ul, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, b); });
+      const int bbl = sweep(bl, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, 2 + b); });
+      for (int j = 0; j < gc; ++j) {
+        const int64_t chain = g0 + j, first = chain * gs;
+        const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
+        const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
+        const int rec_l = (int)(chain * NS + P.s_m1);
+        tensor_op(grp_buf(j, 2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
         StepItem it{};
         it.op_base = P.op_m1;
         it.in_rec = rec_ul;
         it.out_rec = rec_l;
-        RelItem ri{grp(bul), grp(2 + (bbl ^ 1)), false, first};
+        RelItem ri{grp_buf(j, bul), grp_buf(j, 2 + (bbl ^ 1)), false, first};
         add_step_launch(P.s_m1, {it}, {ri}, 1);
       }
-      // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
-      tensor_op(grp(2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2, P.s_m2);
-      for (int64_t base = 0; base < gs; base += P.lanes) {
-        const int nl = (int)std::min<int64_t>(P.lanes, gs - base);
-        auto mch = [&](int l) { return (int64_t)P.n_groups + first + base + l; };
-        auto mbit = [&](int l) { return first + base + l; };
+      const int64_t m0 = (int64_t)g0 * gs, mcount = (int64_t)gc * gs;
+      for (int64_t base = 0; base < mcount; base += P.lanes) {
+        const int nl = (int)std::min<int64_t>(P.lanes, mcount - base);
+        auto mch = [&](int l) { return (int64_t)P.n_groups + m0 + base + l; };
+        auto mbit = [&](int l) { return m0 + base + l; };
         const int bur = sweep(ur, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, b); });
         const int bbr = sweep(br, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, 2 + b); });
-        {
+        // the chunk's lanes by group: lanes [l0, l1) belong to group g
+        for (int l0 = 0; l0 < nl;) {
+          const int64_t g = (m0 + base + l0) / gs;
+          const int l1 = (int)std::min<int64_t>(nl, (g + 1) * gs - (m0 + base));
+          const int j = (int)(g - g0);
+          const int rec_l = (int)(g * NS + P.s_m1);
+          // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
+          tensor_op(grp_buf(j, 2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2,
+                    P.s_m2);
           std::vector<StepItem> its;
           std::vector<RelItem> rs;
           // on the tensor cores the merge's epilogue forms the dot product
           // with F_ur itself (Y is never stored): its items point at F_ur
           const bool fuse = want_tc && tc_supports(P.steps[P.s_m2], fmt);
-          for (int l = 0; l < nl; ++l) {
+          for (int l = l0; l < l1; ++l) {
             const int64_t ch = mch(l);
             StepItem it{};
             it.op_base = P.op_m2;
@@ -1783,28 +1804,29 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
             its.push_back(it);
             rs.push_back(ri);
           }
-          add_step_launch(P.s_m2, its, rs, nl);
+          add_step_launch(P.s_m2, its, rs, l1 - l0);
           if (fuse) P.launches.back().shape.dot = 1;
+          Launch dl{};
+          dl.kind = 3;
+          dl.aux_off = (int64_t)dots.size();
+          dl.n_aux = l1 - l0;
+          dl.flops = dl.bytes = 0;
+          if (P.launches.back().shape.dot) dl.fused_merge = (int)P.launches.size() - 1;
+          for (int l = l0; l < l1; ++l) {
+            const int64_t ch = mch(l);
+            DotEntry d{};
+            d.Y = (const void *)(REL + lane_buf(l, 2 + (bbr ^ 1)));
+            d.F = (const void *)(REL + lane_buf(l, bur));
+            d.n = ur.batch * ur.rest;
+            d.rec_y = (int)(ch * NS + P.s_m2);
+            d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
+            d.out_index = (int)mbit(l);
+            d.nslots = kDotBlocks;   // fused: set once the merge's tiles are known
+            dots.push_back(d);
+          }
+          P.launches.push_back(dl);
+          l0 = l1;
         }
-        Launch dl{};
-        dl.kind = 3;
-        dl.aux_off = (int64_t)dots.size();
-        dl.n_aux = nl;
-        dl.flops = dl.bytes = 0;
-        if (P.launches.back().shape.dot) dl.fused_merge = (int)P.launches.size() - 1;
-        for (int l = 0; l < nl; ++l) {
-          const int64_t ch = mch(l);
-          DotEntry d{};
-          d.Y = (const void *)(REL + lane_buf(l, 2 + (bbr ^ 1)));
-          d.F = (const void *)(REL + lane_buf(l, bur));
-          d.n = ur.batch * ur.rest;
-          d.rec_y = (int)(ch * NS + P.s_m2);
-          d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
-          d.out_index = (int)mbit(l);
-          d.nslots = kDotBlocks;   // fused: set once the merge's tiles are known
-          dots.push_back(d);
-        }
-        P.launches.push_back(dl);
       }
     }
   } else if (pc > 0) {
@@ -2312,10 +2334,11 @@ static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
 // Enqueue the whole call on `s`: status reset, evolution (if `rebuild`), the
 // prefix-group check, and per slice the operand build, the absorption steps
 // and the final reduction.  With `timing`, CUDA events bracket every
-// contraction launch (their count goes to *n_timed, their kind to timed_tc).
+// contraction launch (their count goes to *n_timed, the index of each timed
+// launch in P.launches to timed_idx).
 static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_t s,
                             bool rebuild, bool timing, peps_stats &S, size_t *n_timed,
-                            std::vector<char> *timed_tc, bool capturing = false) {
+                            std::vector<int> *timed_idx, bool capturing = false) {
   // inside a stream capture an event record becomes a graph node only when
   // recorded as an external event (a plain record orders streams)
   auto record = [&](cudaEvent_t e) {
@@ -2426,7 +2449,7 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
         }
         if (timing) {
           CUDA_TRY(record(c->ev[2 * *n_timed + 1]));
-          timed_tc->push_back(l.tc);
+          timed_idx->push_back((int)(&l - P.launches.data()));
           ++*n_timed;
         }
         S.launches_contract++;
@@ -2457,6 +2480,28 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
     }
   }
   S.launches_total = S.launches_evolve + S.launches_operand + S.launches_contract + S.launches_finalize;
+  return PEPS_OK;
+}
+
+// After a timed call (its stream synchronised): the event time of every
+// contraction launch, summed into S and kept per launch in the context's log.
+static int read_launch_times(peps_ctx *c, Plan &P, size_t n_timed, const std::vector<int> &idx,
+                             peps_stats &S) {
+  c->launch_log.clear();
+  for (size_t i = 0; i < n_timed; ++i) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
+    const Launch &l = P.launches[idx[i]];
+    S.contract_ms += ms;
+    if (l.tc) S.contract_tc_ms += ms;
+    peps_launch_info li{};
+    li.flops = l.flops;
+    li.bytes = l.bytes;
+    li.ms = ms;
+    li.tensor_cores = l.tc ? 1 : 0;
+    li.step = l.step;
+    c->launch_log.push_back(li);
+  }
   return PEPS_OK;
 }
 
@@ -2497,9 +2542,9 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
       CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       peps_stats S2{};
       P.graph_n_timed = 0;
-      P.graph_timed_tc.clear();
+      P.graph_timed_idx.clear();
       int rc = enqueue_sequence(c, P, d_bits_in, cs, true, timing, S2, &P.graph_n_timed,
-                                &P.graph_timed_tc, true);
+                                &P.graph_timed_idx, true);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (rc) {
@@ -2517,12 +2562,8 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
     if (rc) return rc;
     if (timing) {
       CUDA_TRY(cudaStreamSynchronize(s));
-      for (size_t i = 0; i < P.graph_n_timed; ++i) {
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
-        S.contract_ms += ms;
-        if (P.graph_timed_tc[i]) S.contract_tc_ms += ms;
-      }
+      int rc2 = read_launch_times(c, P, P.graph_n_timed, P.graph_timed_idx, S);
+      if (rc2) return rc2;
     }
     c->built_generation = c->generation;
     c->built_ws = P.ws;
@@ -2533,14 +2574,14 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
   const bool rebuild = (P.opts.flags & PEPS_FLAG_REBUILD) || c->built_generation != c->generation ||
                        c->built_ws != P.ws;
   size_t n_timed = 0;
-  std::vector<char> timed_tc;
+  std::vector<int> timed_idx;
   if (timing) {
     size_t nl = 0;
     for (auto &l : P.launches) nl += l.kind == 0;
     int rc = ensure_events(c, 2 * nl * P.slice_list.size());
     if (rc) return rc;
   }
-  int rc = enqueue_sequence(c, P, d_bits_in, s, rebuild, timing, S, &n_timed, &timed_tc);
+  int rc = enqueue_sequence(c, P, d_bits_in, s, rebuild, timing, S, &n_timed, &timed_idx);
   if (rc) return rc;
   if (rebuild) {
     c->built_generation = c->generation;
@@ -2548,12 +2589,8 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
   }
   if (timing) {
     CUDA_TRY(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < n_timed; ++i) {
-      float ms = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]));
-      S.contract_ms += ms;
-      if (timed_tc[i]) S.contract_tc_ms += ms;
-    }
+    rc = read_launch_times(c, P, n_timed, timed_idx, S);
+    if (rc) return rc;
   }
   c->stats = S;
   return PEPS_OK;
