@@ -78,30 +78,33 @@ def golden_check(out, bits, first=0):
             "checked": len(idx), "indices": idx,
             "against": "FP64 oracle values of these bitstrings (tests/golden/oracle_6x6_d32.json)"}
 
-# DRAM bytes (read + write) per k_contract_tc launch of this bench line, from
-# one ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
-# dram__bytes_write.sum) of the small case `bench.py --case group --lanes 8`
-# (one prefix group, 8 lanes per launch, 3.3 GB on the device), scaled to the
-# bench's launches by the units each processes: the left quarters' sweeps run
-# 8 groups per launch here (8x the captured one-group launch), the left-half
-# merges one group each (as captured), the members' steps 64 lanes (8x the
-# captured 8-lane launches); then the mean over the 107 launches of a call.
-# Valid while the kernel's sources hash to the captured version.
-TRAFFIC = {"sources_sha256_16": "15c05225d23e805e",
-           "bytes_per_launch": {"quadrants": 1.3932e9}}
+# DRAM bytes (read + write) of the tensor-core kernel per algorithmic byte,
+# from one ncu capture (gpu__time_duration.sum, dram__bytes_read.sum,
+# dram__bytes_write.sum) of the small case `bench.py --case group --lanes 16`
+# (one prefix group of the batch, 16 lanes per launch, a few GB on the device):
+# the sum over its tensor-core launches of the measured bytes over the sum of
+# their algorithmic bytes (which the case prints).  The bench line's traffic
+# per launch is this ratio times its own algorithmic bytes per launch: the
+# same steps, with more lanes per launch, and traffic in proportion to the
+# lanes.  Valid while the kernel's sources hash to the captured version.
+TRAFFIC = {"sources_sha256_16": "1beea0d02ecb095f", "dram_per_algorithmic_byte": 0.698}
 TRAFFIC_SOURCES = ("contract_tc.cu", "common.h", "format.cuh")
 
 
-def measured_traffic(scheme):
+def measured_traffic(scheme, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch of the tensor-core kernel on this line, or None
+    (no capture for this scheme, or the kernel changed since)."""
     import hashlib
 
+    if scheme != "quadrants" or TRAFFIC["dram_per_algorithmic_byte"] is None:
+        return None
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1905_08394_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     if h.hexdigest()[:16] != TRAFFIC["sources_sha256_16"]:
         return None
-    return TRAFFIC["bytes_per_launch"].get(scheme)
+    return TRAFFIC["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
 
 
 def parse():
@@ -516,7 +519,8 @@ def run_mine(args):
         hbm_view = {"achieved": ach_b, "peak": hbm_peak, "unit": "GB/s", "frac": ach_b / hbm_peak}
         main = tensor_view if bound == "tensor" else hbm_view
         return {"bound": bound, "achieved": main["achieved"], "peak": main["peak"],
-                "unit": main["unit"], "frac": main["frac"], "traffic": measured_traffic(which),
+                "unit": main["unit"], "frac": main["frac"],
+                "traffic": measured_traffic(which, nbytes_alg / nl),
                 "algorithmic_bytes": nbytes_alg / nl,
                 "kernel": "k_contract_tc (tcgen05, fp16 hi/lo, 3 MMAs per k-step)",
                 "peak_source": f"{src}: bf16 dense sustained (fp16 dense rate = bf16 rate), "
@@ -766,13 +770,16 @@ def run_group_case(args):
     sim.apply_circuit(circ)
     kw = dict(precision=args.precision, prefix_cols=3, prefix_group=64, max_lanes=args.lanes,
               scheme="quadrants", hold_ties=args.hold_ties)
-    out = sim.amplitudes(bits[:64], **kw)
+    out = sim.amplitudes(bits[:64], flags=B.PEPS_FLAG_TIMING, **kw)
     check = golden_check(out, bits)
     st = sim.stats()
     o, keep = B.make_opts(**kw)
+    log = B.peps_launch_log(sim.h)
     print(json.dumps({"case": "group", "lanes": args.lanes, "hold_ties": args.hold_ties,
                       "launches": st["launches_total"], "tc_launches": st["launches_contract_tc"],
                       "workspace_bytes": B.peps_workspace_bytes(sim.h, 64, o),
+                      "tc_launch_bytes": [r["bytes"] for r in log if r["tensor_cores"]],
+                      "tc_launch_steps": [r["step"] for r in log if r["tensor_cores"]],
                       "check": check, "finite": bool(np.isfinite(out).all())}), flush=True)
     sim.close()
 
