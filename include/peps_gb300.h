@@ -300,6 +300,16 @@ typedef struct {
     int64_t launches;         /* launches of the step in the call            */
     double flops;             /* algorithmic real flops of the step over the
                                  call (8 per complex multiply-add)           */
+    /* layout of the stored output (row m = b Mr + m_hi (Mr / P) + m_lo,
+     * column n = h' dv + v'): entry ((m_lo dh + h') P + m_hi) dv + v' of
+     * batch slice b, or with open_leg = 1 entry (b dv + v') (Mr dh) +
+     * (m_lo dh + h') P + m_hi (v' joins the batch)                         */
+    int64_t P;                /* rotated row legs (moved next to v')         */
+    int64_t Mr;               /* rows per batch slice (M when no batch)      */
+    int32_t dv, dh;           /* dims of v' and of the h' legs               */
+    int32_t open_leg;         /* 1: v' is an open leg stored into the batch  */
+    int32_t fused_dot;        /* 1: the output is only dotted with a stored
+                                 tensor in the epilogue (never written)      */
 } peps_step_info;
 
 /* The steps of the plan of an amplitude call, in sweep order: writes at most

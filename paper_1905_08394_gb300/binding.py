@@ -102,7 +102,9 @@ class peps_plan_info(ct.Structure):
 class peps_step_info(ct.Structure):
     _fields_ = [("M", ct.c_int64), ("K", ct.c_int32), ("N", ct.c_int32),
                 ("sites", ct.c_int32), ("variants", ct.c_int32), ("tensor_cores", ct.c_int32),
-                ("part", ct.c_int32), ("launches", ct.c_int64), ("flops", ct.c_double)]
+                ("part", ct.c_int32), ("launches", ct.c_int64), ("flops", ct.c_double),
+                ("P", ct.c_int64), ("Mr", ct.c_int64), ("dv", ct.c_int32), ("dh", ct.c_int32),
+                ("open_leg", ct.c_int32), ("fused_dot", ct.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

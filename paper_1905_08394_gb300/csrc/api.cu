@@ -2255,6 +2255,12 @@ extern "C" int peps_plan_steps(const peps_ctx *c, int64_t n, const peps_opts *op
     i.N = sh.N;
     i.sites = sh.nq;
     i.variants = step_variants(sh);
+    i.P = sh.P;
+    i.Mr = sh.Mr > 0 ? sh.Mr : sh.M;
+    i.dv = sh.dv_out;
+    i.dh = sh.dh_out;
+    i.open_leg = sh.vb;
+    i.fused_dot = sh.dot;
     i.tensor_cores = (!P.small && want_tc && tc_supports(sh, P.fmt)) ? 1 : 0;
     i.part = -1;
     if (P.scheme == PEPS_SCHEME_QUADRANTS) {
@@ -2277,6 +2283,7 @@ extern "C" int peps_plan_steps(const peps_ctx *c, int64_t n, const peps_opts *op
     if (l.step >= 0 && l.step < P.n_steps) {
       out[l.step].launches += k;
       out[l.step].flops += (double)k * l.flops;
+      if (l.shape.dot) out[l.step].fused_dot = 1;
     }
   }
   for (int64_t s = 0; s < std::min<int64_t>(cap, P.n_steps); ++s) steps[s] = out[s];

@@ -324,3 +324,22 @@ def test_small_lattices_plan_one_contraction_launch():
     o, k = B.make_opts(precision="fp32")
     assert B.peps_plan_info_get(h, 64, o)["n_launches"] > 1
     B.peps_destroy(h)
+
+
+def test_plan_steps_report_a_consistent_output_layout():
+    # every step's stored output: N = dh dv, M = batch x Mr, Mr = P x (rows
+    # kept in place); the 6x6 (1+32+1) square partition with held and linked
+    # bits, both contraction orders
+    c, h = make(6, 6, 32, 4)
+    for scheme in ("quadrants", "columns"):
+        o, k = B.make_opts(precision="fp16x3", scheme=scheme, prefix_cols=3, prefix_group=64,
+                           max_lanes=64, hold_ties=True)
+        steps = B.peps_plan_steps(h, 512, o)
+        assert steps
+        for s in steps:
+            assert s["dh"] * s["dv"] == s["N"], s
+            assert s["M"] % s["Mr"] == 0 and s["Mr"] % s["P"] == 0, s
+            assert s["open_leg"] in (0, 1) and s["fused_dot"] in (0, 1)
+        # on the tensor cores the last merge forms the dot product in its epilogue
+        assert [s["fused_dot"] for s in steps] == [0] * (len(steps) - 1) + [int(scheme == "quadrants")]
+    B.peps_destroy(h)
