@@ -55,6 +55,28 @@ template <> struct FormTraits<FMT_BF16X2> { static constexpr int NP = 2, ESZ = 2
 template <> struct FormTraits<FMT_FP16X2> { static constexpr int NP = 2, ESZ = 2, KIND = 0, AB = 0; };
 template <> struct FormTraits<FMT_TF32>   { static constexpr int NP = 1, ESZ = 4, KIND = 1, AB = 2; };
 
+// x / d and x % d for a divisor fixed per launch (d > 0, x >= 0): a shift and
+// a mask when d is a power of two (every dimension made of CZ bonds), a
+// division otherwise (bonds of general two-qubit gates of Schmidt rank 3).
+struct Div {
+  int64_t d;
+  int32_t s;   // log2(d), or -1
+  int32_t pad_;
+  __device__ __forceinline__ int64_t q(int64_t x) const { return s >= 0 ? (x >> s) : x / d; }
+  __device__ __forceinline__ int64_t r(int64_t x) const {
+    return s >= 0 ? (x & (d - 1)) : x % d;
+  }
+};
+inline Div make_div(int64_t d) {
+  Div v{d > 0 ? d : 1, -1, 0};
+  if ((v.d & (v.d - 1)) == 0) {
+    int k = 0;
+    while (((int64_t)1 << k) < v.d) ++k;
+    v.s = k;
+  }
+  return v;
+}
+
 struct __align__(64) TcParams {
   CUtensorMap mapA;        // {k, m, plane, lane}; m_hi-major steps: {k, m_hi, m_lo, b, plane/lane}
   CUtensorMap mapB[2];     // [plane] {k, n, operand variant}
@@ -85,6 +107,13 @@ struct __align__(64) TcParams {
   int64_t mlo;  // m_hi-major: Mr / P
   int64_t watchdog_ns;
   double2 *dot_partials;   // sh.dot: [item][tiles_per_item * CG * EPI_WARPS]
+  int blocked;  // 1: CTA pair c takes the consecutive tiles [c per, (c + 1) per)
+                // (an item's tiles in a row, so its variant, scale and
+                // addresses are set up once); 0: tiles c, c + pairs, ...
+  // divisors of the tile and store index arithmetic
+  Div d_tpi, d_tn;             // tiles per item, column tiles
+  Div d_hper, d_lper, d_ph;    // m_hi-major tiles: P / ph, (Mr / P) / lh, ph
+  Div d_Mr, d_Mlo, d_dv, d_dh; // output rows per batch slice, Mr / P, dim(v'), dim(h')
 };
 
 // ---------------------------------------------------------------------------
@@ -436,6 +465,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
   const int mgroups = p.tiles_m / CG;               // CG == 2 only when tiles_m is even
   const int tiles_per_item = mgroups * p.tiles_n;  // tiles of the pair
   const int total = p.n_items * tiles_per_item;
+  // this pair's tiles: a consecutive range (blocked) or every ncl-th
+  const int per = p.blocked ? (total + ncl - 1) / ncl : 1;
+  const int t_first = p.blocked ? cid * per : cid;
+  const int t_end = p.blocked ? (t_first + per < total ? t_first + per : total) : total;
+  const int t_step = p.blocked ? 1 : ncl;
   // a row of A holds 2K real entries of ESZ bytes; one stage covers ROWB bytes
   const int kb_count = (2 * p.sh.K * T::ESZ) / ROWB;
   Watch w{abort_flag, p.st, globaltimer() + (uint64_t)p.watchdog_ns, p.sh.q, CG};
@@ -447,24 +481,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     // ---------------- TMA producer (both CTAs) ----------------
     if (lane == 0) {
       uint32_t it = 0;
-      for (int t = cid; t < total; t += ncl) {
-        const int item = t / tiles_per_item;
+      int cached_item = -1, tau = 0, a_lane = 0;
+      for (int t = t_first; t < t_end; t += t_step) {
+        const int item = (int)p.d_tpi.q(t);
         const int rem = t - item * tiles_per_item;
         int mg, nt;
-        tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
+        if (p.gm <= 1) {
+          mg = (int)p.d_tn.q(rem);
+          nt = rem - mg * p.tiles_n;
+        } else {
+          tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
+        }
         const int mt = mg * CG + (int)rank;
-        const StepItem &si = p.items[item];
-        const int tau = block_variant(*si.bits, p.sh);
+        if (item != cached_item) {
+          cached_item = item;
+          const StepItem &si = p.items[item];
+          tau = block_variant(*si.bits, p.sh);
+          a_lane = si.a_lane;
+        }
         // m_hi-major: tile mt is rows m_hi = hb0 .. hb0+ph-1, m_lo = mlo_t ..
         // mlo_t+lh-1 at b_t
         int64_t b_t = 0, mlo_t = 0;
         int hb0 = 0;
         if (p.mhi) {
-          const int64_t hper = p.sh.P / p.ph, lper = p.mlo / p.lh;
-          const int64_t rest = mt / hper;
-          hb0 = (int)(mt - rest * hper) * p.ph;
-          b_t = rest / lper;
-          mlo_t = (rest - b_t * lper) * p.lh;
+          const int64_t rest = p.d_hper.q(mt);
+          hb0 = (int)p.d_hper.r(mt) * p.ph;
+          b_t = p.d_lper.q(rest);
+          mlo_t = p.d_lper.r(rest) * p.lh;
         }
         bool ok = true;
         for (int kb = 0; kb < kb_count; ++kb, ++it) {
@@ -478,9 +521,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
             for (int pl = 0; pl < NP; ++pl) {
               if (p.mhi)
                 tma_load_5d(st + pl * a_bytes, &p.mapA, &full[s], k0, hb0, (int)mlo_t, (int)b_t,
-                            si.a_lane * p.lp_mul + pl);
+                            a_lane * p.lp_mul + pl);
               else
-                tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, si.a_lane);
+                tma_load_4d(st + pl * a_bytes, &p.mapA, &full[s], k0, mt * BM, pl, a_lane);
               tma_load_3d(st + NP * a_bytes + pl * b_bytes, &p.mapB[pl], &full[s], k0,
                           nt * BN, tau);
             }
@@ -490,10 +533,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
             for (int pl = 0; pl < NP; ++pl) {
               if (p.mhi)
                 tma_load_5d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0, hb0,
-                                (int)mlo_t, (int)b_t, si.a_lane * p.lp_mul + pl);
+                                (int)mlo_t, (int)b_t, a_lane * p.lp_mul + pl);
               else
                 tma_load_4d_cg2(st + pl * a_bytes, &p.mapA, full0 + (uint32_t)s * 8u, k0,
-                                mt * BM, pl, si.a_lane);
+                                mt * BM, pl, a_lane);
               tma_load_3d_cg2(st + NP * a_bytes + pl * b_bytes, &p.mapB[pl],
                               full0 + (uint32_t)s * 8u, k0, nt * BN + (int)rank * BNL, tau);
             }
@@ -543,7 +586,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((BM * CG) >> 4) << 24);
       uint32_t it = 0, local = 0;
       const int KSP = p.ksplit, NB = p.nbuf;
-      for (int t = cid; t < total; t += ncl, ++local) {
+      for (int t = t_first; t < t_end; t += t_step, ++local) {
         const int acc = NB == 2 ? (int)(local & 1) : 0;
         const uint32_t aph = NB == 2 ? (local >> 1) & 1u : local & 1u;
         if (!mbar_wait(&tempty[acc], aph ^ 1u, w)) break;
@@ -613,11 +656,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     const StepItem *si = nullptr;
     float sc = 1.f;
     int x = 0, s_in = 0;
-    for (int t = cid; t < total; t += ncl, ++local) {
-      const int item = t / tiles_per_item;
+    for (int t = t_first; t < t_end; t += t_step, ++local) {
+      const int item = (int)p.d_tpi.q(t);
       const int rem = t - item * tiles_per_item;
       int mg, nt;
-      tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
+      if (p.gm <= 1) {
+        mg = (int)p.d_tn.q(rem);
+        nt = rem - mg * p.tiles_n;
+      } else {
+        tile_of(rem, mgroups, p.tiles_n, p.gm, mg, nt);
+      }
       const int mt = mg * CG + (int)rank;
       if (item != cached_item) {
         cached_item = item;
@@ -641,19 +689,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       bool live;
       if (p.mhi) {
         // row = l ph + h: m_hi = hb0 + h, m_lo = mlo_t + l (the tile of the producer)
-        const int64_t hper = P / p.ph, lper = Mlo / p.lh, rest = mt / hper;
-        m_hi = (mt - rest * hper) * p.ph + row % p.ph;
-        b = rest / lper;
-        m_lo = (rest - b * lper) * p.lh + row / p.ph;
+        const int64_t rest = p.d_hper.q(mt);
+        m_hi = p.d_hper.r(mt) * p.ph + p.d_ph.r(row);
+        b = p.d_lper.q(rest);
+        m_lo = p.d_lper.r(rest) * p.lh + p.d_ph.q(row);
         live = true;
       } else {
         const int64_t m = (int64_t)mt * BM + row;
         live = m < M;
         // row m = b * Mr + m_r (b: the batch of open legs, when there is one)
-        b = live ? m / Mr : 0;
+        b = live ? p.d_Mr.q(m) : 0;
         const int64_t mr = live ? m - b * Mr : 0;
-        m_hi = mr / Mlo;
-        m_lo = mr % Mlo;
+        m_hi = p.d_Mlo.q(mr);
+        m_lo = p.d_Mlo.r(mr);
       }
       float vmax = 0.f;
       const int KSP = p.nacc;   // K segments, then the correction accumulator
@@ -709,10 +757,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           if (vec) {
             int64_t dest0;
             if (nvs) {
-              const int vv = nc0 / dh, hh = nc0 - vv * dh;   // P = 1: m_hi = 0
+              const int vv = (int)p.d_dh.q(nc0), hh = nc0 - vv * dh;   // P = 1: m_hi = 0
               dest0 = (b * dv + vv) * Mrdh + row_base + hh;
             } else {
-              const int hh = nc0 / dv, vv = nc0 - hh * dv;
+              const int hh = (int)p.d_dv.q(nc0), vv = nc0 - hh * dv;
               dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
             }
             vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
@@ -720,7 +768,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
             // open-leg store with dv' a multiple of 8: the chunk's 8 columns
             // share h' and are 8 consecutive v', each a whole batch slice
             // (Mr dh' entries) apart; a warp's rows are consecutive m_hi
-            const int hh = nc0 / dv, vv0 = nc0 - hh * dv;
+            const int hh = (int)p.d_dv.q(nc0), vv0 = nc0 - hh * dv;
             const int64_t base = (b * dv + vv0) * Mrdh + (row_base + hh) * P + m_hi;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -732,7 +780,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
               const int nc = nc0 + j;
-              const int hh = nvs ? nc % dh : nc / dv, vv = nvs ? nc / dh : nc % dv;
+              const int hh = (int)(nvs ? p.d_dh.r(nc) : p.d_dv.q(nc));
+              const int vv = (int)(nvs ? p.d_dh.q(nc) : p.d_dv.r(nc));
               const int64_t rot = (row_base + hh) * P + m_hi;
               const int64_t dest = vbm ? (b * dv + vv) * Mrdh + rot : bofs + rot * dv + vv;
               float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
@@ -986,6 +1035,21 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   {
     const int mgroups = d->prm.tiles_m / d->cg;
     d->prm.gm = (d->prm.tiles_n >= 32 && mgroups >= 16) ? 8 : 1;
+    // outside the grouped order a pair walks consecutive tiles
+    d->prm.blocked = d->prm.gm == 1 ? 1 : 0;
+    d->prm.d_tpi = make_div((int64_t)mgroups * d->prm.tiles_n);
+    d->prm.d_tn = make_div(d->prm.tiles_n);
+  }
+  {
+    const int64_t Mr = sh.Mr > 0 ? sh.Mr : sh.M, P = sh.P > 0 ? sh.P : 1;
+    d->prm.d_Mr = make_div(Mr);
+    d->prm.d_Mlo = make_div(Mr / P);
+    d->prm.d_dv = make_div(sh.dv_out);
+    d->prm.d_dh = make_div(sh.dh_out);
+    const int ph = d->prm.mhi ? d->prm.ph : 1, lh = d->prm.mhi ? d->prm.lh : 1;
+    d->prm.d_ph = make_div(ph);
+    d->prm.d_hper = make_div(d->prm.mhi ? P / ph : 1);
+    d->prm.d_lper = make_div(d->prm.mhi ? d->prm.mlo / lh : 1);
   }
   d->prm.ksplit = KS;
   d->prm.csep = CS;
