@@ -409,11 +409,11 @@ def run_mine(args):
         best = autotune.tune(sim, d_bits, d_out, kw, cands=cands, repeats=1, stream=stream,
                              log=log.append)
         if pg:   # rank 0's choice everywhere
-            t = torch.tensor([best["max_lanes"], best["tc_kchunk"], best["tc_cluster"]],
-                             device=dev)
+            t = torch.tensor([best["max_lanes"], best["tc_kchunk"], best["tc_cluster"],
+                              best.get("tc_epi", 0)], device=dev)
             torch.distributed.broadcast(t, 0, group=pg)
             best = {"scheme": scheme, "max_lanes": int(t[0]), "tc_kchunk": int(t[1]),
-                    "tc_cluster": int(t[2])}
+                    "tc_cluster": int(t[2]), "tc_epi": int(t[3])}
         kw.update(best)
         tuned = dict(tuned or {}, tile=best, tile_trials=log)
     # every step replays the call's CUDA graph (circuit evolution included),
@@ -611,6 +611,7 @@ def run_mine(args):
                 "tuning": {"precision": args.precision, "lanes": kw.get("max_lanes", args.lanes),
                            "scheme": scheme, "hold_ties": args.hold_ties,
                            "tc_kchunk": kw.get("tc_kchunk", 0), "tc_cluster": kw.get("tc_cluster", 0),
+                           "tc_epi": kw.get("tc_epi", 0),
                            "prefix_reuse": "columns 0-2 per group of 64", "autotune": tuned},
                 "rel_err": check["rel_err"] if check else None,
                 "rel_err_ok": check["rel_err_ok"] if check else None, "check": check,

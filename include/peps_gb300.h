@@ -183,6 +183,12 @@ typedef struct {
     int32_t scheme;           /* PEPS_SCHEME_*: the contraction scheme        */
     uint64_t measured_mask;   /* with PEPS_FLAG_MARGINALS: bit q set = qubit q
                                  is measured                                 */
+    int32_t tc_epi;           /* tensor-core tuning: epilogue warps per CTA, 4
+                                 (one per accumulator lane quadrant) or 8 (two,
+                                 each draining half of a tile's columns); 0 =
+                                 8 on steps of at most 16 K stages per tile,
+                                 where the epilogue outlasts the MMAs, else 4 */
+    int32_t pad_;
 } peps_opts;
 
 /* Contraction schemes (supplementary, "exact contraction"):

@@ -29,11 +29,12 @@ def signature(sim, n: int, kw: dict) -> str:
     return json.dumps({"R": sim.R, "C": sim.C, "dims": dims, "n": n, **rest}, sort_keys=True)
 
 
-def candidates(lanes=(8, 16, 32), kchunk=(128, 64), cluster=(1, 2), schemes=("columns",)):
+def candidates(lanes=(8, 16, 32), kchunk=(128, 64), cluster=(1, 2), schemes=("columns",),
+               epi=(0,)):
     """The product of the given choices; pass schemes=("columns", "quadrants")
     on an even lattice to let the contraction order be tuned as well."""
-    for sc, l, k, c in itertools.product(schemes, lanes, kchunk, cluster):
-        yield {"scheme": sc, "max_lanes": l, "tc_kchunk": k, "tc_cluster": c}
+    for sc, l, k, c, e in itertools.product(schemes, lanes, kchunk, cluster, epi):
+        yield {"scheme": sc, "max_lanes": l, "tc_kchunk": k, "tc_cluster": c, "tc_epi": e}
 
 
 def tune(sim, d_bits, d_out, kw: dict, cands=None, repeats: int = 2, cache: str = DEFAULT_CACHE,

@@ -71,7 +71,7 @@ class peps_opts(ct.Structure):
                 ("fixed_cz", ct.POINTER(ct.c_uint32)), ("fixed_s", ct.POINTER(ct.c_uint8)),
                 ("tc_kchunk", ct.c_int32), ("tc_cluster", ct.c_int32),
                 ("fuse_rows", ct.c_int32), ("scheme", ct.c_int32),
-                ("measured_mask", ct.c_uint64)]
+                ("measured_mask", ct.c_uint64), ("tc_epi", ct.c_int32), ("pad_", ct.c_int32)]
 
 
 class peps_stats(ct.Structure):
@@ -222,6 +222,7 @@ def peps_cz_count(h) -> int:
 def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_group: int = 0,
               max_lanes: int = 0, sliced_cz=None, slice_ids=None, watchdog_ns: int = 0,
               fixed_cz=None, fixed_s=None, tc_kchunk: int = 0, tc_cluster: int = 0,
+              tc_epi: int = 0,
               fuse_rows: int = 0, scheme="columns", tc_ksplit: int = 0,
               measured_mask=None, hold_ties: bool = False):
     """peps_opts plus the arrays it points to (keep both alive).  With
@@ -248,6 +249,7 @@ def make_opts(precision="fp32", flags: int = 0, prefix_cols: int = 0, prefix_gro
     o.watchdog_ns = watchdog_ns
     o.tc_kchunk = tc_kchunk
     o.tc_cluster = tc_cluster
+    o.tc_epi = tc_epi
     o.fuse_rows = fuse_rows
     o.tc_ksplit = tc_ksplit
     if measured_mask is not None:

@@ -75,7 +75,8 @@ struct Launch {
   double flops, bytes;
   bool lower = false;   // odd side: a launch of the lower half (bl, br -> F_b)
   bool small = false;   // kind 0: every step of every bitstring in one launch
-  int step = -1;        // kind 0: the plan step it runs (-1: the whole sweep)
+  int step = -1;        // kind 0: the plan step it runs (-1: the whole sweep); kind 2:
+                        // the merge step whose operands it builds
   int fused_merge = -1; // kind 3: index of the merge launch whose epilogue wrote
                         // the dot's partial sums (-1: the separate dot kernel)
 };
@@ -145,6 +146,9 @@ struct Plan {
   double flops_lower = 0;       // per slice
   int s_m1 = -1, s_m2 = -1;     // merge steps F_l = F_ul F_bl, Y = F_br F_l^T
   int op_m1 = -1, op_m2 = -1;
+  int merge_slots = 1;          // operands per merge step: even square partition,
+                                // one per group of a chunk (glanes), so that the
+                                // chunk's merges share one launch
   int n_site_ops = 0;           // ops rebuilt from the site tensors per slice
   int64_t max_kn_merge = 0;
   size_t off_tops = 0, off_dots = 0, off_partials = 0;
@@ -669,6 +673,13 @@ static bool opts_equal(const peps_opts &a, const peps_opts &b) {
 }
 
 // Build (or size) the plan.  With ws == nullptr only sizes are computed.
+// Operand slots of step s: the bitstring variants of a site step, or the
+// per-group slots of a square-partition merge.
+static int op_slots(const Plan &P, int s) {
+  if (P.scheme == PEPS_SCHEME_QUADRANTS && (s == P.s_m1 || s == P.s_m2)) return P.merge_slots;
+  return step_variants(P.steps[s]);
+}
+
 static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws,
                       size_t ws_bytes, const uint64_t *bits_dev, bool host_bits, Plan &P) {
   const int R = c->R, C = c->C, NQ = c->n;
@@ -705,8 +716,8 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     return fail(PEPS_EINVAL, "with the square partition prefix_cols must be 0 or C/2");
   if (odd && o.prefix_cols != 0)
     return fail(PEPS_EINVAL, "the odd-side partition takes no prefix groups");
-  if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster))
-    return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128 and tc_cluster 0, 1 or 2");
+  if (!tc_tuning_valid(o.tc_kchunk, o.tc_cluster, o.tc_epi))
+    return fail(PEPS_EINVAL, "tc_kchunk must be 0, 64 or 128, tc_cluster 0, 1 or 2, tc_epi 0, 4 or 8");
   if (o.n_fixed > 0 && (!o.fixed_cz || !o.fixed_s)) return fail(PEPS_EINVAL, "fixed_cz / fixed_s is NULL");
 
   P.generation = c->generation;
@@ -1266,11 +1277,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         if ((rc = add_merge(sh))) return rc;
       }
     }
-    P.n_site_ops = n_ops_total;
-    P.op_m1 = n_ops_total++;
-    P.op_m2 = n_ops_total++;
-    P.step_opbase[P.s_m1] = P.op_m1;
-    P.step_opbase[P.s_m2] = P.op_m2;
+    P.n_site_ops = n_ops_total;   // merge operands: placed once glanes is known
   }
   if (!quad) P.n_site_ops = n_ops_total;
   // tensor-core accumulation.  An FP32 accumulator that the tensor core adds
@@ -1368,6 +1375,16 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   // square partition: the left quarters of up to this many groups share a
   // launch, and the members of those groups may share their lanes' launches
   P.glanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(P.n_groups, 1));
+  if (quad) {
+    // the merge operands: one slot per group of a chunk (even side), one
+    // otherwise
+    P.merge_slots = (!odd && P.n_groups > 0) ? P.glanes : 1;
+    P.op_m1 = n_ops_total;
+    P.op_m2 = n_ops_total + P.merge_slots;
+    n_ops_total += 2 * P.merge_slots;
+    P.step_opbase[P.s_m1] = P.op_m1;
+    P.step_opbase[P.s_m2] = P.op_m2;
+  }
   const int64_t span = (quad && !odd) ? gs * P.glanes : gs;
   lanes = (int)std::min<int64_t>(lanes, std::max<int64_t>(std::min<int64_t>(n, span), 1));
   P.lanes = lanes;
@@ -1554,7 +1571,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     }  // nq == 0: a merge operand, built from a stored tensor during the call
     // a tensor-core merge builds its planes straight from the stored tensor
     const bool merge_tc = sh.nq == 0 && want_tc && tc_supports(sh, fmt);
-    for (int t = 0; t < step_variants(sh); ++t) {
+    for (int t = 0; t < op_slots(P, s); ++t) {
       const int op = P.step_opbase[s] + t;
       P.ec_off[op] = 0;
       if (!merge_tc) {
@@ -1670,8 +1687,20 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
       t.rec = rec;
       t.op = op;
       t.target = scale_target(fmt);
+      // operands of the same merge step for consecutive slots, one after the
+      // other, share a launch
+      if (!P.launches.empty()) {
+        Launch &pl = P.launches.back();
+        if (pl.kind == 2 && pl.step == consumer && pl.op + pl.n_aux == op &&
+            pl.aux_off + pl.n_aux == (int64_t)tops.size() && pl.kn == K * N) {
+          tops.push_back(t);
+          ++pl.n_aux;
+          return;
+        }
+      }
       Launch ln{};
       ln.kind = 2;
+      ln.step = consumer;
       ln.aux_off = (int64_t)tops.size();
       ln.n_aux = 1;
       ln.op = op;
@@ -1743,90 +1772,92 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         P.launches.push_back(dl);
       }
     }
-    // the left quarters of up to `lanes` groups in one sweep each (a lane per
-    // group; group slot j's four buffers sit after the member lanes' with the
-    // same per-lane layout), then per group the left half F_l and its members
+    // Groups in chunks of glanes (a lane per group; group slot j's four
+    // buffers sit after the member lanes' with the same per-lane layout):
+    // their left quarters swept together; F_bl of every group turned into its
+    // merge operand (slot op_m1 + j); the groups' left halves
+    // F_l = F_ul F_bl^T merged in one launch and kept in the groups' buffers,
+    // each then turned into the group's operand of the last merge (slot
+    // op_m2 + j).  Then the chunk's members in chunks of `lanes` bitstrings
+    // (which may span groups): their right quarters swept together, and one
+    // launch of the merges Y = F_br F_l^T of all of them, each against its
+    // group's operand, with the dot product against F_ur.
     const int G = P.odd ? 0 : P.n_groups;
-    // Groups in chunks of glanes: their left quarters swept together (a lane
-    // per group), each group's left half F_l merged and kept in the group's
-    // buffers; then the chunk's members in chunks of `lanes` bitstrings
-    // (which may span groups): their right quarters swept together, and per
-    // group the merge Y = F_br F_l^T of its members in the chunk with the
-    // dot product against F_ur.
     for (int g0 = 0; g0 < G; g0 += P.glanes) {
       const int gc = std::min(P.glanes, G - g0);
       auto gch = [&](int l) { return (int64_t)(g0 + l); };
       auto gbit = [&](int l) { return (int64_t)(g0 + l) * gs; };
       const int bul = sweep(ul, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, b); });
       const int bbl = sweep(bl, gc, gch, gbit, [&](int l, int b) { return grp_buf(l, 2 + b); });
+      std::vector<StepItem> mits;
+      std::vector<RelItem> mrs;
       for (int j = 0; j < gc; ++j) {
         const int64_t chain = g0 + j, first = chain * gs;
         const int rec_ul = (int)(chain * NS + ul.first + ul.count - 1);
         const int rec_bl = (int)(chain * NS + bl.first + bl.count - 1);
         const int rec_l = (int)(chain * NS + P.s_m1);
-        tensor_op(grp_buf(j, 2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1, P.s_m1);
+        tensor_op(grp_buf(j, 2 + bbl), bl.rest, bl.batch, bl.rest, rec_bl, P.op_m1 + j, P.s_m1);
         StepItem it{};
-        it.op_base = P.op_m1;
+        it.op_base = P.op_m1 + j;
+        it.b_slot = j;
         it.in_rec = rec_ul;
         it.out_rec = rec_l;
-        RelItem ri{grp_buf(j, bul), grp_buf(j, 2 + (bbl ^ 1)), false, first};
-        add_step_launch(P.s_m1, {it}, {ri}, 1);
+        mits.push_back(it);
+        mrs.push_back(RelItem{grp_buf(j, bul), grp_buf(j, 2 + (bbl ^ 1)), false, first});
+      }
+      add_step_launch(P.s_m1, mits, mrs, gc);
+      for (int j = 0; j < gc; ++j) {
+        // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
+        const int rec_l = (int)((g0 + j) * NS + P.s_m1);
+        tensor_op(grp_buf(j, 2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2 + j,
+                  P.s_m2);
       }
       const int64_t m0 = (int64_t)g0 * gs, mcount = (int64_t)gc * gs;
+      // on the tensor cores the merge's epilogue forms the dot product with
+      // F_ur itself (Y is never stored): its items point at F_ur
+      const bool fuse = want_tc && tc_supports(P.steps[P.s_m2], fmt);
       for (int64_t base = 0; base < mcount; base += P.lanes) {
         const int nl = (int)std::min<int64_t>(P.lanes, mcount - base);
         auto mch = [&](int l) { return (int64_t)P.n_groups + m0 + base + l; };
         auto mbit = [&](int l) { return m0 + base + l; };
         const int bur = sweep(ur, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, b); });
         const int bbr = sweep(br, nl, mch, mbit, [&](int l, int b) { return lane_buf(l, 2 + b); });
-        // the chunk's lanes by group: lanes [l0, l1) belong to group g
-        for (int l0 = 0; l0 < nl;) {
-          const int64_t g = (m0 + base + l0) / gs;
-          const int l1 = (int)std::min<int64_t>(nl, (g + 1) * gs - (m0 + base));
-          const int j = (int)(g - g0);
-          const int rec_l = (int)(g * NS + P.s_m1);
-          // F_l = [a][b] (N of the first merge = bl.batch per row); operand Ec[b][a]
-          tensor_op(grp_buf(j, 2 + (bbl ^ 1)), bl.batch, ul.batch, bl.batch, rec_l, P.op_m2,
-                    P.s_m2);
-          std::vector<StepItem> its;
-          std::vector<RelItem> rs;
-          // on the tensor cores the merge's epilogue forms the dot product
-          // with F_ur itself (Y is never stored): its items point at F_ur
-          const bool fuse = want_tc && tc_supports(P.steps[P.s_m2], fmt);
-          for (int l = l0; l < l1; ++l) {
-            const int64_t ch = mch(l);
-            StepItem it{};
-            it.op_base = P.op_m2;
-            it.in_rec = (int)(ch * NS + br.first + br.count - 1);
-            it.out_rec = (int)(ch * NS + P.s_m2);
-            RelItem ri{lane_buf(l, 2 + bbr), fuse ? lane_buf(l, bur) : lane_buf(l, 2 + (bbr ^ 1)),
-                       false, mbit(l)};
-            its.push_back(it);
-            rs.push_back(ri);
-          }
-          add_step_launch(P.s_m2, its, rs, l1 - l0);
-          if (fuse) P.launches.back().shape.dot = 1;
-          Launch dl{};
-          dl.kind = 3;
-          dl.aux_off = (int64_t)dots.size();
-          dl.n_aux = l1 - l0;
-          dl.flops = dl.bytes = 0;
-          if (P.launches.back().shape.dot) dl.fused_merge = (int)P.launches.size() - 1;
-          for (int l = l0; l < l1; ++l) {
-            const int64_t ch = mch(l);
-            DotEntry d{};
-            d.Y = (const void *)(REL + lane_buf(l, 2 + (bbr ^ 1)));
-            d.F = (const void *)(REL + lane_buf(l, bur));
-            d.n = ur.batch * ur.rest;
-            d.rec_y = (int)(ch * NS + P.s_m2);
-            d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
-            d.out_index = (int)mbit(l);
-            d.nslots = kDotBlocks;   // fused: set once the merge's tiles are known
-            dots.push_back(d);
-          }
-          P.launches.push_back(dl);
-          l0 = l1;
+        std::vector<StepItem> its;
+        std::vector<RelItem> rs;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t ch = mch(l);
+          const int j = (int)((m0 + base + l) / gs - g0);
+          StepItem it{};
+          it.op_base = P.op_m2 + j;
+          it.b_slot = j;
+          it.in_rec = (int)(ch * NS + br.first + br.count - 1);
+          it.out_rec = (int)(ch * NS + P.s_m2);
+          its.push_back(it);
+          rs.push_back(RelItem{lane_buf(l, 2 + bbr),
+                               fuse ? lane_buf(l, bur) : lane_buf(l, 2 + (bbr ^ 1)), false,
+                               mbit(l)});
         }
+        add_step_launch(P.s_m2, its, rs, nl);
+        if (fuse) P.launches.back().shape.dot = 1;
+        Launch dl{};
+        dl.kind = 3;
+        dl.aux_off = (int64_t)dots.size();
+        dl.n_aux = nl;
+        dl.flops = dl.bytes = 0;
+        if (P.launches.back().shape.dot) dl.fused_merge = (int)P.launches.size() - 1;
+        for (int l = 0; l < nl; ++l) {
+          const int64_t ch = mch(l);
+          DotEntry d{};
+          d.Y = (const void *)(REL + lane_buf(l, 2 + (bbr ^ 1)));
+          d.F = (const void *)(REL + lane_buf(l, bur));
+          d.n = ur.batch * ur.rest;
+          d.rec_y = (int)(ch * NS + P.s_m2);
+          d.rec_f = (int)(ch * NS + ur.first + ur.count - 1);
+          d.out_index = (int)mbit(l);
+          d.nslots = kDotBlocks;   // fused: set once the merge's tiles are known
+          dots.push_back(d);
+        }
+        P.launches.push_back(dl);
       }
     }
   } else if (pc > 0) {
@@ -1974,7 +2005,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
     const int ob = l.op_base;
     // the variants' planes are equally spaced (allocated one after another
     // with the same padded size)
-    const int nv = step_variants(l.shape);
+    const int nv = op_slots(P, l.step);
     const void *bb[2];
     for (int pl = 0; pl < 2; ++pl)
       bb[pl] = P.bt_off[pl][ob] ? (const void *)(base + P.bt_off[pl][ob])
@@ -1987,7 +2018,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
           return fail(PEPS_EINVAL, "internal: operand variants not equally spaced at site %d", q);
     int rc = tc_prepare(l.shape, fmt, base + P.lane_off + l.a_base_rel, l.a_lanes,
                         (int64_t)(BPL * P.gbuf_bytes), P.plane * 2, bb, nv, vst, o.tc_kchunk,
-                        o.tc_cluster, &l.tc_handle);
+                        o.tc_cluster, o.tc_epi, &l.tc_handle);
     if (rc != 0)
       return fail(PEPS_ECUDA, "tensor-map encoding failed (%d) for the step at site %d", rc, q);
   }
@@ -2001,7 +2032,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<OpDesc> ops(n_ops);
   for (int s = 0; s < P.n_steps; ++s) {
     const StepShape &sh = P.steps[s];
-    for (int t = 0; t < step_variants(sh); ++t) {
+    for (int t = 0; t < op_slots(P, s); ++t) {
       const int op = P.step_opbase[s] + t;
       OpDesc d{};
       d.Ec = P.ec_off[op] ? (const float2 *)(base + P.ec_off[op]) : nullptr;
@@ -2466,12 +2497,13 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
         // a merge operand from a stored tensor: for the tensor cores its bound
         // and planes straight from the tensor, else Ec and its bound
         if (l.tc) {
-          CUDA_TRY(launch_tensor_operand_tc(tops + l.aux_off, l.shape.K, l.shape.N, P.fmt, P.plane,
-                                            ops, recs, s));
+          CUDA_TRY(launch_tensor_operand_tc(tops + l.aux_off, l.n_aux, l.shape.K, l.shape.N, P.fmt,
+                                            P.plane, ops, recs, s));
           S.launches_operand += 3;
         } else {
-          CUDA_TRY(launch_tensor_operand(tops + l.aux_off, l.kn, P.fmt, P.plane, ops, recs, s));
-          CUDA_TRY(launch_operand_bounds(1, ops + l.op, s, l.shape.N));
+          CUDA_TRY(launch_tensor_operand(tops + l.aux_off, l.n_aux, l.kn, P.fmt, P.plane, ops, recs,
+                                         s));
+          CUDA_TRY(launch_operand_bounds(l.n_aux, ops + l.op, s, l.shape.N));
           S.launches_operand += 2;
         }
       } else if (l.kind == 3 && l.fused_merge >= 0) {

@@ -88,6 +88,12 @@ struct StepItem {
   int32_t in_rec;         // Rec index of the input (-1: the unit scalar)
   int32_t out_rec;        // Rec index of the output
   int32_t a_lane;         // lane coordinate of A in the launch's tensor map
+  int32_t b_slot;         // operand slot of the item past the launch's first
+                          // (the tensor-core B map's variant coordinate is
+                          // b_slot + the bitstring's variant; op_base already
+                          // includes it): the square partition's merges of
+                          // several groups, each with its own operand
+  int32_t pad_;
 };
 
 // Shape shared by all items of a launch.  A step absorbs a block of nq
@@ -303,8 +309,9 @@ cudaError_t launch_build_operands(const OpBuildEntry *d_entries, int n, int max_
 // `n_cols`: the widest operand's N (sizes the grid of a single op)
 cudaError_t launch_operand_bounds(int n_ops, OpDesc *d_ops, cudaStream_t s,
                                   int64_t n_cols = 4096);
-cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int fmt, int64_t plane,
-                                  OpDesc *d_ops, const Rec *d_recs, cudaStream_t s);
+cudaError_t launch_tensor_operand(const TensorOpEntry *d_entries, int n_entries, int64_t kn,
+                                  int fmt, int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+                                  cudaStream_t s);
 // Blocks per DotEntry; `d_partials` holds kDotBlocks double2 per entry.
 constexpr int kDotBlocks = 256;
 cudaError_t launch_dot(const DotEntry *d_entries, int n, int fmt, int64_t plane,
@@ -316,8 +323,8 @@ cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int ma
                                    OpDesc *d_ops, cudaStream_t s);
 // A merge operand's tensor-core planes and bound straight from the stored
 // tensor (no Ec); K, N are the operand's sizes.
-cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int K, int N, int fmt,
-                                     int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entries, int n_entries, int K, int N,
+                                     int fmt, int64_t plane, OpDesc *d_ops, const Rec *d_recs,
                                      cudaStream_t s);
 // Tensor-core planes (and their bound) of ops [0, n_ops) from their Ec.
 cudaError_t launch_build_tc_operands(int n_ops, int64_t max_kn, OpDesc *d_ops, int fmt,
@@ -354,14 +361,15 @@ cudaError_t launch_check_groups(const uint64_t *d_bits, int64_t n, int group,
 
 // tcgen05 contraction (contract_tc.cu).
 bool tc_supports(const StepShape &sh, int fmt);
-bool tc_tuning_valid(int kchunk, int cluster);
+bool tc_tuning_valid(int kchunk, int cluster, int epi);
 // Encode the launch's tensor maps (A over the lanes' input buffers, Bt for
 // tau = 0/1 and each plane); returns 0 and an opaque handle, or < 0.
 // The B operands: plane pl of variant t at b_base[pl] + t * b_var_stride
 // bytes (n_var variants, equally spaced).
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
                int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_base[2],
-               int n_var, int64_t b_var_stride, int kchunk, int cluster, void **out_handle);
+               int n_var, int64_t b_var_stride, int kchunk, int cluster, int epi,
+               void **out_handle);
 void tc_release(void *handle);
 // One-time set-up of the kernel a handle launches (attributes, occupancy);
 // done before a stream capture so that no such call happens inside it.

@@ -45,8 +45,10 @@ namespace peps {
 namespace {
 
 constexpr int BM = 128;
-constexpr int EPI_WARPS = 4;                  // one per TMEM lane quadrant
-constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer, mma, epilogue warps
+// Warps: a TMA producer, an MMA issuer and EPI epilogue warps; EPI = 4 (one per
+// TMEM lane quadrant) or 8 (two per quadrant, each draining half of the
+// tile's columns, for steps whose epilogue outlasts their MMAs).
+constexpr int threads_of(int epi) { return 64 + 32 * epi; }
 
 template <int FMT> struct FormTraits;
 template <> struct FormTraits<FMT_BF16>   { static constexpr int NP = 1, ESZ = 2, KIND = 0, AB = 1; };
@@ -106,7 +108,7 @@ struct __align__(64) TcParams {
                 // (1: n fastest over a whole row group)
   int64_t mlo;  // m_hi-major: Mr / P
   int64_t watchdog_ns;
-  double2 *dot_partials;   // sh.dot: [item][tiles_per_item * CG * EPI_WARPS]
+  double2 *dot_partials;   // sh.dot: [item][tiles_per_item * CG * EPI]
   int blocked;  // 1: CTA pair c takes the consecutive tiles [c per, (c + 1) per)
                 // (an item's tiles in a row, so its variant, scale and
                 // addresses are set up once); 0: tiles c, c + pairs, ...
@@ -397,8 +399,9 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
 // ---------------------------------------------------------------------------
 // CG: CTAs per MMA.  CG = 1: one CTA per 128-row tile.  CG = 2: a cluster of
 // two CTAs per 256-row tile (2-SM UMMA), see the file comment.
-template <int FMT, int ROWB, int CG>
-__global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constant__ TcParams p) {
+template <int FMT, int ROWB, int CG, int EPI>
+__global__ void __launch_bounds__(threads_of(EPI), 1)
+    k_contract_tc(const __grid_constant__ TcParams p) {
   using T = FormTraits<FMT>;
   constexpr int NP = T::NP;
   constexpr int KSTEPS = ROWB / 32;  // 32-byte MMA k-steps per stage
@@ -434,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
       // the pair's epilogue warps (one elected lane each) release an accumulator
-      mbar_init(&tempty[a], CG == 2 ? 2 * EPI_WARPS : 32 * EPI_WARPS);
+      mbar_init(&tempty[a], CG == 2 ? 2 * EPI : 32 * EPI);
     }
     mbar_init(done, 1);
     mbar_init(pdone, 1);
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
         if (item != cached_item) {
           cached_item = item;
           const StepItem &si = p.items[item];
-          tau = block_variant(*si.bits, p.sh);
+          tau = block_variant(*si.bits, p.sh) + si.b_slot;
           a_lane = si.a_lane;
         }
         // m_hi-major: tile mt is rows m_hi = hb0 .. hb0+ph-1, m_lo = mlo_t ..
@@ -645,6 +648,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
     // while chunk c is scaled, split and stored.
     const int quad = warp & 3;
     const int row = 32 * quad + lane;
+    // EPI = 8: warps ew and ew + 4 share a quadrant and split its columns
+    // (a 16-column tile stays with the first)
+    const int ew = warp - 2;
+    const bool split_cols = EPI == 8 && p.BN >= 32;
+    const int c_begin = split_cols ? (ew >> 2) * (p.BN / 2) : 0;
+    const bool idle = EPI == 8 && !split_cols && ew >= 4;
+    const int c_end = idle ? 0 : (split_cols ? c_begin + p.BN / 2 : p.BN);
     const int dv = p.sh.dv_out, dh = p.sh.dh_out;
     const int64_t M = p.sh.M, P = p.sh.P;
     const int64_t Mr = p.sh.Mr > 0 ? p.sh.Mr : M, Mlo = Mr / P;
@@ -721,16 +731,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
       float dre = 0.f, dim = 0.f;   // fused dot: this row's partial sum
       // fused dot: the partner entries of row m (P = 1, row-major m N + n),
       // loaded one chunk ahead of their use
-      const int64_t dot_e = m_lo * (int64_t)p.sh.N + ((nt * BN) >> 1);
+      const int64_t dot_e = m_lo * (int64_t)p.sh.N + ((nt * BN + c_begin) >> 1);
       Raw8 fcur, fnext;
-      if (dotm && live) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
+      if (dotm && live && !idle) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
       uint32_t ra[16], rb[16];
-      tmem_ld16_issue(tbase, ra);
-      tmem_wait(ra);
-      for (int c = 0; c < BN; c += 16) {
-        const bool more = c + 16 < BN;
+      if (!idle) {
+        tmem_ld16_issue(tbase + (uint32_t)c_begin, ra);
+        tmem_wait(ra);
+      }
+      for (int c = c_begin; c < c_end; c += 16) {
+        const bool more = c + 16 < c_end;
         if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), rb);
-        if (dotm && live && more) load8_raw<FMT>(D, dot_e + ((c + 16) >> 1), p.sh.plane, fnext);
+        if (dotm && live && more)
+          load8_raw<FMT>(D, dot_e + ((c + 16 - c_begin) >> 1), p.sh.plane, fnext);
         float v[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
@@ -811,8 +824,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_contract_tc(const __grid_constan
           i += __shfl_xor_sync(0xffffffffu, i, o);
         }
         if (lane == 0)
-          p.dot_partials[((int64_t)item * tiles_per_item + rem) * (CG * EPI_WARPS) +
-                         (int)rank * EPI_WARPS + quad] = make_double2(r, i);
+          p.dot_partials[((int64_t)item * tiles_per_item + rem) * (CG * EPI) + (int)rank * EPI +
+                         ew] = make_double2(r, i);
       } else {
         for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
         if (lane == 0) atomicMax(&p.recs[si->out_rec].maxbits, __float_as_uint(vmax));
@@ -876,8 +889,9 @@ int rowb_for(int Kr, int esz, int want = 0) {
 
 int tc_Kr_pad(int K) { return 2 * K; }
 
-bool tc_tuning_valid(int kchunk, int cluster) {
-  return (kchunk == 0 || kchunk == 64 || kchunk == 128) && (cluster >= 0 && cluster <= 2);
+bool tc_tuning_valid(int kchunk, int cluster, int epi) {
+  return (kchunk == 0 || kchunk == 64 || kchunk == 128) && (cluster >= 0 && cluster <= 2) &&
+         (epi == 0 || epi == 4 || epi == 8);
 }
 int tc_Nr_pad(int N) { return 2 * N; }
 
@@ -898,12 +912,14 @@ bool tc_supports(const StepShape &sh, int fmt) {
 struct TcLaunchData {
   TcParams prm;
   int rowb;
-  int cg;  // CTAs per MMA: 1, or 2 for the 2-SM UMMA
+  int cg;   // CTAs per MMA: 1, or 2 for the 2-SM UMMA
+  int epi;  // epilogue warps: 4, or 8 where the epilogue bounds the step
 };
 
 int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
                int64_t a_lane_stride, int64_t plane_stride_bytes, const void *const b_base[2],
-               int n_var, int64_t b_var_stride, int kchunk, int cluster, void **out_handle) {
+               int n_var, int64_t b_var_stride, int kchunk, int cluster, int epi,
+               void **out_handle) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return -1;
   const int esz = esz_of(fmt), np = np_of(fmt);
@@ -1064,22 +1080,25 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   int stages = budget / stage_bytes;
   if (stages > 8) stages = 8;
   d->prm.stages = stages;
+  // a short K (at most 16 k-chunks per tile) leaves the epilogue as the
+  // bound: two warps per TMEM lane quadrant
+  d->epi = epi == 4 || epi == 8 ? epi : (kb_count <= 16 ? 8 : 4);
   *out_handle = d;
   return stages >= 2 ? 0 : -5;
 }
 
 void tc_release(void *h) { delete (TcLaunchData *)h; }
 
-template <int FMT, int ROWB, int CG>
+template <int FMT, int ROWB, int CG, int EPI>
 static int &max_clusters_of() {
   static int v = -1;  // co-resident clusters at the largest smem size (-1: not set up)
   return v;
 }
 
-template <int FMT, int ROWB, int CG>
+template <int FMT, int ROWB, int CG, int EPI>
 static cudaError_t init_kernel() {
-  auto kern = k_contract_tc<FMT, ROWB, CG>;
-  int &max_clusters = max_clusters_of<FMT, ROWB, CG>();
+  auto kern = k_contract_tc<FMT, ROWB, CG, EPI>;
+  int &max_clusters = max_clusters_of<FMT, ROWB, CG, EPI>();
   if (max_clusters < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
@@ -1091,7 +1110,7 @@ static cudaError_t init_kernel() {
     qa[0].val.clusterDim.y = 1;
     qa[0].val.clusterDim.z = 1;
     q.gridDim = dim3(CG * 64);
-    q.blockDim = dim3(THREADS);
+    q.blockDim = dim3(threads_of(EPI));
     q.dynamicSmemBytes = 227 * 1024;
     q.attrs = qa;
     q.numAttrs = 1;
@@ -1106,12 +1125,12 @@ static cudaError_t init_kernel() {
   return cudaSuccess;
 }
 
-template <int FMT, int ROWB, int CG>
+template <int FMT, int ROWB, int CG, int EPI>
 static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaStream_t s) {
-  auto kern = k_contract_tc<FMT, ROWB, CG>;
-  cudaError_t e0 = init_kernel<FMT, ROWB, CG>();
+  auto kern = k_contract_tc<FMT, ROWB, CG, EPI>;
+  cudaError_t e0 = init_kernel<FMT, ROWB, CG, EPI>();
   if (e0 != cudaSuccess) return e0;
-  const int max_clusters = max_clusters_of<FMT, ROWB, CG>();
+  const int max_clusters = max_clusters_of<FMT, ROWB, CG, EPI>();
   // units = SMs to use; one CTA per SM, clusters of CG
   int clusters = units / CG;
   if (max_clusters > 0 && clusters > max_clusters) clusters = max_clusters;
@@ -1123,7 +1142,7 @@ static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaS
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(clusters * CG);
-  cfg.blockDim = dim3(THREADS);
+  cfg.blockDim = dim3(threads_of(EPI));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
@@ -1131,37 +1150,48 @@ static cudaError_t launch_one(const TcParams &prm, int units, size_t smem, cudaS
   return cudaLaunchKernelEx(&cfg, kern, prm);
 }
 
+template <int FMT, int EPI>
+static cudaError_t warm_epi(int rowb, int cg) {
+  if (rowb == 128)
+    return cg == 2 ? init_kernel<FMT, 128, 2, EPI>() : init_kernel<FMT, 128, 1, EPI>();
+  return cg == 2 ? init_kernel<FMT, 64, 2, EPI>() : init_kernel<FMT, 64, 1, EPI>();
+}
 template <int FMT>
-static cudaError_t warm_fmt(int rowb, int cg) {
-  if (rowb == 128) return cg == 2 ? init_kernel<FMT, 128, 2>() : init_kernel<FMT, 128, 1>();
-  return cg == 2 ? init_kernel<FMT, 64, 2>() : init_kernel<FMT, 64, 1>();
+static cudaError_t warm_fmt(int rowb, int cg, int epi) {
+  return epi == 8 ? warm_epi<FMT, 8>(rowb, cg) : warm_epi<FMT, 4>(rowb, cg);
 }
 
 cudaError_t tc_warm(void *handle) {
   TcLaunchData *d = (TcLaunchData *)handle;
   switch (d->prm.sh.fmt) {
-    case FMT_BF16: return warm_fmt<FMT_BF16>(d->rowb, d->cg);
-    case FMT_FP16: return warm_fmt<FMT_FP16>(d->rowb, d->cg);
-    case FMT_BF16X2: return warm_fmt<FMT_BF16X2>(d->rowb, d->cg);
-    case FMT_FP16X2: return warm_fmt<FMT_FP16X2>(d->rowb, d->cg);
-    case FMT_TF32: return warm_fmt<FMT_TF32>(d->rowb, d->cg);
+    case FMT_BF16: return warm_fmt<FMT_BF16>(d->rowb, d->cg, d->epi);
+    case FMT_FP16: return warm_fmt<FMT_FP16>(d->rowb, d->cg, d->epi);
+    case FMT_BF16X2: return warm_fmt<FMT_BF16X2>(d->rowb, d->cg, d->epi);
+    case FMT_FP16X2: return warm_fmt<FMT_FP16X2>(d->rowb, d->cg, d->epi);
+    case FMT_TF32: return warm_fmt<FMT_TF32>(d->rowb, d->cg, d->epi);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int FMT>
-static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cg, int units, size_t smem,
+template <int FMT, int EPI>
+static cudaError_t launch_epi(const TcParams &prm, int rowb, int cg, int units, size_t smem,
                               cudaStream_t s) {
   if (rowb == 128)
-    return cg == 2 ? launch_one<FMT, 128, 2>(prm, units, smem, s)
-                   : launch_one<FMT, 128, 1>(prm, units, smem, s);
-  return cg == 2 ? launch_one<FMT, 64, 2>(prm, units, smem, s)
-                 : launch_one<FMT, 64, 1>(prm, units, smem, s);
+    return cg == 2 ? launch_one<FMT, 128, 2, EPI>(prm, units, smem, s)
+                   : launch_one<FMT, 128, 1, EPI>(prm, units, smem, s);
+  return cg == 2 ? launch_one<FMT, 64, 2, EPI>(prm, units, smem, s)
+                 : launch_one<FMT, 64, 1, EPI>(prm, units, smem, s);
+}
+template <int FMT>
+static cudaError_t launch_fmt(const TcParams &prm, int rowb, int cg, int epi, int units,
+                              size_t smem, cudaStream_t s) {
+  return epi == 8 ? launch_epi<FMT, 8>(prm, rowb, cg, units, smem, s)
+                  : launch_epi<FMT, 4>(prm, rowb, cg, units, smem, s);
 }
 
 int tc_dot_slots(const void *handle) {
   const TcLaunchData *d = (const TcLaunchData *)handle;
-  return d->prm.tiles_m * d->prm.tiles_n * EPI_WARPS;
+  return d->prm.tiles_m * d->prm.tiles_n * d->epi;
 }
 
 cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_items,
@@ -1186,11 +1216,11 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
   const size_t smem = (size_t)prm.stages * np * (BM + prm.BN / cg) * d->rowb + 1024 +
                       (2 * prm.stages + 6) * 8 + 16;
   switch (prm.sh.fmt) {
-    case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cg, units, smem, s);
-    case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cg, units, smem, s);
-    case FMT_BF16X2: return launch_fmt<FMT_BF16X2>(prm, d->rowb, cg, units, smem, s);
-    case FMT_FP16X2: return launch_fmt<FMT_FP16X2>(prm, d->rowb, cg, units, smem, s);
-    case FMT_TF32: return launch_fmt<FMT_TF32>(prm, d->rowb, cg, units, smem, s);
+    case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cg, d->epi, units, smem, s);
+    case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cg, d->epi, units, smem, s);
+    case FMT_BF16X2: return launch_fmt<FMT_BF16X2>(prm, d->rowb, cg, d->epi, units, smem, s);
+    case FMT_FP16X2: return launch_fmt<FMT_FP16X2>(prm, d->rowb, cg, d->epi, units, smem, s);
+    case FMT_TF32: return launch_fmt<FMT_TF32>(prm, d->rowb, cg, d->epi, units, smem, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -1245,8 +1275,11 @@ __global__ void k_build_bt(OpDesc *ops) {
 // sum_k |Ec[k][n]|_1 (one block per column, the threads along k), k_tensor_bt
 // the complex-as-real planes Bt[(n, b)][(k, a)] (reads and writes both run
 // along k).  Same values as Ec -> k_beta_ops -> k_build_bt.
-__global__ void k_tensor_init(const TensorOpEntry *__restrict__ e, OpDesc *ops, const Rec *recs) {
-  const TensorOpEntry g = *e;
+__global__ void k_tensor_init(const TensorOpEntry *__restrict__ e, int n, OpDesc *ops,
+                              const Rec *recs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const TensorOpEntry g = e[i];
   OpDesc &op = ops[g.op];
   op.beta_c_bits = 0u;
   op.beta_t_bits = 0u;
@@ -1256,7 +1289,7 @@ __global__ void k_tensor_init(const TensorOpEntry *__restrict__ e, OpDesc *ops, 
 template <int FMT>
 __global__ void __launch_bounds__(256) k_tensor_bound(const TensorOpEntry *__restrict__ e,
                                                       int64_t plane, OpDesc *ops) {
-  const TensorOpEntry g = *e;
+  const TensorOpEntry g = e[blockIdx.y];   // one entry per grid row
   const float sc = pow2f(-g.target);
   __shared__ float red[8];
   float best = 0.f;
@@ -1284,7 +1317,7 @@ __global__ void __launch_bounds__(256) k_tensor_bound(const TensorOpEntry *__res
 
 template <int FMT>
 __global__ void k_tensor_bt(const TensorOpEntry *__restrict__ e, int64_t plane, OpDesc *ops) {
-  const TensorOpEntry g = *e;
+  const TensorOpEntry g = e[blockIdx.y];   // one entry per grid row
   OpDesc &op = ops[g.op];
   const int64_t K = g.K, N = g.N;
   const float sc = pow2f(-g.target), sb = ldexpf(1.f, op.b_t);
@@ -1323,21 +1356,23 @@ __global__ void k_tensor_bt(const TensorOpEntry *__restrict__ e, int64_t plane, 
   }
 }
 
-cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int K, int N, int fmt,
-                                     int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int n_entries, int K, int N,
+                                     int fmt, int64_t plane, OpDesc *d_ops, const Rec *d_recs,
                                      cudaStream_t s) {
+  if (n_entries <= 0) return cudaSuccess;
   const int64_t kn = (int64_t)K * N;
   int64_t gb = N < 16384 ? N : 16384;
   if (gb < 1) gb = 1;
   int64_t gt = (kn + 255) / 256;
   if (gt > 16384) gt = 16384;
   if (gt < 1) gt = 1;
-  k_tensor_init<<<1, 1, 0, s>>>(d_entry, d_ops, d_recs);
+  k_tensor_init<<<(n_entries + 127) / 128, 128, 0, s>>>(d_entry, n_entries, d_ops, d_recs);
+  const dim3 grid_b((unsigned)gb, (unsigned)n_entries), grid_t((unsigned)gt, (unsigned)n_entries);
   switch (fmt) {
 #define PEPS_TOP_CASE(F)                                                              \
   case F:                                                                            \
-    k_tensor_bound<F><<<(int)gb, 256, 0, s>>>(d_entry, plane, d_ops);                \
-    k_tensor_bt<F><<<(int)gt, 256, 0, s>>>(d_entry, plane, d_ops);                   \
+    k_tensor_bound<F><<<grid_b, 256, 0, s>>>(d_entry, plane, d_ops);                 \
+    k_tensor_bt<F><<<grid_t, 256, 0, s>>>(d_entry, plane, d_ops);                    \
     break;
     PEPS_TOP_CASE(FMT_TF32)
     PEPS_TOP_CASE(FMT_BF16)

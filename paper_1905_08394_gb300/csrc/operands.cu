@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(1024) k_beta_ops(OpDesc *ops) {
 template <int FMT>
 __global__ void k_tensor_op(const TensorOpEntry *__restrict__ e, int64_t plane, OpDesc *ops,
                             const Rec *recs) {
-  const TensorOpEntry g = *e;
+  const TensorOpEntry g = e[blockIdx.y];   // one entry per grid row
   OpDesc &op = ops[g.op];
   float2 *Ec = const_cast<float2 *>(op.Ec);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -259,18 +259,21 @@ __global__ void k_tensor_op(const TensorOpEntry *__restrict__ e, int64_t plane, 
   }
 }
 
-cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int64_t kn, int fmt, int64_t plane,
-                                  OpDesc *d_ops, const Rec *d_recs, cudaStream_t s) {
-  int64_t blocks = (kn + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
+cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int n_entries, int64_t kn,
+                                  int fmt, int64_t plane, OpDesc *d_ops, const Rec *d_recs,
+                                  cudaStream_t s) {
+  if (n_entries <= 0) return cudaSuccess;
+  int64_t bx = (kn + 255) / 256;
+  if (bx > 4096) bx = 4096;
+  if (bx < 1) bx = 1;
+  const dim3 blocks((unsigned)bx, (unsigned)n_entries);
   switch (fmt) {
-    case FMT_F32: k_tensor_op<FMT_F32><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
-    case FMT_TF32: k_tensor_op<FMT_TF32><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
-    case FMT_BF16: k_tensor_op<FMT_BF16><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
-    case FMT_FP16: k_tensor_op<FMT_FP16><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
-    case FMT_BF16X2: k_tensor_op<FMT_BF16X2><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
-    case FMT_FP16X2: k_tensor_op<FMT_FP16X2><<<(int)blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_F32: k_tensor_op<FMT_F32><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_TF32: k_tensor_op<FMT_TF32><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_BF16: k_tensor_op<FMT_BF16><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_FP16: k_tensor_op<FMT_FP16><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_BF16X2: k_tensor_op<FMT_BF16X2><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
+    case FMT_FP16X2: k_tensor_op<FMT_FP16X2><<<blocks, 256, 0, s>>>(d_entry, plane, d_ops, d_recs); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
