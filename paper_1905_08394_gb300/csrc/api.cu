@@ -1142,7 +1142,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
         sh.vb = last ? 1 : 0;
         // the open leg's store is contiguous in h' when nothing moves (P = 1):
         // order the operand's N with v' slowest there
-        sh.nvs = (last && Pd == 1 && k == 1 && dh % 8 == 0) ? 1 : 0;
+        sh.nvs = (last && Pd == 1 && k == 1 && dh > 1) ? 1 : 0;
         sh.Mr = Mr;
         if (int rc = set_variant_qubits(sh)) return rc;
         P.steps.push_back(sh);

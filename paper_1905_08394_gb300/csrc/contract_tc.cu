@@ -717,96 +717,150 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
       const int KSP = p.nacc;   // K segments, then the correction accumulator
       const uint32_t tbase =
           tmem_base + ((uint32_t)(32 * quad) << 16) + (uint32_t)(acc * BN * KSP);
-      // 8 consecutive complex columns per 16-column chunk; contiguous in the
-      // permuted destination when dim(v') is a multiple of 8 (then one row
-      // chunk is 32 or 64 bytes per plane, written with 16-byte stores).
-      // n = h' dv' + v' (nvs = 0): 8 consecutive n are contiguous when dv' % 8 == 0
-      // (not for vb); n = v' dh' + h' (nvs = 1, vb with P = 1): when dh' % 8 == 0
-      const bool nvs = p.sh.nvs != 0;
-      const bool vec = nvs ? (P == 1 && (dh & 7) == 0) : ((dv & 7) == 0 && !vbm);
-      const int64_t row_base = m_lo * dh;
-      const int64_t bofs = b * MrN;
       void *D = si->D;
       const bool dotm = p.sh.dot != 0;
       float dre = 0.f, dim = 0.f;   // fused dot: this row's partial sum
-      // fused dot: the partner entries of row m (P = 1, row-major m N + n),
-      // loaded one chunk ahead of their use
-      const int64_t dot_e = m_lo * (int64_t)p.sh.N + ((nt * BN + c_begin) >> 1);
-      Raw8 fcur, fnext;
-      if (dotm && live && !idle) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
+      // The columns in chunks of 16 (8 complex entries), chunk c + 16 loaded
+      // from TMEM while chunk c is used; the two register buffers take turns
+      // (an unrolled pair of chunks per iteration), so nothing is copied.
       uint32_t ra[16], rb[16];
-      if (!idle) {
-        tmem_ld16_issue(tbase + (uint32_t)c_begin, ra);
+      if (!idle) tmem_ld16_issue(tbase + (uint32_t)c_begin, ra);
+      if (dotm) {
+        // fused dot: the partner entries of row m (P = 1, row-major m N + n),
+        // loaded one chunk ahead of their use
+        const int64_t dot_e = m_lo * (int64_t)p.sh.N + ((nt * BN + c_begin) >> 1);
+        Raw8 fcur, fnext;
+        if (live && !idle) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
         tmem_wait(ra);
-      }
-      for (int c = c_begin; c < c_end; c += 16) {
-        const bool more = c + 16 < c_end;
-        if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), rb);
-        if (dotm && live && more)
-          load8_raw<FMT>(D, dot_e + ((c + 16 - c_begin) >> 1), p.sh.plane, fnext);
-        float v[16];
+        auto dot_chunk = [&](int c, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
+          const bool more = c + 16 < c_end;
+          float v[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
-        // the other K segments of these columns, added with FP32 round-to-nearest
-        for (int sg = 1; sg < KSP; ++sg) {
-          uint32_t rc[16];
-          tmem_ld16_issue(tbase + (uint32_t)(sg * BN + c), rc);
-          tmem_wait(rc);
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(cur[i]);
+          if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), nxt);
+          if (live && more) load8_raw<FMT>(D, dot_e + ((c + 16 - c_begin) >> 1), p.sh.plane, fnext);
+          for (int sg = 1; sg < KSP; ++sg) {
+            uint32_t rc[16];
+            tmem_ld16_issue(tbase + (uint32_t)(sg * BN + c), rc);
+            tmem_wait(rc);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(rc[i]);
-        }
-        if (live && dotm) {
-          // merge output row m times the stored tensor's entries at the same place
-          float2 f[8];
-          unpack8<FMT>(fcur, f);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            dre = fmaf(v[2 * j], f[j].x, fmaf(-v[2 * j + 1], f[j].y, dre));
-            dim = fmaf(v[2 * j], f[j].y, fmaf(v[2 * j + 1], f[j].x, dim));
+            for (int i = 0; i < 16; ++i) v[i] += __uint_as_float(rc[i]);
           }
-          fcur = fnext;
-        } else if (live) {
+          if (live) {
+            float2 f[8];
+            unpack8<FMT>(fcur, f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              dre = fmaf(v[2 * j], f[j].x, fmaf(-v[2 * j + 1], f[j].y, dre));
+              dim = fmaf(v[2 * j], f[j].y, fmaf(v[2 * j + 1], f[j].x, dim));
+            }
+            fcur = fnext;
+          }
+          if (more) tmem_wait(nxt);
+        };
+        for (int c = c_begin; c < c_end; c += 32) {
+          dot_chunk(c, ra, rb);
+          if (c + 16 < c_end) dot_chunk(c + 16, rb, ra);
+        }
+      } else {
+        // Destination of complex column nc of this row:
+        //   base + q(nc) * stride_q + r(nc) * stride_r  (q, r: nc / R, nc % R)
+        //   vb = 0:          n = h' dv' + v', entry b Mr N + ((m_lo dh' + h') P + m_hi) dv' + v'
+        //   vb = 1, nvs = 0: n = h' dv' + v', entry (b dv' + v') Mr dh' + (m_lo dh' + h') P + m_hi
+        //   vb = 1, nvs = 1: n = v' dh' + h', the same entry
+        // Runs of consecutive nc with stride_r = 1 are contiguous: they are
+        // stored W entries at a time (W = 8, 4, 2 dividing R), else one by one.
+        const bool nvs = p.sh.nvs != 0;
+        const Div &dR = vbm && nvs ? p.d_dh : p.d_dv;
+        const int64_t base = !vbm ? b * MrN + (m_lo * dh * P + m_hi) * dv
+                                  : b * dv * Mrdh + m_lo * dh * P + m_hi;
+        const int64_t stride_q = !vbm ? P * dv : (nvs ? Mrdh : P);
+        const int64_t stride_r = !vbm ? 1 : (nvs ? P : Mrdh);
+        const int64_t R = dR.d;
+        const int W = stride_r != 1 ? 1 : (R % 8 == 0 ? 8 : (R % 4 == 0 ? 4 : (R % 2 == 0 ? 2 : 1)));
+        // chunk c (16 columns, 8 complex entries): scaled, rounded to the
+        // storage format and stored in runs of W
+        auto emit = [&](int c, const float (&o)[16]) {
+          Packed8<FMT> w;
+          vmax = fmaxf(vmax, pack8<FMT>(o, sc, w));
           const int nc0 = (nt * BN + c) >> 1;
-          if (vec) {
-            int64_t dest0;
-            if (nvs) {
-              const int vv = (int)p.d_dh.q(nc0), hh = nc0 - vv * dh;   // P = 1: m_hi = 0
-              dest0 = (b * dv + vv) * Mrdh + row_base + hh;
-            } else {
-              const int hh = (int)p.d_dv.q(nc0), vv = nc0 - hh * dv;
-              dest0 = bofs + ((row_base + hh) * P + m_hi) * dv + vv;
-            }
-            vmax = fmaxf(vmax, store8_g<FMT>(D, dest0, p.sh.plane, v, sc));
-          } else if (vbm && !nvs && (dv & 7) == 0) {
-            // open-leg store with dv' a multiple of 8: the chunk's 8 columns
-            // share h' and are 8 consecutive v', each a whole batch slice
-            // (Mr dh' entries) apart; a warp's rows are consecutive m_hi
-            const int hh = (int)p.d_dv.q(nc0), vv0 = nc0 - hh * dv;
-            const int64_t base = (b * dv + vv0) * Mrdh + (row_base + hh) * P + m_hi;
+          switch (W) {
+            case 8:
+              store_run<FMT, 8>(D, base + dR.q(nc0) * stride_q + dR.r(nc0), p.sh.plane, w, 0);
+              break;
+            case 4:
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
-              store_g<FMT>(D, base + (int64_t)j * Mrdh, p.sh.plane, o);
-              vmax = fmaxf(vmax, max_abs2(o));
-            }
-          } else {
+              for (int j = 0; j < 8; j += 4)
+                store_run<FMT, 4>(D, base + dR.q(nc0 + j) * stride_q + dR.r(nc0 + j), p.sh.plane,
+                                  w, j);
+              break;
+            case 2:
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const int nc = nc0 + j;
-              const int hh = (int)(nvs ? p.d_dh.r(nc) : p.d_dv.q(nc));
-              const int vv = (int)(nvs ? p.d_dh.q(nc) : p.d_dv.r(nc));
-              const int64_t rot = (row_base + hh) * P + m_hi;
-              const int64_t dest = vbm ? (b * dv + vv) * Mrdh + rot : bofs + rot * dv + vv;
-              float2 o = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
-              store_g<FMT>(D, dest, p.sh.plane, o);
-              vmax = fmaxf(vmax, max_abs2(o));
-            }
+              for (int j = 0; j < 8; j += 2)
+                store_run<FMT, 2>(D, base + dR.q(nc0 + j) * stride_q + dR.r(nc0 + j), p.sh.plane,
+                                  w, j);
+              break;
+            default:
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                store_run<FMT, 1>(D, base + dR.q(nc0 + j) * stride_q + dR.r(nc0 + j) * stride_r,
+                                  p.sh.plane, w, j);
           }
-        }
-        if (more) {
-          tmem_wait(rb);
+        };
+        // the other K segments of chunk c, added with FP32 round-to-nearest
+        auto add_segments = [&](int c, float (&o)[16]) {
+          for (int sg = 1; sg < KSP; ++sg) {
+            uint32_t rc[16];
+            tmem_ld16_issue(tbase + (uint32_t)(sg * BN + c), rc);
+            tmem_wait(rc);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) ra[i] = rb[i];
+            for (int i = 0; i < 16; ++i) o[i] += __uint_as_float(rc[i]);
+          }
+        };
+        if (EPI == 4) {
+          // two chunks per iteration (twice the independent work in flight);
+          // the next pair's TMEM loads overlap this pair's arithmetic
+          if (c_begin + 16 < c_end) tmem_ld16_issue(tbase + (uint32_t)(c_begin + 16), rb);
+          tmem_wait(ra);
+          for (int c = c_begin; c < c_end; c += 32) {
+            const bool two = c + 16 < c_end;
+            float o0[16], o1[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              o0[i] = __uint_as_float(ra[i]);
+              o1[i] = __uint_as_float(rb[i]);
+            }
+            const bool more = c + 32 < c_end;
+            if (more) {
+              tmem_ld16_issue(tbase + (uint32_t)(c + 32), ra);
+              if (c + 48 < c_end) tmem_ld16_issue(tbase + (uint32_t)(c + 48), rb);
+            }
+            add_segments(c, o0);
+            if (two) add_segments(c + 16, o1);
+            if (live) {
+              emit(c, o0);
+              if (two) emit(c + 16, o1);
+            }
+            if (more) tmem_wait(ra);
+          }
+        } else {
+          // one chunk at a time (the register budget of eight epilogue warps):
+          // chunk c + 16 loads while chunk c is used
+          tmem_wait(ra);
+          auto one = [&](int c, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
+            const bool more = c + 16 < c_end;
+            float o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = __uint_as_float(cur[i]);
+            if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), nxt);
+            add_segments(c, o);
+            if (live) emit(c, o);
+            if (more) tmem_wait(nxt);
+          };
+          for (int c = c_begin; c < c_end; c += 32) {
+            one(c, ra, rb);
+            if (c + 16 < c_end) one(c + 16, rb, ra);
+          }
         }
       }
       tc_fence_before();
@@ -1080,9 +1134,13 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   int stages = budget / stage_bytes;
   if (stages > 8) stages = 8;
   d->prm.stages = stages;
-  // a short K (at most 16 k-chunks per tile) leaves the epilogue as the
-  // bound: two warps per TMEM lane quadrant
-  d->epi = epi == 4 || epi == 8 ? epi : (kb_count <= 16 ? 8 : 4);
+  // Epilogue warps (measured on the square partition's steps): four where
+  // wide tiles store runs of 8 entries (each warp keeps two chunks in
+  // flight), eight where the stores go out 1 to 4 entries at a time, where
+  // nothing is stored (the fused dot) and on narrower tiles
+  const bool runs8 = !sh.dot && ((!sh.vb && sh.dv_out % 8 == 0) ||
+                                 (sh.vb && sh.nvs && sh.P == 1 && sh.dh_out % 8 == 0));
+  d->epi = epi == 4 || epi == 8 ? epi : ((runs8 && BN >= 256) ? 4 : 8);
   *out_handle = d;
   return stages >= 2 ? 0 : -5;
 }

@@ -168,6 +168,78 @@ __device__ __forceinline__ float store8_g(void *base, int64_t dest0, int64_t pla
   return m;
 }
 
+// 8 complex entries (16 floats, re / im interleaved) in a storage format:
+// F32 / TF32 two words per entry; BF16 / FP16 one word (re, im) per entry;
+// the split forms one word per entry in each of the hi and lo planes.
+template <int FMT>
+struct Packed8 {
+  uint32_t w[(FMT == FMT_F32 || FMT == FMT_TF32 || FMT == FMT_BF16X2 || FMT == FMT_FP16X2) ? 16 : 8];
+};
+
+// v * sc (sc a power of two) rounded to the storage format; returns the max
+// |scaled component| before rounding (step_scale_exp allows for the rounding).
+template <int FMT>
+__device__ __forceinline__ float pack8(const float (&v)[16], float sc, Packed8<FMT> &p) {
+  float m = 0.f;
+  float o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    o[i] = v[i] * sc;
+    m = fmaxf(m, fabsf(o[i]));
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (FMT == FMT_F32) {
+      p.w[2 * j] = __float_as_uint(o[2 * j]);
+      p.w[2 * j + 1] = __float_as_uint(o[2 * j + 1]);
+    } else if (FMT == FMT_TF32) {
+      p.w[2 * j] = __float_as_uint(round_tf32(o[2 * j]));
+      p.w[2 * j + 1] = __float_as_uint(round_tf32(o[2 * j + 1]));
+    } else if (FMT == FMT_BF16) {
+      p.w[j] = pack_bf16(o[2 * j], o[2 * j + 1]);
+    } else if (FMT == FMT_FP16) {
+      p.w[j] = pack_f16(o[2 * j], o[2 * j + 1]);
+    } else if (FMT == FMT_BF16X2) {
+      p.w[j] = pack_bf16(o[2 * j], o[2 * j + 1]);
+      const float2 h = unpack_bf16(p.w[j]);
+      p.w[8 + j] = pack_bf16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
+    } else {
+      p.w[j] = pack_f16(o[2 * j], o[2 * j + 1]);
+      const float2 h = unpack_f16(p.w[j]);
+      p.w[8 + j] = pack_f16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
+    }
+  }
+  return m;
+}
+
+// Store entries j0 .. j0+W-1 of p at dest .. dest+W-1 (dest % W == 0), with
+// vector stores of up to 16 bytes.
+template <int W>
+__device__ __forceinline__ void store_words(uint32_t *d, const uint32_t *w) {
+  if (W == 1) {
+    d[0] = w[0];
+  } else if (W == 2) {
+    *reinterpret_cast<uint2 *>(d) = make_uint2(w[0], w[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < W; i += 4)
+      *reinterpret_cast<uint4 *>(d + i) = make_uint4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+  }
+}
+template <int FMT, int W>
+__device__ __forceinline__ void store_run(void *base, int64_t dest, int64_t plane,
+                                          const Packed8<FMT> &p, int j0) {
+  uint32_t *b = reinterpret_cast<uint32_t *>(base);
+  if (FMT == FMT_F32 || FMT == FMT_TF32) {
+    store_words<2 * W>(b + 2 * dest, p.w + 2 * j0);
+  } else if (FMT == FMT_BF16 || FMT == FMT_FP16) {
+    store_words<W>(b + dest, p.w + j0);
+  } else {
+    store_words<W>(b + dest, p.w + j0);
+    store_words<W>(b + plane / 2 + dest, p.w + 8 + j0);
+  }
+}
+
 // 8 consecutive complex entries e0 .. e0+7 (e0 % 8 == 0) in a storage
 // format, loaded with 16-byte vector loads into raw words (so that a load can
 // be issued early and unpacked later), and unpacked to float2.
