@@ -720,9 +720,8 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
       void *D = si->D;
       const bool dotm = p.sh.dot != 0;
       float dre = 0.f, dim = 0.f;   // fused dot: this row's partial sum
-      // The columns in chunks of 16 (8 complex entries), chunk c + 16 loaded
-      // from TMEM while chunk c is used; the two register buffers take turns
-      // (an unrolled pair of chunks per iteration), so nothing is copied.
+      // The columns in chunks of 16 (8 complex entries), the next chunk (or
+      // pair) loaded from TMEM while the current one is used.
       uint32_t ra[16], rb[16];
       if (!idle) tmem_ld16_issue(tbase + (uint32_t)c_begin, ra);
       if (dotm) {
@@ -732,12 +731,12 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
         Raw8 fcur, fnext;
         if (live && !idle) load8_raw<FMT>(D, dot_e, p.sh.plane, fcur);
         tmem_wait(ra);
-        auto dot_chunk = [&](int c, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
+        for (int c = c_begin; c < c_end; c += 16) {
           const bool more = c + 16 < c_end;
           float v[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(cur[i]);
-          if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), nxt);
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(ra[i]);
+          if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), ra);
           if (live && more) load8_raw<FMT>(D, dot_e + ((c + 16 - c_begin) >> 1), p.sh.plane, fnext);
           for (int sg = 1; sg < KSP; ++sg) {
             uint32_t rc[16];
@@ -756,11 +755,7 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
             }
             fcur = fnext;
           }
-          if (more) tmem_wait(nxt);
-        };
-        for (int c = c_begin; c < c_end; c += 32) {
-          dot_chunk(c, ra, rb);
-          if (c + 16 < c_end) dot_chunk(c + 16, rb, ra);
+          if (more) tmem_wait(ra);
         }
       } else {
         // Destination of complex column nc of this row:
@@ -844,22 +839,20 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
             if (more) tmem_wait(ra);
           }
         } else {
-          // one chunk at a time (the register budget of eight epilogue warps):
-          // chunk c + 16 loads while chunk c is used
+          // one chunk at a time (the register budget of eight epilogue warps),
+          // one copy of the code in the loop (the instruction cache holds the
+          // three roles' loops at once): chunk c is copied out of the load
+          // registers, chunk c + 16 loads into them while c is used
           tmem_wait(ra);
-          auto one = [&](int c, uint32_t (&cur)[16], uint32_t (&nxt)[16]) {
+          for (int c = c_begin; c < c_end; c += 16) {
             const bool more = c + 16 < c_end;
             float o[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = __uint_as_float(cur[i]);
-            if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), nxt);
+            for (int i = 0; i < 16; ++i) o[i] = __uint_as_float(ra[i]);
+            if (more) tmem_ld16_issue(tbase + (uint32_t)(c + 16), ra);
             add_segments(c, o);
             if (live) emit(c, o);
-            if (more) tmem_wait(nxt);
-          };
-          for (int c = c_begin; c < c_end; c += 32) {
-            one(c, ra, rb);
-            if (c + 16 < c_end) one(c + 16, rb, ra);
+            if (more) tmem_wait(ra);
           }
         }
       }

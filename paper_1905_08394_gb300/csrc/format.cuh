@@ -178,14 +178,37 @@ struct Packed8 {
 
 // v * sc (sc a power of two) rounded to the storage format; returns the max
 // |scaled component| before rounding (step_scale_exp allows for the rounding).
+// Packed FP32 pairs (sm_100 and later): one instruction for two lanes of
+// arithmetic, the same IEEE round-to-nearest results as two scalar ones.
+__device__ __forceinline__ void mul2(float a0, float a1, float b0, float b1, float &r0, float &r1) {
+  unsigned long long a, b, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(r));
+}
+__device__ __forceinline__ void sub2(float a0, float a1, float b0, float b1, float &r0, float &r1) {
+  unsigned long long a, b, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(b0), "f"(b1));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r0), "=f"(r1) : "l"(r));
+}
+// max(a, |b|, |c|)
+__device__ __forceinline__ float max_abs3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(fabsf(b)), "f"(fabsf(c)));
+  return r;
+}
+
 template <int FMT>
 __device__ __forceinline__ float pack8(const float (&v)[16], float sc, Packed8<FMT> &p) {
   float m = 0.f;
   float o[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    o[i] = v[i] * sc;
-    m = fmaxf(m, fabsf(o[i]));
+  for (int i = 0; i < 16; i += 2) {
+    mul2(v[i], v[i + 1], sc, sc, o[i], o[i + 1]);
+    m = max_abs3(m, o[i], o[i + 1]);
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -199,14 +222,14 @@ __device__ __forceinline__ float pack8(const float (&v)[16], float sc, Packed8<F
       p.w[j] = pack_bf16(o[2 * j], o[2 * j + 1]);
     } else if (FMT == FMT_FP16) {
       p.w[j] = pack_f16(o[2 * j], o[2 * j + 1]);
-    } else if (FMT == FMT_BF16X2) {
-      p.w[j] = pack_bf16(o[2 * j], o[2 * j + 1]);
-      const float2 h = unpack_bf16(p.w[j]);
-      p.w[8 + j] = pack_bf16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
     } else {
-      p.w[j] = pack_f16(o[2 * j], o[2 * j + 1]);
-      const float2 h = unpack_f16(p.w[j]);
-      p.w[8 + j] = pack_f16(o[2 * j] - h.x, o[2 * j + 1] - h.y);
+      // hi = the nearest 16-bit value, lo = the rounded remainder
+      constexpr bool BF = FMT == FMT_BF16X2;
+      p.w[j] = BF ? pack_bf16(o[2 * j], o[2 * j + 1]) : pack_f16(o[2 * j], o[2 * j + 1]);
+      const float2 h = BF ? unpack_bf16(p.w[j]) : unpack_f16(p.w[j]);
+      float d0, d1;
+      sub2(o[2 * j], o[2 * j + 1], h.x, h.y, d0, d1);
+      p.w[8 + j] = BF ? pack_bf16(d0, d1) : pack_f16(d0, d1);
     }
   }
   return m;
