@@ -102,39 +102,40 @@ __global__ void k_build_ec(const OpBuildEntry *__restrict__ entries, OpDesc *ops
   }
 }
 
-// ---- float-float helpers (as in the evolution kernels) ----
-struct ff2 {
-  float hi, lo;
-};
-__device__ __forceinline__ ff2 ff_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ ff2 ff_fast(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-__device__ __forceinline__ ff2 ffadd(ff2 x, ff2 y) {
-  ff2 s = ff_two_sum(x.hi, y.hi);
-  s.lo += x.lo + y.lo;
-  return ff_fast(s.hi, s.lo);
-}
-__device__ __forceinline__ ff2 ffmul(ff2 x, ff2 y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  return ff_fast(p, e);
-}
-
 // legs of a two-site block operand whose element offsets are tabulated in
 // shared memory (longer legs compute them per entry)
 constexpr int kMaxLeg2 = 256;
 
 // Two-site block operand W (see OpBuild2Entry), summed over the internal
-// vertical bond in float-float from the float-float site tensors, rounded
-// once to FP32.  k = (l_a * Lb + l_b) * Ua + u_a, n = (r_a * Rb + r_b) * Db + d_b.
+// vertical bond from the float-float site tensors and rounded once to FP32.
+// k = (l_a * Lb + l_b) * Ua + u_a, n = (r_a * Rb + r_b) * Db + d_b.
+//
+// The sum is compensated: each product of the hi parts is split exactly
+// into p + e (an FMA gives e), the p's are added with an error-free
+// two-sum, and the errors e, the sums' rounding errors and the cross terms
+// hi*lo + lo*hi (lo*lo, 2^-48 relative, is dropped as in a float-float
+// product) collect in a second FP32 accumulator; W = main + correction,
+// rounded once.  Its error is the final rounding plus O(2^-48) of the sum of
+// |terms|, as with float-float arithmetic throughout.
+__device__ __forceinline__ void acc_prod(float x, float y, float &s, float &c) {
+  const float p = x * y;
+  const float e = fmaf(x, y, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  c += ((s - (t - bb)) + (p - bb)) + e;
+  s = t;
+}
+
+// x / d and x % d for the index decomposition, by shifts when d is a power of two
+struct IxDiv {
+  int d, sh;   // sh = log2(d), or -1
+  __device__ __forceinline__ int q(int x) const { return sh >= 0 ? x >> sh : x / d; }
+  __device__ __forceinline__ int r(int x) const { return sh >= 0 ? x & (d - 1) : x % d; }
+};
+__device__ __forceinline__ IxDiv ixdiv(int d) {
+  return {d, (d > 0 && (d & (d - 1)) == 0) ? __ffs(d) - 1 : -1};
+}
+
 __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *ops) {
   const OpBuild2Entry &g = entries[blockIdx.y];
   OpDesc &op = ops[g.op];
@@ -175,10 +176,11 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
   const float2 *__restrict__ Ab = g.b.A;
   const int64_t loa = g.a.lo_off, lob = g.b.lo_off;
   const int64_t a_sd = g.a.stride[3], b_su = g.b.stride[2];  // the shared bond on each site
+  const IxDiv dN = ixdiv(N), dUa = ixdiv(Ua), dLb = ixdiv(Lb), dDb = ixdiv(Db), dRb = ixdiv(Rb);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
-    const int k = i / N, n = i - k * N;
-    const int ua = k % Ua, lb = (k / Ua) % Lb, la = k / (Ua * Lb);
-    const int db = n % Db, rb = (n / Db) % Rb, ra = n / (Db * Rb);
+    const int k = dN.q(i), n = i - k * N;
+    const int kq = dUa.q(k), ua = k - kq * Ua, la = dLb.q(kq), lb = kq - la * Lb;
+    const int nq = dDb.q(n), db = n - nq * Db, ra = dRb.q(nq), rb = nq - ra * Rb;
     int64_t pa0, pb0;
     if (tab) {
       pa0 = (int64_t)g.a.tau * g.a.tau_stride + off_la[la] + off_ra[ra] + off_ua[ua];
@@ -187,16 +189,22 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
       pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
       pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
     }
-    ff2 re = {0.f, 0.f}, im = {0.f, 0.f};
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
     for (int m = 0; m < Mid; ++m) {
       const int64_t pa = pa0 + (int64_t)mid_a[m] * a_sd, pb = pb0 + (int64_t)mid_b[m] * b_su;
       const float2 ah = Aa[pa], al = Aa[loa + pa];
       const float2 bh = Ab[pb], bl = Ab[lob + pb];
-      const ff2 ar = {ah.x, al.x}, ai = {ah.y, al.y}, br = {bh.x, bl.x}, bi = {bh.y, bl.y};
-      re = ffadd(re, ffadd(ffmul(ar, br), ffmul({-ai.hi, -ai.lo}, bi)));
-      im = ffadd(im, ffadd(ffmul(ar, bi), ffmul(ai, br)));
+      // re = ar br - ai bi, im = ar bi + ai br
+      acc_prod(ah.x, bh.x, sr, cr);
+      acc_prod(-ah.y, bh.y, sr, cr);
+      acc_prod(ah.x, bh.y, si, ci);
+      acc_prod(ah.y, bh.x, si, ci);
+      cr = fmaf(ah.x, bl.x, fmaf(al.x, bh.x, cr));
+      cr = fmaf(-ah.y, bl.y, fmaf(-al.y, bh.y, cr));
+      ci = fmaf(ah.x, bl.y, fmaf(al.x, bh.y, ci));
+      ci = fmaf(ah.y, bl.x, fmaf(al.y, bh.x, ci));
     }
-    Ec[i] = make_float2(re.hi + re.lo, im.hi + im.lo);
+    Ec[i] = make_float2(sr + cr, si + ci);
   }
 }
 
@@ -282,7 +290,12 @@ cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int n_entries, i
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  // about 4096 blocks in all (a few per SM and resident set), each thread
+  // looping over several entries of W so that a block's index tables (set up
+  // once per block) serve many of them
   int blocks = (max_kn + 255) / 256;
+  const int share = (4096 + n - 1) / n;
+  if (blocks > share) blocks = share < 16 ? 16 : share;
   if (blocks > 2048) blocks = 2048;
   if (blocks < 1) blocks = 1;
   k_build_ec2<<<dim3(blocks, n), 256, 0, s>>>(d_entries, d_ops);

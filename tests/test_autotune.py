@@ -17,7 +17,10 @@ def test_candidates_span_the_grid():
                                  schemes=("columns", "quadrants")))
     assert len(c) == 2 * 2 * 1 * 2
     assert {x["scheme"] for x in c} == {"columns", "quadrants"}
-    assert all(set(x) == {"scheme", "max_lanes", "tc_kchunk", "tc_cluster"} for x in c)
+    assert all(set(x) == {"scheme", "max_lanes", "tc_kchunk", "tc_cluster", "tc_epi"} for x in c)
+    assert {x["tc_epi"] for x in c} == {0}
+    e = list(autotune.candidates(lanes=(8,), kchunk=(128,), cluster=(2,), epi=(0, 4, 8)))
+    assert [x["tc_epi"] for x in e] == [0, 4, 8]
 
 
 def test_signature_depends_on_the_workload_and_order():
