@@ -126,28 +126,33 @@ __device__ __forceinline__ void acc_prod(float x, float y, float &s, float &c) {
   s = t;
 }
 
-// x / d and x % d for the index decomposition, by shifts when d is a power of two
-struct IxDiv {
-  int d, sh;   // sh = log2(d), or -1
-  __device__ __forceinline__ int q(int x) const { return sh >= 0 ? x >> sh : x / d; }
-  __device__ __forceinline__ int r(int x) const { return sh >= 0 ? x & (d - 1) : x % d; }
-};
-__device__ __forceinline__ IxDiv ixdiv(int d) {
-  return {d, (d > 0 && (d & (d - 1)) == 0) ? __ffs(d) - 1 : -1};
-}
+// The sum is the product of two matrices, A'[(l_a, u_a, r_a), m] and
+// B'[m, (l_b, r_b, d_b)], whose entries land at W[k, n] with k, n as above.
+// A block takes 32 x 32 tiles of that product: the tile's rows of A' and
+// columns of B' pass through shared memory 16 values of m at a time, and each
+// thread accumulates four entries (one column, four rows).
+constexpr int kEc2T = 32;   // tile rows and columns
+constexpr int kEc2M = 16;   // m per shared-memory pass
 
-__global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *ops) {
+__global__ void __launch_bounds__(256) k_build_ec2(const OpBuild2Entry *__restrict__ entries,
+                                                   OpDesc *ops) {
   const OpBuild2Entry &g = entries[blockIdx.y];
   OpDesc &op = ops[g.op];
   const int La = g.a.rdims[0], Ra = g.a.rdims[1], Ua = g.a.rdims[2], Mid = g.a.rdims[3];
   const int Lb = g.b.rdims[0], Rb = g.b.rdims[1], Db = g.b.rdims[3];
-  const int K = La * Lb * Ua, N = Ra * Rb * Db;
-  if (blockIdx.x * blockDim.x >= K * N) return;
+  const int N = Ra * Rb * Db;
+  const int Rows = La * Ua * Ra, Cols = Lb * Rb * Db;
+  const int tiles_c = (Cols + kEc2T - 1) / kEc2T;
+  const int n_tiles = ((Rows + kEc2T - 1) / kEc2T) * tiles_c;
+  if ((int)blockIdx.x >= n_tiles) return;
   // full index of every restricted value of the shared bond, on both sites,
   // and (where the legs are short enough) element offsets of the other legs
   __shared__ int mid_a[kMaxMid], mid_b[kMaxMid];
   __shared__ int64_t off_la[kMaxLeg2], off_ra[kMaxLeg2], off_ua[kMaxLeg2];
   __shared__ int64_t off_lb[kMaxLeg2], off_rb[kMaxLeg2], off_db[kMaxLeg2];
+  __shared__ float4 As[kEc2T][kEc2M + 1];   // (hi re, hi im, lo re, lo im), padded rows
+  __shared__ float4 Bs[kEc2M][kEc2T];
+  __shared__ int64_t row_a[kEc2T], col_b[kEc2T], row_out[kEc2T], col_out[kEc2T];
   for (int m = threadIdx.x; m < Mid; m += blockDim.x) {
     mid_a[m] = expand_leg(g.a, 3, m);
     mid_b[m] = expand_leg(g.b, 2, m);
@@ -176,35 +181,88 @@ __global__ void k_build_ec2(const OpBuild2Entry *__restrict__ entries, OpDesc *o
   const float2 *__restrict__ Ab = g.b.A;
   const int64_t loa = g.a.lo_off, lob = g.b.lo_off;
   const int64_t a_sd = g.a.stride[3], b_su = g.b.stride[2];  // the shared bond on each site
-  const IxDiv dN = ixdiv(N), dUa = ixdiv(Ua), dLb = ixdiv(Lb), dDb = ixdiv(Db), dRb = ixdiv(Rb);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
-    const int k = dN.q(i), n = i - k * N;
-    const int kq = dUa.q(k), ua = k - kq * Ua, la = dLb.q(kq), lb = kq - la * Lb;
-    const int nq = dDb.q(n), db = n - nq * Db, ra = dRb.q(nq), rb = nq - ra * Rb;
-    int64_t pa0, pb0;
-    if (tab) {
-      pa0 = (int64_t)g.a.tau * g.a.tau_stride + off_la[la] + off_ra[ra] + off_ua[ua];
-      pb0 = (int64_t)g.b.tau * g.b.tau_stride + off_lb[lb] + off_rb[rb] + off_db[db];
-    } else {
-      pa0 = pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
-      pb0 = pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
+  const int cc = threadIdx.x & (kEc2T - 1), rq = threadIdx.x / kEc2T;  // column, row group
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int tr = t / tiles_c, tc = t - tr * tiles_c;
+    // the tile's rows (a: l_a, u_a, r_a with r_a fastest) and columns
+    // (b: l_b, r_b, d_b with d_b fastest): element bases at m = 0 and their
+    // share of the output index k N + n
+    if (threadIdx.x < kEc2T) {
+      const int r = tr * kEc2T + threadIdx.x;
+      int64_t base = -1, out = 0;
+      if (r < Rows) {
+        const int ra = r % Ra, lu = r / Ra, ua = lu % Ua, la = lu / Ua;
+        base = tab ? (int64_t)g.a.tau * g.a.tau_stride + off_la[la] + off_ra[ra] + off_ua[ua]
+                   : pos_E(g.a, la, ra, ua, 0) - (int64_t)mid_a[0] * a_sd;
+        out = ((int64_t)la * Lb * Ua + ua) * N + (int64_t)ra * Rb * Db;
+      }
+      row_a[threadIdx.x] = base;
+      row_out[threadIdx.x] = out;
+    } else if (threadIdx.x < 2 * kEc2T) {
+      const int c = tc * kEc2T + threadIdx.x - kEc2T;
+      int64_t base = -1, out = 0;
+      if (c < Cols) {
+        const int db = c % Db, lr = c / Db, rb = lr % Rb, lb = lr / Rb;
+        base = tab ? (int64_t)g.b.tau * g.b.tau_stride + off_lb[lb] + off_rb[rb] + off_db[db]
+                   : pos_E(g.b, lb, rb, 0, db) - (int64_t)mid_b[0] * b_su;
+        out = (int64_t)lb * Ua * N + (int64_t)rb * Db + db;
+      }
+      col_b[threadIdx.x - kEc2T] = base;
+      col_out[threadIdx.x - kEc2T] = out;
     }
-    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-    for (int m = 0; m < Mid; ++m) {
-      const int64_t pa = pa0 + (int64_t)mid_a[m] * a_sd, pb = pb0 + (int64_t)mid_b[m] * b_su;
-      const float2 ah = Aa[pa], al = Aa[loa + pa];
-      const float2 bh = Ab[pb], bl = Ab[lob + pb];
-      // re = ar br - ai bi, im = ar bi + ai br
-      acc_prod(ah.x, bh.x, sr, cr);
-      acc_prod(-ah.y, bh.y, sr, cr);
-      acc_prod(ah.x, bh.y, si, ci);
-      acc_prod(ah.y, bh.x, si, ci);
-      cr = fmaf(ah.x, bl.x, fmaf(al.x, bh.x, cr));
-      cr = fmaf(-ah.y, bl.y, fmaf(-al.y, bh.y, cr));
-      ci = fmaf(ah.x, bl.y, fmaf(al.x, bh.y, ci));
-      ci = fmaf(ah.y, bl.x, fmaf(al.y, bh.x, ci));
+    __syncthreads();
+    float sr[4] = {0.f, 0.f, 0.f, 0.f}, cr[4] = {0.f, 0.f, 0.f, 0.f};
+    float si[4] = {0.f, 0.f, 0.f, 0.f}, ci[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int m0 = 0; m0 < Mid; m0 += kEc2M) {
+      const int mc = Mid - m0 < kEc2M ? Mid - m0 : kEc2M;
+      for (int e = threadIdx.x; e < kEc2T * kEc2M; e += blockDim.x) {
+        const int r = e / kEc2M, mm = e - r * kEc2M;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mm < mc && row_a[r] >= 0) {
+          const int64_t pa = row_a[r] + (int64_t)mid_a[m0 + mm] * a_sd;
+          const float2 h = Aa[pa], l = Aa[loa + pa];
+          v = make_float4(h.x, h.y, l.x, l.y);
+        }
+        As[r][mm] = v;
+      }
+      for (int e = threadIdx.x; e < kEc2M * kEc2T; e += blockDim.x) {
+        const int mm = e / kEc2T, c = e - mm * kEc2T;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mm < mc && col_b[c] >= 0) {
+          const int64_t pb = col_b[c] + (int64_t)mid_b[m0 + mm] * b_su;
+          const float2 h = Ab[pb], l = Ab[lob + pb];
+          v = make_float4(h.x, h.y, l.x, l.y);
+        }
+        Bs[mm][c] = v;
+      }
+      __syncthreads();
+      for (int mm = 0; mm < mc; ++mm) {
+        const float4 b = Bs[mm][cc];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 a = As[rq + 8 * i][mm];
+          // re = ar br - ai bi, im = ar bi + ai br (hi products exact, cross terms
+          // hi lo + lo hi in the correction)
+          acc_prod(a.x, b.x, sr[i], cr[i]);
+          acc_prod(-a.y, b.y, sr[i], cr[i]);
+          acc_prod(a.x, b.y, si[i], ci[i]);
+          acc_prod(a.y, b.x, si[i], ci[i]);
+          cr[i] = fmaf(a.x, b.z, fmaf(a.z, b.x, cr[i]));
+          cr[i] = fmaf(-a.y, b.w, fmaf(-a.w, b.y, cr[i]));
+          ci[i] = fmaf(a.x, b.w, fmaf(a.z, b.y, ci[i]));
+          ci[i] = fmaf(a.y, b.z, fmaf(a.w, b.x, ci[i]));
+        }
+      }
+      __syncthreads();
     }
-    Ec[i] = make_float2(sr + cr, si + ci);
+    if (col_b[cc] >= 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = rq + 8 * i;
+        if (row_a[r] >= 0) Ec[row_out[r] + col_out[cc]] = make_float2(sr[i] + cr[i], si[i] + ci[i]);
+      }
+    }
+    __syncthreads();   // the next tile rewrites the row and column tables
   }
 }
 
@@ -290,12 +348,11 @@ cudaError_t launch_tensor_operand(const TensorOpEntry *d_entry, int n_entries, i
 cudaError_t launch_build_operands2(const OpBuild2Entry *d_entries, int n, int max_kn,
                                    OpDesc *d_ops, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  // about 4096 blocks in all (a few per SM and resident set), each thread
-  // looping over several entries of W so that a block's index tables (set up
-  // once per block) serve many of them
-  int blocks = (max_kn + 255) / 256;
-  const int share = (4096 + n - 1) / n;
-  if (blocks > share) blocks = share < 16 ? 16 : share;
+  // 32 x 32 tiles of W; about 2048 blocks in all, each walking several tiles
+  // of its entry so that its index tables (set up once per block) serve them
+  int blocks = (max_kn + 1023) / 1024 + 1;
+  const int share = (2048 + n - 1) / n;
+  if (blocks > share) blocks = share < 8 ? 8 : share;
   if (blocks > 2048) blocks = 2048;
   if (blocks < 1) blocks = 1;
   k_build_ec2<<<dim3(blocks, n), 256, 0, s>>>(d_entries, d_ops);
