@@ -179,7 +179,10 @@ struct Plan {
   int small_cap_g = 0, small_cap_e = 0;
   size_t off_small_steps = 0, off_small_opbase = 0;
   const uint64_t *small_bits = nullptr;
-  bool evo_sites = false;
+  bool evo_sites = false;       // the whole evolution in one launch
+  int evo_prefix = 0;           // leading gate batches done by that launch (a block
+                                // per site) while every site tensor is small; the
+                                // rest one launch per batch
   size_t off_evo_refs = 0, off_evo_first = 0;
 
   // host copy of the tables (uploaded once): [off_site_ptrs, off_ops_begin)
@@ -188,15 +191,16 @@ struct Plan {
   std::vector<unsigned char> blob;
   size_t off_ops_begin = 0;
 
-  // CUDA graph of the whole launch sequence (PEPS_FLAG_GRAPH); with timing
-  // events around its contraction launches (graph_timed)
-  cudaGraphExec_t graph_exec = nullptr;
-  bool graph_timed = false;
+  // CUDA graphs of the whole launch sequence (PEPS_FLAG_GRAPH): [0] plain,
+  // [1] with timing events around its contraction launches; each captured
+  // on its first use
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
   size_t graph_n_timed = 0;
   std::vector<int> graph_timed_idx;   // launch index of each timed launch
 
   ~Plan() {
-    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    for (auto g : graph_exec)
+      if (g) cudaGraphExecDestroy(g);
     for (auto &l : launches)
       if (l.tc_handle) tc_release(l.tc_handle);
   }
@@ -1419,6 +1423,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   std::vector<Gate2Entry> g2e;
   P.evo.clear();
   std::vector<std::vector<EvoRef>> site_refs(NQ);
+  std::vector<std::vector<int>> site_ref_batch(NQ);   // the batch of each reference
   {
     std::vector<int> cur(NQ, 0);
     std::vector<int> dims(4 * NQ, 1);
@@ -1459,6 +1464,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
                                   (float)(g.U[2 * i + 1] - (double)hi_));
         }
         site_refs[q].push_back(EvoRef{0, (int32_t)g1.size()});
+        site_ref_batch[q].push_back(batch_id);
         g1.push_back(e);
         eb.n++;
         eb.max_work = std::max(eb.max_work, e.half);
@@ -1490,6 +1496,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
               2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
           cur[q] ^= 1;
           site_refs[q].push_back(EvoRef{2, (int32_t)g2e.size()});
+          site_ref_batch[q].push_back(batch_id);
           g2e.push_back(e);
           eb.n++;
           eb.max_work = std::max(eb.max_work, out_n);
@@ -1515,6 +1522,7 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
               2LL * dims[4 * q] * dims[4 * q + 1] * dims[4 * q + 2] * dims[4 * q + 3];
           cur[q] ^= 1;
           site_refs[q].push_back(EvoRef{1, (int32_t)cz.size()});
+          site_ref_batch[q].push_back(batch_id);
           cz.push_back(e);
           eb.n++;
           eb.max_work = std::max(eb.max_work, out_n);
@@ -1531,20 +1539,24 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
   P.off_g1 = off; off = align_up(off + std::max<size_t>(g1.size(), 1) * sizeof(Gate1Entry));
   P.off_cz = off; off = align_up(off + std::max<size_t>(cz.size(), 1) * sizeof(CzEntry));
   P.off_g2 = off; off = align_up(off + std::max<size_t>(g2e.size(), 1) * sizeof(Gate2Entry));
-  // the whole evolution as one launch (a block per site) where every site
-  // tensor is small enough for one block
+  // The evolution's leading gate batches, while every site tensor they touch
+  // is small enough for one block (16384 entries), run as one launch with a
+  // block per site (each site evolves through its own gate halves only); the
+  // rest one launch per batch.  All of it in that launch when every site
+  // tensor stays small.
+  P.evo_prefix = 0;
+  if (!(o.flags & PEPS_FLAG_STEPWISE))
+    while (P.evo_prefix < (int)P.evo.size() && P.evo[P.evo_prefix].max_work <= 16384)
+      ++P.evo_prefix;
+  P.evo_sites = P.evo_prefix == (int)P.evo.size();
   std::vector<EvoRef> evo_refs;
   std::vector<int32_t> evo_first(NQ + 1, 0);
   for (int q = 0; q < NQ; ++q) {
     evo_first[q] = (int32_t)evo_refs.size();
-    evo_refs.insert(evo_refs.end(), site_refs[q].begin(), site_refs[q].end());
+    for (size_t i = 0; i < site_refs[q].size(); ++i)
+      if (site_ref_batch[q][i] < P.evo_prefix) evo_refs.push_back(site_refs[q][i]);
   }
   evo_first[NQ] = (int32_t)evo_refs.size();
-  {
-    int64_t big = 0;
-    for (int q = 0; q < NQ; ++q) big = std::max(big, P.site_elems[q]);
-    P.evo_sites = big <= 16384 && !(o.flags & PEPS_FLAG_STEPWISE);
-  }
   P.off_evo_refs = off; off = align_up(off + std::max<size_t>(evo_refs.size(), 1) * sizeof(EvoRef));
   P.off_evo_first = off; off = align_up(off + (size_t)(NQ + 1) * sizeof(int32_t));
   P.off_ops_begin = off;
@@ -2337,7 +2349,7 @@ static int ensure_events(peps_ctx *c, size_t n) {
 // Launch counters of one graph replay (the same sequence as an eager call
 // with the evolution included).
 static int enqueue_sequence_stats_only(Plan &P, peps_stats &S) {
-  S.launches_evolve = P.evo_sites ? 1 : 1 + (int64_t)P.evo.size();
+  S.launches_evolve = 1 + (int64_t)P.evo.size() - P.evo_prefix;
   if (P.opts.prefix_cols > 0 && P.n > 0) S.launches_finalize++;
   bool any_tc = false;
   for (auto &l : P.launches) any_tc |= (l.kind == 0 && l.tc);
@@ -2387,20 +2399,22 @@ static int enqueue_sequence(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cud
   DeviceStatus *st = (DeviceStatus *)(base + P.off_status);
   const int64_t wd_ns = P.opts.watchdog_ns > 0 ? P.opts.watchdog_ns : 2000000000LL;
   CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(DeviceStatus), s));
-  if (rebuild && P.evo_sites) {
-    CUDA_TRY(launch_evolve_sites((const Gate1Entry *)(base + P.off_g1),
-                                 (const CzEntry *)(base + P.off_cz),
-                                 (const Gate2Entry *)(base + P.off_g2),
-                                 (const EvoRef *)(base + P.off_evo_refs),
-                                 (const int32_t *)(base + P.off_evo_first),
-                                 (float2 *const *)(base + P.off_site_ptrs),
+  if (rebuild) {
+    // the leading batches (sites initialised there too), then the rest
+    if (P.evo_prefix > 0)
+      CUDA_TRY(launch_evolve_sites((const Gate1Entry *)(base + P.off_g1),
+                                   (const CzEntry *)(base + P.off_cz),
+                                   (const Gate2Entry *)(base + P.off_g2),
+                                   (const EvoRef *)(base + P.off_evo_refs),
+                                   (const int32_t *)(base + P.off_evo_first),
+                                   (float2 *const *)(base + P.off_site_ptrs),
+                                   (const int64_t *)(base + P.off_site_lo), c->n, st, s));
+    else
+      CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
                                  (const int64_t *)(base + P.off_site_lo), c->n, st, s));
     S.launches_evolve++;
-  } else if (rebuild) {
-    CUDA_TRY(launch_init_sites((float2 *const *)(base + P.off_site_ptrs),
-                               (const int64_t *)(base + P.off_site_lo), c->n, st, s));
-    S.launches_evolve++;
-    for (auto &eb : P.evo) {
+    for (size_t bi = (size_t)P.evo_prefix; bi < P.evo.size(); ++bi) {
+      const Plan::EvoBatch &eb = P.evo[bi];
       if (eb.kind == 0)
         CUDA_TRY(launch_gate1((const Gate1Entry *)(base + P.off_g1) + eb.off, eb.n, eb.max_work, s));
       else if (eb.kind == 1)
@@ -2559,15 +2573,12 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
 
   if (graph) {
     // the graph always contains the evolution, so a replay never depends on
-    // what an earlier call left in the site tensors.  With TIMING the capture
-    // also records the events around every contraction launch (event-record
-    // nodes), so that a replay times its own launches; a graph captured
-    // without them is captured again when timing is asked for.
-    if (P.graph_exec && timing && !P.graph_timed) {
-      CUDA_TRY(cudaGraphExecDestroy(P.graph_exec));
-      P.graph_exec = nullptr;
-    }
-    if (!P.graph_exec) {
+    // what an earlier call left in the site tensors.  With TIMING the replay
+    // is of a second graph whose capture also recorded the events around
+    // every contraction launch (event-record nodes), so that it times its
+    // own launches; the plain graph carries no events.
+    cudaGraphExec_t &gx = P.graph_exec[timing ? 1 : 0];
+    if (!gx) {
       for (auto &l : P.launches)
         if (l.kind == 0 && l.tc) CUDA_TRY(tc_warm(l.tc_handle));
       if (timing) {
@@ -2580,10 +2591,13 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
       cudaStream_t cs = c->cap_stream;
       CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       peps_stats S2{};
-      P.graph_n_timed = 0;
-      P.graph_timed_idx.clear();
-      int rc = enqueue_sequence(c, P, d_bits_in, cs, true, timing, S2, &P.graph_n_timed,
-                                &P.graph_timed_idx, true);
+      size_t n_t = 0;
+      std::vector<int> t_idx;
+      int rc = enqueue_sequence(c, P, d_bits_in, cs, true, timing, S2, &n_t, &t_idx, true);
+      if (timing) {
+        P.graph_n_timed = n_t;
+        P.graph_timed_idx = t_idx;
+      }
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (rc) {
@@ -2591,12 +2605,11 @@ static int run_plan(peps_ctx *c, Plan &P, const uint64_t *d_bits_in, cudaStream_
         return rc;
       }
       CUDA_TRY(e);
-      e = cudaGraphInstantiate(&P.graph_exec, g, 0);
+      e = cudaGraphInstantiate(&gx, g, 0);
       cudaGraphDestroy(g);
       CUDA_TRY(e);
-      P.graph_timed = timing;
     }
-    CUDA_TRY(cudaGraphLaunch(P.graph_exec, s));
+    CUDA_TRY(cudaGraphLaunch(gx, s));
     int rc = enqueue_sequence_stats_only(P, S);
     if (rc) return rc;
     if (timing) {

@@ -116,7 +116,6 @@ struct __align__(64) TcParams {
   Div d_tpi, d_tn;             // tiles per item, column tiles
   Div d_hper, d_lper, d_ph;    // m_hi-major tiles: P / ph, (Mr / P) / lh, ph
   Div d_Mr, d_Mlo, d_dv, d_dh; // output rows per batch slice, Mr / P, dim(v'), dim(h')
-  int stg_bytes;  // shared memory for the epilogue's store transpose (0: none)
 };
 
 // ---------------------------------------------------------------------------
@@ -416,8 +415,7 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
   const uint32_t a_bytes = BM * ROWB;
   const uint32_t b_bytes = (uint32_t)BNL * ROWB;
   const uint32_t stage_bytes = NP * (a_bytes + b_bytes);  // this CTA's share
-  uint4 *stg = (uint4 *)(smem + (size_t)S * stage_bytes);  // epilogue store transpose
-  uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes + p.stg_bytes);
+  uint64_t *bars = (uint64_t *)(smem + (size_t)S * stage_bytes);
   uint64_t *full = bars;
   uint64_t *empty = bars + S;
   uint64_t *tfull = bars + 2 * S;
@@ -814,49 +812,6 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
             for (int i = 0; i < 16; ++i) o[i] += __uint_as_float(rc[i]);
           }
         };
-        // Pairs of chunks whose 16 entries are one contiguous run (R a multiple
-        // of 16, nothing dead in the warp) go through shared memory: each lane
-        // writes its four 16-byte pieces (per plane), then lane l stores piece
-        // l & 3 of source lane s(l / 4 + 8 j), j = 0..3, to that source's
-        // run.  Sources are taken m_hi fastest where a warp's rows span several
-        // m_hi (Mr / P < 32), so that a store instruction covers neighbouring
-        // runs; the pieces are swizzled (slot p ^ ((lane >> 1) & 3)) so that
-        // both shared-memory passes are free of bank conflicts.
-        const bool tpose = p.stg_bytes > 0 && W == 8 && R % 16 == 0 && __all_sync(0xffffffffu, live);
-        const int mlo_w = (int)p.d_Mlo.d;
-        const int G = (mlo_w < 32 && 32 % mlo_w == 0) ? 32 / mlo_w : 1;
-        uint4 *wbuf = stg + (size_t)ew * 256;   // [plane][lane][4 pieces]
-        auto store_pair_t = [&](int c, const Packed8<FMT> &w0, const Packed8<FMT> &w1) {
-          constexpr int NPL = (FMT == FMT_BF16X2 || FMT == FMT_FP16X2) ? 2 : 1;
-          const int sw = (lane >> 1) & 3;
-#pragma unroll
-          for (int pl = 0; pl < NPL; ++pl) {
-            const uint32_t *a = w0.w + 8 * pl, *b = w1.w + 8 * pl;
-            uint4 *row = wbuf + pl * 128 + lane * 4;
-            row[0 ^ sw] = make_uint4(a[0], a[1], a[2], a[3]);
-            row[1 ^ sw] = make_uint4(a[4], a[5], a[6], a[7]);
-            row[2 ^ sw] = make_uint4(b[0], b[1], b[2], b[3]);
-            row[3 ^ sw] = make_uint4(b[4], b[5], b[6], b[7]);
-          }
-          const int nc0 = (nt * BN + c) >> 1;
-          const int64_t dest = base + dR.q(nc0) * stride_q + dR.r(nc0);   // run start, entries
-          __syncwarp();
-          const int pc = lane & 3;
-          uint32_t *Dw = reinterpret_cast<uint32_t *>(D);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int i = (lane >> 2) + 8 * j;
-            const int src = G > 1 ? (i % G) * mlo_w + i / G : i;
-            const int64_t ds = __shfl_sync(0xffffffffu, dest, src);
-            const int slot = src * 4 + (pc ^ ((src >> 1) & 3));
-#pragma unroll
-            for (int pl = 0; pl < NPL; ++pl) {
-              const uint4 v = wbuf[pl * 128 + slot];
-              *reinterpret_cast<uint4 *>(Dw + (pl ? p.sh.plane / 2 : 0) + ds + 4 * pc) = v;
-            }
-          }
-          __syncwarp();   // the pieces are read before the next pair overwrites them
-        };
         if (EPI == 4) {
           // two chunks per iteration (twice the independent work in flight);
           // the next pair's TMEM loads overlap this pair's arithmetic
@@ -877,11 +832,7 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
             }
             add_segments(c, o0);
             if (two) add_segments(c + 16, o1);
-            if (tpose && two) {
-              Packed8<FMT> w0, w1;
-              vmax = fmaxf(vmax, fmaxf(pack8<FMT>(o0, sc, w0), pack8<FMT>(o1, sc, w1)));
-              store_pair_t(c, w0, w1);
-            } else if (live) {
+            if (live) {
               emit(c, o0);
               if (two) emit(c + 16, o1);
             }
@@ -1171,6 +1122,11 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   while (cols < d->prm.nbuf * BN * NA) cols *= 2;
   d->prm.tmem_cols = cols;
   const int stage_bytes = np * (BM + BN / d->cg) * rowb;  // this CTA's share
+  // 227 KiB per CTA, less the 1 KiB alignment pad and the barriers
+  const int budget = 227 * 1024 - 1024 - 256;
+  int stages = budget / stage_bytes;
+  if (stages > 8) stages = 8;
+  d->prm.stages = stages;
   // Epilogue warps (measured on the square partition's steps): four where
   // wide tiles store runs of 8 entries (each warp keeps two chunks in
   // flight), eight where the stores go out 1 to 4 entries at a time, where
@@ -1178,19 +1134,6 @@ int tc_prepare(const StepShape &sh, int fmt, const void *a_base, int a_lanes,
   const bool runs8 = !sh.dot && ((!sh.vb && sh.dv_out % 8 == 0) ||
                                  (sh.vb && sh.nvs && sh.P == 1 && sh.dh_out % 8 == 0));
   d->epi = epi == 4 || epi == 8 ? epi : ((runs8 && BN >= 256) ? 4 : 8);
-  // Four epilogue warps whose stores are runs of 16 entries (4 bytes per entry
-  // and plane) pass each pair of chunks through shared memory, so that a
-  // warp's store instruction covers 512 contiguous bytes where the layout
-  // allows: 4 KiB per warp (32 lanes x 4 pieces of 16 bytes x 2 planes)
-  const bool runs16 = !sh.dot && ((!sh.vb && sh.dv_out % 16 == 0) ||
-                                  (sh.vb && sh.nvs && sh.P == 1 && sh.dh_out % 16 == 0));
-  const bool w4 = fmt == FMT_FP16X2 || fmt == FMT_BF16X2 || fmt == FMT_FP16 || fmt == FMT_BF16;
-  d->prm.stg_bytes = (d->epi == 4 && runs16 && w4 && BN >= 32) ? 4 * 4096 : 0;
-  // 227 KiB per CTA, less the 1 KiB alignment pad, the barriers and the transpose
-  const int budget = 227 * 1024 - 1024 - 256 - d->prm.stg_bytes;
-  int stages = budget / stage_bytes;
-  if (stages > 8) stages = 8;
-  d->prm.stages = stages;
   *out_handle = d;
   return stages >= 2 ? 0 : -5;
 }
@@ -1322,7 +1265,7 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
   const int units = pair_tiles * cg < sm_count ? pair_tiles * cg : sm_count;
   const int np = np_of(prm.sh.fmt);
   const size_t smem = (size_t)prm.stages * np * (BM + prm.BN / cg) * d->rowb + 1024 +
-                      prm.stg_bytes + (2 * prm.stages + 6) * 8 + 16;
+                      (2 * prm.stages + 6) * 8 + 16;
   switch (prm.sh.fmt) {
     case FMT_BF16: return launch_fmt<FMT_BF16>(prm, d->rowb, cg, d->epi, units, smem, s);
     case FMT_FP16: return launch_fmt<FMT_FP16>(prm, d->rowb, cg, d->epi, units, smem, s);
@@ -1344,10 +1287,22 @@ __global__ void k_build_bt(OpDesc *ops) {
   const int K = op.K, N = op.N;
   const int64_t Kr = 2 * (int64_t)K, Nr = 2 * (int64_t)N;
   const float sc = ldexpf(1.f, op.b_t);
+  // 32-bit index arithmetic below 2^31 real entries (64-bit division runs as a
+  // long instruction sequence); larger operands take the 64-bit form
+  const bool narrow = Kr * Nr < ((int64_t)1 << 31);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Kr * Nr;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t nr = i / Kr, kr = i - nr * Kr;
-    const int k = kr >> 1, a = kr & 1, n = nr >> 1, b = nr & 1;
+    int64_t nr, kr;
+    if (narrow) {
+      const uint32_t i32 = (uint32_t)i, k32 = (uint32_t)Kr;
+      const uint32_t q = i32 / k32;
+      nr = q;
+      kr = i32 - q * k32;
+    } else {
+      nr = i / Kr;
+      kr = i - nr * Kr;
+    }
+    const int k = (int)(kr >> 1), a = (int)(kr & 1), n = (int)(nr >> 1), b = (int)(nr & 1);
     const float2 e = op.Ec[(int64_t)k * N + n];
     float v;
     if (b == 0) v = a == 0 ? e.x : -e.y;
@@ -1429,10 +1384,22 @@ __global__ void k_tensor_bt(const TensorOpEntry *__restrict__ e, int64_t plane, 
   OpDesc &op = ops[g.op];
   const int64_t K = g.K, N = g.N;
   const float sc = pow2f(-g.target), sb = ldexpf(1.f, op.b_t);
+  const bool narrow = K * N < ((int64_t)1 << 31) && g.Nlo < ((int64_t)1 << 31);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K * N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = i / K, k = i - n * K;
-    const int64_t nh = n / g.Nlo, nl = n - nh * g.Nlo;
+    int64_t n, k, nh, nl;
+    if (narrow) {   // 32-bit index arithmetic
+      const uint32_t i32 = (uint32_t)i, n32 = i32 / (uint32_t)K, lo = (uint32_t)g.Nlo;
+      n = n32;
+      k = i32 - n32 * (uint32_t)K;
+      nh = n32 / lo;
+      nl = n32 - (uint32_t)nh * lo;
+    } else {
+      n = i / K;
+      k = i - n * K;
+      nh = n / g.Nlo;
+      nl = n - nh * g.Nlo;
+    }
     const float2 v = load_g<FMT>(g.G, k * g.ks + nh * g.ns_hi + nl * g.ns, plane);
     const float re = (v.x * sc) * sb, im = (v.y * sc) * sb;
     // row 2n holds (re, -im) at columns 2k, 2k+1; row 2n+1 holds (im, re)
