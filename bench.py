@@ -110,7 +110,7 @@ def measured_traffic(scheme, algorithmic_bytes_per_launch):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="fp16x3")
@@ -416,16 +416,20 @@ def run_mine(args):
                     "tc_cluster": int(t[2]), "tc_epi": int(t[3])}
         kw.update(best)
         tuned = dict(tuned or {}, tile=best, tile_trials=log)
-    # every step replays the call's CUDA graph (circuit evolution included),
-    # which also records the events around each contraction launch
-    flags = B.PEPS_FLAG_GRAPH | B.PEPS_FLAG_TIMING
+    # every step replays the call's CUDA graph (circuit evolution included);
+    # the first and the last timed steps also record events around each
+    # contraction launch (the graph with its 2 x 21 event nodes; reading them
+    # back synchronises), which give the per-launch times of the roofline
+    flags = B.PEPS_FLAG_GRAPH
+    timed_event_steps = {0, args.steps - 1}
 
-    def step(s):
-        sim.amplitudes_device(d_bits, d_out, stream=s, flags=flags, **kw)
+    def step(s, events=True):
+        f = flags | (B.PEPS_FLAG_TIMING if events else 0)
+        sim.amplitudes_device(d_bits, d_out, stream=s, flags=f, **kw)
 
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step(stream)
+        for i in range(args.warmup):   # both graphs (with and without events) captured here
+            step(stream, events=i == 0)
     stream.synchronize()
     if pg:
         pg.barrier()
@@ -438,16 +442,18 @@ def run_mine(args):
     torch.cuda.synchronize(dev)
     ev0.record(stream)
     tc_log = []   # (flops, bytes, ms) of every tensor-core contraction launch
-    for _ in range(args.steps):
-        step(stream)
+    for i in range(args.steps):
+        ev = i in timed_event_steps
+        step(stream, events=ev)
         st = sim.stats()
-        tc_ms += st["contract_tc_ms"]
-        tc_launches += st["launches_contract_tc"]
-        tc_flops += st["contract_tc_flops"]
-        tc_bytes += st["contract_tc_bytes"]
         launches += st["launches_total"]
-        tc_log += [(r["flops"], r["bytes"], r["ms"]) for r in B.peps_launch_log(sim.h)
-                   if r["tensor_cores"]]
+        if ev:
+            tc_ms += st["contract_tc_ms"]
+            tc_launches += st["launches_contract_tc"]
+            tc_flops += st["contract_tc_flops"]
+            tc_bytes += st["contract_tc_bytes"]
+            tc_log += [(r["flops"], r["bytes"], r["ms"]) for r in B.peps_launch_log(sim.h)
+                       if r["tensor_cores"]]
     ev1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize(dev)

@@ -93,9 +93,10 @@ enum {
     PEPS_FLAG_GRAPH = 8,    /* capture the call's launch sequence (evolution
                                included) into a CUDA graph on the first call
                                and replay it on later calls with the same
-                               plan; with PEPS_FLAG_TIMING the graph also
-                               records the events around its contraction
-                               launches, and each replay reports their times */
+                               plan; with PEPS_FLAG_TIMING a second graph
+                               that also records the events around its
+                               contraction launches (captured on its first
+                               use) is replayed, and reports their times */
     PEPS_FLAG_MARGINALS = 16, /* return marginal probabilities P(x_S) =
                                <psi| Pi_S |psi> instead of amplitudes: S = the
                                set bits of opts.measured_mask, their values

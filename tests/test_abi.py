@@ -343,3 +343,18 @@ def test_plan_steps_report_a_consistent_output_layout():
         # on the tensor cores the last merge forms the dot product in its epilogue
         assert [s["fused_dot"] for s in steps] == [0] * (len(steps) - 1) + [int(scheme == "quadrants")]
     B.peps_destroy(h)
+
+
+def test_tensor_core_tuning_knobs_are_validated():
+    # K bytes per stage 0/64/128, CTA pairing 0/1/2, epilogue warps 0/4/8;
+    # anything else is refused before any device work
+    c, h = make(4, 4, 8, 1)
+    for kw in ({"tc_kchunk": 64}, {"tc_cluster": 1}, {"tc_epi": 4}, {"tc_epi": 8}, {"tc_epi": 0}):
+        o, k = B.make_opts(precision="fp16x3", **kw)
+        B.peps_plan_info_get(h, 16, o)
+    for kw in ({"tc_kchunk": 32}, {"tc_cluster": 3}, {"tc_epi": 6}, {"tc_epi": -1}):
+        o, k = B.make_opts(precision="fp16x3", **kw)
+        with pytest.raises(B.PepsError) as e:
+            B.peps_plan_info_get(h, 16, o)
+        assert "tc_epi" in str(e.value)
+    B.peps_destroy(h)
