@@ -1996,8 +1996,6 @@ static int build_plan(peps_ctx *c, int64_t n, const peps_opts &o, const void *ws
 
   // ---- resolve addresses and assemble the table blob ----
   char *base = (char *)ws;
-  const DeviceStatus *st = (const DeviceStatus *)(base + P.off_status);
-  (void)st;
   const uint64_t *bsrc = host_bits ? (const uint64_t *)(base + P.off_bits) : bits_dev;
   P.small_bits = bsrc;
   for (size_t i = 0; i < items.size(); ++i) {

@@ -79,7 +79,7 @@ inline Div make_div(int64_t d) {
   return v;
 }
 
-struct __align__(64) TcParams {
+struct __align__(128) TcParams {   // the tensor maps need 128-byte alignment
   CUtensorMap mapA;        // {k, m, plane, lane}; m_hi-major steps: {k, m_hi, m_lo, b, plane/lane}
   CUtensorMap mapB[2];     // [plane] {k, n, operand variant}
   StepShape sh;
@@ -260,14 +260,6 @@ __device__ __forceinline__ void tma_load_5d_cg2(void *dst, const CUtensorMap *ma
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar_cluster_addr)
       : "memory");
 }
-__device__ __forceinline__ void tma_load_2d_cg2(void *dst, const CUtensorMap *map,
-                                                uint32_t bar_cluster_addr, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar_cluster_addr)
-      : "memory");
-}
 __device__ __forceinline__ void tma_load_3d_cg2(void *dst, const CUtensorMap *map,
                                                 uint32_t bar_cluster_addr, int c0, int c1,
                                                 int c2) {
@@ -283,14 +275,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -657,7 +641,7 @@ __global__ void __launch_bounds__(threads_of(EPI), 1)
     const int c_end = idle ? 0 : (split_cols ? c_begin + p.BN / 2 : p.BN);
     const int dv = p.sh.dv_out, dh = p.sh.dh_out;
     const int64_t M = p.sh.M, P = p.sh.P;
-    const int64_t Mr = p.sh.Mr > 0 ? p.sh.Mr : M, Mlo = Mr / P;
+    const int64_t Mr = p.sh.Mr > 0 ? p.sh.Mr : M;
     const int64_t MrN = Mr * (int64_t)p.sh.N, Mrdh = Mr * (int64_t)dh;
     const bool vbm = p.sh.vb != 0;
     uint32_t local = 0;
@@ -1281,48 +1265,47 @@ cudaError_t launch_contract_tc(void *handle, const StepItem *d_items, int n_item
 // into the form's planes, K-major [Nr][Kr].  Also the bound beta_t.
 // ---------------------------------------------------------------------------
 template <int FMT>
-__global__ void k_build_bt(OpDesc *ops) {
+__global__ void __launch_bounds__(256) k_build_bt(OpDesc *ops) {
   OpDesc &op = ops[blockIdx.y];
   if (op.Bt[0] == nullptr) return;
   const int K = op.K, N = op.N;
-  const int64_t Kr = 2 * (int64_t)K, Nr = 2 * (int64_t)N;
   const float sc = ldexpf(1.f, op.b_t);
-  // 32-bit index arithmetic below 2^31 real entries (64-bit division runs as a
-  // long instruction sequence); larger operands take the 64-bit form
-  const bool narrow = Kr * Nr < ((int64_t)1 << 31);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Kr * Nr;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t nr, kr;
-    if (narrow) {
-      const uint32_t i32 = (uint32_t)i, k32 = (uint32_t)Kr;
-      const uint32_t q = i32 / k32;
-      nr = q;
-      kr = i32 - q * k32;
-    } else {
-      nr = i / Kr;
-      kr = i - nr * Kr;
+  // 32 x 32 complex tiles of Ec through shared memory: read along n, written
+  // along k, two real columns (a = 0, 1 of one k) per store
+  __shared__ float2 tile[32][33];
+  const int tn = (N + 31) / 32, n_tiles = ((K + 31) / 32) * tn;
+  const int64_t Kr = 2 * (int64_t)K;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int k0 = (t / tn) * 32, n0 = (t % tn) * 32;
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int kk = e >> 5, nn = e & 31;
+      tile[kk][nn] = (k0 + kk < K && n0 + nn < N) ? op.Ec[(int64_t)(k0 + kk) * N + n0 + nn]
+                                                    : make_float2(0.f, 0.f);
     }
-    const int k = (int)(kr >> 1), a = (int)(kr & 1), n = (int)(nr >> 1), b = (int)(nr & 1);
-    const float2 e = op.Ec[(int64_t)k * N + n];
-    float v;
-    if (b == 0) v = a == 0 ? e.x : -e.y;
-    else v = a == 0 ? e.y : e.x;
-    v *= sc;
-    if (FMT == FMT_TF32) {
-      ((float *)op.Bt[0])[i] = round_tf32(v);
-    } else if (FMT == FMT_BF16) {
-      ((__nv_bfloat16 *)op.Bt[0])[i] = __float2bfloat16_rn(v);
-    } else if (FMT == FMT_FP16) {
-      ((__half *)op.Bt[0])[i] = __float2half_rn(v);
-    } else if (FMT == FMT_BF16X2) {
-      __nv_bfloat16 h = __float2bfloat16_rn(v);
-      ((__nv_bfloat16 *)op.Bt[0])[i] = h;
-      ((__nv_bfloat16 *)op.Bt[1])[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-    } else {
-      __half h = __float2half_rn(v);
-      ((__half *)op.Bt[0])[i] = h;
-      ((__half *)op.Bt[1])[i] = __float2half_rn(v - __half2float(h));
+    __syncthreads();
+    const int kk = threadIdx.x & 31, k = k0 + kk;
+    for (int r = threadIdx.x >> 5; r < 64; r += blockDim.x >> 5) {
+      const int nn = r >> 1, b = r & 1, n = n0 + nn;
+      if (k >= K || n >= N) continue;
+      // row 2n holds (re, -im) at columns 2k, 2k+1; row 2n+1 holds (im, re)
+      const float2 e = tile[kk][nn];
+      const float v0 = (b == 0 ? e.x : e.y) * sc, v1 = (b == 0 ? -e.y : e.x) * sc;
+      const int64_t w = ((int64_t)(2 * n + b) * Kr + 2 * (int64_t)k) >> 1;   // in column pairs
+      if (FMT == FMT_TF32) {
+        ((float2 *)op.Bt[0])[w] = make_float2(round_tf32(v0), round_tf32(v1));
+      } else if (FMT == FMT_BF16) {
+        ((uint32_t *)op.Bt[0])[w] = pack_bf16(v0, v1);
+      } else if (FMT == FMT_FP16) {
+        ((uint32_t *)op.Bt[0])[w] = pack_f16(v0, v1);
+      } else {
+        constexpr bool BF = FMT == FMT_BF16X2;
+        uint32_t h, l;
+        split16<BF>(make_float2(v0, v1), h, l);
+        ((uint32_t *)op.Bt[0])[w] = h;
+        ((uint32_t *)op.Bt[1])[w] = l;
+      }
     }
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // beta_t = beta_c * 2^b_t (beta_c already carries a rounding margin; the
@@ -1463,7 +1446,8 @@ cudaError_t launch_tensor_operand_tc(const TensorOpEntry *d_entry, int n_entries
 cudaError_t launch_build_tc_operands(int n, int64_t max_kn, OpDesc *d_ops, int fmt,
                                      cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  int64_t blocks = (4 * max_kn + 255) / 256;
+  // 32 x 32 tiles of the largest operand (ops with fewer tiles leave early)
+  int64_t blocks = (max_kn + 1023) / 1024 + 2;
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
   dim3 grid(blocks, n);
