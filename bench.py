@@ -49,9 +49,10 @@ REL_ERR_GATE = 1e-5
 # the workload, identical in both arms' lines
 CONFIG = {"workload": "6x6 (1+32+1), 512 bitstrings = 8 groups x 64 sharing columns 0-2",
           "seed": 4, "bitstrings": 512,
-          "l2": "inputs larger than L2: running tensors of up to 2^23 entries (64 MiB) x 4 "
-                "buffers per lane x 64 lanes (17 GB) for the square partition, 2 GiB per lane "
-                "for the column sweep"}
+          "l2": "inputs larger than L2: with held and linked bits the square partition's "
+                "running tensors have up to 2^22 entries (32 MiB) per lane, 4 buffers per lane "
+                "x 512 lanes, 70 GB of workspace; the column sweep's up to 2^25 (256 MiB) "
+                "per lane"}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_6x6_d32.json")
 
 
