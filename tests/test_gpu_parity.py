@@ -355,3 +355,20 @@ def test_fused_rows_with_prefix_and_slices(sim_factory):
         for prec in ("fp32", "fp16x3"):
             a = sim.amplitudes(bits, precision=prec, **kw)
             assert relerr(a, ref) < SPLIT_TOL, (kw, prec)
+
+
+def test_evolution_prefix_matches_per_layer_launches(sim_factory):
+    # 6x6 (1+32+1): the evolution's leading layers, while every site tensor is
+    # small, run as one launch (a block per site); the rest one launch per
+    # layer.  STEPWISE takes one launch per layer throughout: the same
+    # arithmetic per entry, so the amplitudes are bit-identical
+    circ, bits = workload("6x6_d32")
+    sim = sim_factory(circ)
+    kw = dict(precision="fp16x3", scheme="quadrants", hold_ties=True)
+    f = B.PEPS_FLAG_REBUILD | B.PEPS_FLAG_TIMING
+    a = sim.amplitudes(bits[:4], flags=f, **kw)
+    ev_a = sim.stats()["launches_evolve"]
+    b = sim.amplitudes(bits[:4], flags=f | B.PEPS_FLAG_STEPWISE, **kw)
+    ev_b = sim.stats()["launches_evolve"]
+    assert np.array_equal(a, b)
+    assert 1 < ev_a < ev_b
