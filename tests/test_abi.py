@@ -358,3 +358,21 @@ def test_tensor_core_tuning_knobs_are_validated():
             B.peps_plan_info_get(h, 16, o)
         assert "tc_epi" in str(e.value)
     B.peps_destroy(h)
+
+
+def test_square_partition_merges_share_launches():
+    # 6x6 (1+32+1), 8 groups of 64: the groups' left halves (and their merge
+    # F_l) in one launch per step, and one launch of the last merge per chunk
+    # of member lanes, whatever groups the chunk spans
+    c, h = make(6, 6, 32, 4)
+    for lanes, chunks in ((512, 1), (64, 8), (16, 32)):
+        o, k = B.make_opts(precision="fp16x3", scheme="quadrants", prefix_cols=3,
+                           prefix_group=64, max_lanes=lanes, hold_ties=True)
+        steps = B.peps_plan_steps(h, 512, o)
+        merges = [s for s in steps if s["part"] == 4]
+        assert len(merges) == 2
+        assert merges[0]["launches"] == 1            # F_l of all 8 groups
+        assert merges[1]["launches"] == chunks       # Y = F_br F_l^T and the dot
+        left = [s for s in steps if s["part"] in (0, 1) and s["sites"] > 0]
+        assert all(s["launches"] == 1 for s in left)
+    B.peps_destroy(h)
